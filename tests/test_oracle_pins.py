@@ -1,0 +1,422 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix (CPU only).
+
+Each test compares the oracle with something other than itself: closed forms,
+exact quadrature, manufactured solutions built with numpy's Chebyshev routines,
+symmetries the paper states, and the adjoint identity of its Appendix A.
+"""
+import math
+
+import numpy as np
+import pytest
+from numpy.polynomial import chebyshev as npC
+
+import pcf_inputs as gi
+from oracle import PCFOracle, dmd
+from oracle import pcf_oracle as po
+from tests.analytic_fields import Grid, Scalar, vector_eval
+
+LX, LZ = gi.LX_PAPER, gi.LZ_PAPER
+
+
+@pytest.fixture(scope="module")
+def o16():
+    return PCFOracle(16, 17, 16)
+
+
+# ------------------------------------------------------------------ transforms
+@pytest.mark.parametrize("N", [8, 16, 32, 96])
+def test_cheb_derivative_exact(N):
+    """d/dy T_n = n U_{n-1}(y) = n sin(n t)/sin(t), y = cos t, for every n <= N."""
+    t = np.linspace(0.1, 3.0, 23)
+    y = np.cos(t)
+    for n in range(N + 1):
+        e = np.zeros(N + 1)
+        e[n] = 1.0
+        got = npC.chebval(y, po.cheb_deriv(e))
+        want = n * np.sin(n * t) / np.sin(t)
+        assert np.max(np.abs(got - want)) <= 1e-13 * max(1, n * n)
+
+
+@pytest.mark.parametrize("N", [16, 32, 48, 96])
+def test_clenshaw_curtis_exact(N):
+    """sum_j w_j T_n(y_j) = int T_n = 2/(1-n^2) (n even), 0 (n odd), for n <= N."""
+    w = po.clenshaw_curtis_weights(N)
+    y = np.cos(math.pi * np.arange(N + 1) / N)
+    for n in range(N + 1):
+        want = 2.0 / (1.0 - n * n) if n % 2 == 0 else 0.0
+        assert abs((w * np.cos(n * np.arccos(y))).sum() - want) <= 1e-14 * N
+
+
+def test_single_mode_synthesis(o16):
+    """A single (m, p, n) coefficient synthesises to 2 Re(c T_n(y) e^{i(kx x + kz z)})."""
+    rng = np.random.default_rng(1)
+    x = np.arange(o16.nx) * LX / o16.nx
+    z = np.arange(o16.nz) * LZ / o16.nz
+    for (i, j, n) in [(1, 1, 3), (o16.Mx - 2, 2, 7), (2, 0, 0), (0, 3, 16)]:
+        a = np.zeros((o16.Mx, o16.Mz, o16.N + 1), np.complex128)
+        c = rng.standard_normal() + 1j * rng.standard_normal()
+        a[i, j, n] = c
+        if j == 0:
+            a[o16.Mx - i, 0, n] = np.conj(c)
+        got = o16.to_phys(a)
+        kx, kz = o16.kx[i], o16.kz[j]
+        E = np.exp(1j * (kx * x[:, None] + kz * z[None, :]))
+        Tn = np.cos(n * np.arccos(o16.y))[:, None, None]
+        want = 2 * np.real(c * E)[None] * Tn
+        assert np.max(np.abs(got - want)) < 1e-13
+
+
+def test_round_trip(o16):
+    u = gi.random_perturbation(16, 17, 16, 0.1, 3)
+    assert np.max(np.abs(o16.to_spec(o16.to_phys(u)) - u)) < 1e-15
+
+
+# ------------------------------------------------------------------ Stokes step
+def _manufactured(o, sigma, rng):
+    """Admissible (u, v, w) plus arbitrary P; F = (sigma - Lap) u + grad P via numpy Chebyshev."""
+    u = gi.random_perturbation(o.nx, o.ny, o.nz, 1.0, int(rng.integers(1 << 30)))
+    P = rng.standard_normal(u.shape[1:]) + 1j * rng.standard_normal(u.shape[1:])
+    P[0, 0] = 0.0
+    F = np.zeros_like(u)
+    for i in range(o.Mx):
+        for j in range(o.Mz):
+            kx, kz = o.kx[i], o.kz[j]
+            k2 = kx * kx + kz * kz
+            for c in range(3):
+                prof = u[c, i, j]
+                lap = np.zeros(o.N + 1, np.complex128)
+                d2 = npC.chebder(prof, 2)
+                lap[: len(d2)] = d2
+                F[c, i, j] = (sigma + k2) * prof - lap
+            F[0, i, j] += 1j * kx * P[i, j]
+            F[2, i, j] += 1j * kz * P[i, j]
+            dP = npC.chebder(P[i, j])
+            F[1, i, j, : len(dP)] += dP
+    return u, F
+
+
+@pytest.mark.parametrize("grid", [(16, 17, 16), (32, 33, 32)])
+def test_stokes_manufactured(grid):
+    """The tau Stokes solve recovers an admissible polynomial field exactly."""
+    o = PCFOracle(*grid)
+    rng = np.random.default_rng(7)
+    sigma = 1.0 / (o.nu * o.dt)
+    u, F = _manufactured(o, sigma, rng)
+    got = o.stokes(F, sigma)
+    assert np.max(np.abs(got - u)) <= 1e-12 * np.max(np.abs(u)) * 100
+
+
+def test_stokes_output_admissible(o16):
+    """Any right-hand side gives a divergence-free (all coefficients), no-slip output."""
+    rng = np.random.default_rng(2)
+    F = rng.standard_normal((3, o16.Mx, o16.Mz, o16.N + 1)) + 1j * rng.standard_normal((3, o16.Mx, o16.Mz, o16.N + 1))
+    F[:, o16.Mx - 1:o16.Kx:-1, 0] = np.conj(F[:, 1:o16.Kx + 1, 0])
+    out = o16.stokes_step(F, 0.25)
+    scale = np.max(np.abs(out))
+    assert np.max(np.abs(o16.divergence(out))) <= 1e-12 * scale * 10
+    for wv in o16.wall_values(out):
+        assert np.max(np.abs(wv)) <= 1e-12 * scale
+
+
+# ------------------------------------------------------------------ the method
+def test_laminar_is_equilibrium(o16):
+    """u = 0 (laminar Couette u_b = y) gives r1 = 0 and f = 0 exactly (§5)."""
+    z = np.zeros((3, o16.Mx, o16.Mz, o16.N + 1), np.complex128)
+    r1, J = o16.residual(z)
+    assert J == 0.0 and np.all(r1 == 0)
+    assert np.all(o16.adjoint_direction(z, r1) == 0)
+
+
+def test_r1_and_f_admissible(o16):
+    """§4 steps 2 and 4: r1 and f are divergence-free and vanish at the walls."""
+    u = gi.random_perturbation(16, 17, 16, 0.1, 0)
+    _, _, r1, f = o16.descent_step(u, 0.01)
+    for a in (r1, f):
+        scale = np.max(np.abs(a))
+        assert np.max(np.abs(o16.divergence(a))) <= 1e-13 * scale * 100
+        for wv in o16.wall_values(a):
+            assert np.max(np.abs(wv)) <= 1e-14 * scale * 100
+
+
+def test_descent_monotone(o16):
+    """J decreases monotonically along the descent for a small step (§2, §3.4)."""
+    u = gi.random_perturbation(16, 17, 16, 0.1, 1)
+    _, hist = o16.run(u, 0.01, 40)
+    assert np.all(np.diff(hist) < 0)
+
+
+def _shift(o, a, lx, lz):
+    return a * np.exp(1j * (o.KX * lx + o.KZ * lz))
+
+
+def _sigma1(o, a):
+    """[u,v,w](x,y,z) -> [-u,-v,w](-x,-y,z)."""
+    n = np.arange(o.N + 1)
+    idx = (-np.arange(o.Mx)) % o.Mx
+    out = a[:, idx] * ((-1.0) ** n)
+    out[0] *= -1
+    out[1] *= -1
+    return out
+
+
+def _sigma2(o, a):
+    """[u,v,w](x,y,z) -> [u,v,-w](x,y,-z)."""
+    idx = (-np.arange(o.Mx)) % o.Mx
+    out = np.conj(a[:, idx])
+    out[2] *= -1
+    return out
+
+
+@pytest.mark.parametrize("op", ["shift", "sigma1", "sigma2", "s1"])
+def test_equivariance(o16, op):
+    """The descent step commutes with the symmetries of plane Couette flow (§3.4, §5)."""
+    u = gi.random_perturbation(16, 17, 16, 0.1, 5)
+    if op == "shift":
+        g = lambda a: _shift(o16, a, 0.37 * LX, 0.81 * LZ)
+    elif op == "sigma1":
+        g = lambda a: _sigma1(o16, a)
+    elif op == "sigma2":
+        g = lambda a: _sigma2(o16, a)
+    else:
+        g = lambda a: _shift(o16, _sigma1(o16, a), LX / 2, LZ / 2)
+    a1 = g(o16.descent_step(u, 0.01)[0])
+    a2 = o16.descent_step(g(u), 0.01)[0]
+    assert np.max(np.abs(a1 - a2)) <= 1e-14
+
+
+# ------------------------------------------------------------------ continuous pins
+def _residual(v, gv, lapv, gq, Y, nu, M=po.nonlinear_M):
+    """R(U) = [F(v, q), div v], F = M(v) - grad q + nu Lap v (§3.1, Eq. (momentum))."""
+    r1 = M(v, gv, Y) - gq + nu * lapv
+    r2 = gv[0, 0] + gv[1, 1] + gv[2, 2]
+    return r1, r2
+
+
+def _adjoint(v, gv, r1, gr1, lapr1, rho, grho, Y, nu, Nfun=po.adjoint_N):
+    """L+(U; R) of §3.3 / Appendix A: [N(r1) + (div v) r1 + nu Lap r1 - grad rho, div r1]."""
+    divv = gv[0, 0] + gv[1, 1] + gv[2, 2]
+    a1 = Nfun(r1, gr1, v, gv, Y) + divv[None] * r1 + nu * lapr1 - grho
+    a2 = gr1[0, 0] + gr1[1, 1] + gr1[2, 2]
+    return a1, a2
+
+
+def _fields(rng, K, n0, walls):
+    return [Scalar.random(rng, K, n0, w, LX, LZ) for w in walls]
+
+
+def _eval_U(comps, g):
+    v, gv, lapv = vector_eval(comps[:3], g)
+    q = comps[3].eval(g)
+    return v, gv, lapv, np.stack([q["fx"], q["fy"], q["fz"]]), q["f"]
+
+
+def _adjoint_identity_gap(Nfun=po.adjoint_N, M=po.nonlinear_M):
+    rng = np.random.default_rng(11)
+    g = Grid(LX, LZ, nf=12, ng=24)
+    nu = 1.0 / 400.0
+    K, n0 = 1, 5
+    U = _fields(rng, K, n0, [1, 1, 1, 0])
+    Rf = _fields(rng, K, n0, [1, 1, 1, 0])
+    G = _fields(rng, K, n0, [1, 1, 1, 0])
+    Up = [a + b for a, b in zip(U, G)]
+    Um = [a + b.scaled(-1.0) for a, b in zip(U, G)]
+    # L(U; G) = (R(U + G) - R(U - G))/2, exact for the quadratic residual
+    vp, gvp, lvp, gqp, _ = _eval_U(Up, g)
+    vm, gvm, lvm, gqm, _ = _eval_U(Um, g)
+    r1p, r2p = _residual(vp, gvp, lvp, gqp, g.Y, nu, M)
+    r1m, r2m = _residual(vm, gvm, lvm, gqm, g.Y, nu, M)
+    L1, L2 = 0.5 * (r1p - r1m), 0.5 * (r2p - r2m)
+    r, gr, lapr = vector_eval(Rf[:3], g)
+    rho = Rf[3].eval(g)
+    lhs_t = (L1 * r).sum(axis=0) + L2 * rho["f"]
+    v, gv, _, _, _ = _eval_U(U, g)
+    a1, a2 = _adjoint(v, gv, r, gr, lapr, rho["f"], np.stack([rho["fx"], rho["fy"], rho["fz"]]), g.Y, nu, Nfun)
+    gvv, _, _ = vector_eval(G[:3], g)
+    g2 = G[3].eval(g)["f"]
+    rhs_t = (gvv * a1).sum(axis=0) + g2 * a2
+    lhs, rhs = g.integrate(lhs_t), g.integrate(rhs_t)
+    scale = g.integrate(np.abs(lhs_t)) + g.integrate(np.abs(rhs_t))
+    return abs(lhs - rhs) / scale
+
+
+def test_adjoint_identity():
+    """<L(U;G), R> = <G, L+(U;R)> for U, R, G in P0 (Appendix A), exact quadrature."""
+    assert _adjoint_identity_gap() <= 1e-12
+
+
+def _bad_N_sign(q, gq, u, gu, y):
+    out = po.adjoint_N(q, gq, u, gu, y)
+    out[1] = out[1] + 2.0 * q[0]          # flips the sign of the base-flow transpose term
+    return out
+
+
+def _bad_N_index(q, gq, u, gu, y):
+    U0 = u[0] + y
+    out = np.empty_like(q)
+    for i in range(3):
+        adv = U0 * gq[i, 0] + u[1] * gq[i, 1] + u[2] * gq[i, 2]
+        tr = q[0] * gu[i, 0] + q[1] * gu[i, 1] + q[2] * gu[i, 2]   # (grad U) q instead of (grad U)^T q
+        out[i] = adv - tr
+    out[1] = out[1] - q[0]
+    return out
+
+
+@pytest.mark.parametrize("bad", [_bad_N_sign, _bad_N_index])
+def test_adjoint_identity_catches_planted_mistakes(bad):
+    """A dropped or transposed term in N breaks the identity by many orders of magnitude."""
+    assert _adjoint_identity_gap(Nfun=bad) > 1e-4
+
+
+def test_M_is_perturbative_nse():
+    """M(u) = -((u_b+u).grad)(u_b+u) + (u_b.grad)u_b with u_b = (y,0,0) (§3.1)."""
+    rng = np.random.default_rng(3)
+    g = Grid(LX, LZ, nf=8, ng=10)
+    comps = _fields(rng, 1, 4, [1, 1, 1])
+    u, gu, _ = vector_eval(comps, g)
+    Ut = u.copy()
+    Ut[0] += g.Y
+    gUt = gu.copy()
+    gUt[0, 1] += 1.0
+    full = -np.einsum("j...,ij...->i...", Ut, gUt)
+    got = po.nonlinear_M(u, gu, g.Y)
+    assert np.max(np.abs(got - full)) <= 1e-13
+
+
+def test_gradient_vs_finite_differences():
+    """dJ^2/dU along G equals 2 <G, L+(U; R(U))> (the gradient of §2), to 1e-6 relative.
+
+    G satisfies g1 = dg1/dy = 0 and g2 = 0 at the walls, so every boundary term of
+    Appendix A vanishes for any U in P0 without requiring R(U) in P0.
+    """
+    rng = np.random.default_rng(5)
+    g = Grid(LX, LZ, nf=12, ng=24)
+    nu = 1.0 / 400.0
+    U = _fields(rng, 1, 5, [1, 1, 1, 0])
+    G = _fields(rng, 1, 5, [2, 2, 2, 1])
+
+    def cost(eps):
+        comps = []
+        for a, b in zip(U, G):
+            # promote both to the same wall factor by folding the wall into the coefficients
+            comps.append(_sum_fields(a, b, eps))
+        v, gv, lv, gq, _ = _eval_U_mixed(comps, g)
+        r1, r2 = _residual(v, gv, lv, gq, g.Y, nu)
+        return g.integrate((r1 ** 2).sum(axis=0) + r2 ** 2)
+
+    eps = 1e-3
+    d1 = (cost(eps) - cost(-eps)) / (2 * eps)
+    d2 = (cost(eps / 2) - cost(-eps / 2)) / eps
+    fd = (4 * d2 - d1) / 3.0        # removes the exact eps^2 term of the quartic
+    a_dot = _adjoint_on_residual(U, g, nu)
+    gvv, _, _ = vector_eval(G[:3], g)
+    g2 = G[3].eval(g)["f"]
+    grad_dot = 2.0 * g.integrate((gvv * a_dot[0]).sum(axis=0) + g2 * a_dot[1])
+    assert abs(fd - grad_dot) <= 1e-6 * abs(grad_dot)
+
+
+class _Mixed:
+    """Sum of two Scalars with different wall factors (evaluated term by term)."""
+
+    def __init__(self, parts):
+        self.parts = parts
+
+    def eval(self, g):
+        evs = [p.eval(g) for p in self.parts]
+        return {k: sum(e[k] for e in evs) for k in evs[0]}
+
+
+def _sum_fields(a, b, eps):
+    return _Mixed([a, b.scaled(eps)])
+
+
+def _eval_U_mixed(comps, g):
+    ev = [c.eval(g) for c in comps[:3]]
+    v = np.stack([e["f"] for e in ev])
+    gv = np.stack([np.stack([e["fx"], e["fy"], e["fz"]]) for e in ev])
+    lv = np.stack([e["lap"] for e in ev])
+    q = comps[3].eval(g)
+    return v, gv, lv, np.stack([q["fx"], q["fy"], q["fz"]]), q["f"]
+
+
+def _adjoint_on_residual(U, g, nu):
+    """L+(U; R(U)), with R(U) and its derivatives obtained exactly.
+
+    R(U) is a trigonometric polynomial in (x, z) (degree <= 2K) and a polynomial in y
+    (degree well below 40); sampled on an FFT x Chebyshev-Lobatto grid it is interpolated
+    exactly (numpy FFT and chebfit), then differentiated and evaluated on the quadrature grid.
+    """
+    K = U[0].K
+    nfx = 4 * K + 8
+    ny = 40
+    yy = np.cos(np.pi * np.arange(ny + 1) / ny)
+    gg = Grid(g.Lx, g.Lz, nf=nfx, ng=2)
+    gg.y = yy
+    gg.Y = yy[:, None, None]
+    v, gv, lv, gq, _ = _eval_U(U, gg)
+    r1, r2 = _residual(v, gv, lv, gq, gg.Y, nu)
+
+    def spectral(fgrid):
+        """Return callables evaluating f, grad f, Lap f on g from samples on gg."""
+        Fh = np.fft.fft2(fgrid, axes=(1, 2)) / nfx ** 2
+        kx = 2 * np.pi * np.fft.fftfreq(nfx, 1.0 / nfx) / g.Lx
+        kz = 2 * np.pi * np.fft.fftfreq(nfx, 1.0 / nfx) / g.Lz
+        coef = npC.chebfit(yy, Fh.reshape(ny + 1, -1), ny)      # (ny+1, nfx*nfx)
+        X = g.x[None, :, None]
+        Z = g.z[None, None, :]
+        res = {k: np.zeros((len(g.y), len(g.x), len(g.z))) for k in ("f", "fx", "fy", "fz", "lap")}
+        for a in range(nfx):
+            for b in range(nfx):
+                c = coef[:, a * nfx + b]
+                if np.max(np.abs(c)) < 1e-300:
+                    continue
+                P0 = npC.chebval(g.y, c)[:, None, None]
+                P1 = npC.chebval(g.y, npC.chebder(c))[:, None, None]
+                P2 = npC.chebval(g.y, npC.chebder(c, 2))[:, None, None]
+                E = np.exp(1j * (kx[a] * X + kz[b] * Z))
+                res["f"] += np.real(P0 * E)
+                res["fx"] += np.real(1j * kx[a] * P0 * E)
+                res["fy"] += np.real(P1 * E)
+                res["fz"] += np.real(1j * kz[b] * P0 * E)
+                res["lap"] += np.real((P2 - (kx[a] ** 2 + kz[b] ** 2) * P0) * E)
+        return res
+    rr = [spectral(r1[i]) for i in range(3)]
+    rh = spectral(r2)
+    r = np.stack([e["f"] for e in rr])
+    gr = np.stack([np.stack([e["fx"], e["fy"], e["fz"]]) for e in rr])
+    lapr = np.stack([e["lap"] for e in rr])
+    vq, gvq, _, _, _ = _eval_U(U, g)
+    return _adjoint(vq, gvq, r, gr, lapr, rh["f"], np.stack([rh["fx"], rh["fy"], rh["fz"]]), g.Y, nu)
+
+
+# ------------------------------------------------------------------ snapshot vector, DMD
+def test_psi_dimension_matches_paper():
+    """N = 20218 independent reals at Nx x Ny x Nz = 32 x 31 x 32 (§6.2)."""
+    assert PCFOracle(32, 31, 32).psi_dim() == 20218
+
+
+@pytest.mark.parametrize("grid", [(16, 17, 16), (32, 33, 32)])
+def test_psi_round_trip(grid):
+    o = PCFOracle(*grid)
+    u = gi.streak_roll(*grid, seed=2)
+    psi = o.to_psi(u)
+    assert psi.shape == (o.psi_dim(),)
+    assert np.max(np.abs(o.from_psi(psi) - u)) < 1e-15
+
+
+def test_dmd_recovers_affine_fixed_point():
+    """Snapshots of psi_{k+1} = psi* + A (psi_k - psi*) with symmetric A, spectrum in (0,1):
+    the steady DMD mode is psi* exactly (§6.2: omega_1 = 0, real eigenvalues)."""
+    rng = np.random.default_rng(0)
+    n, r0, M = 400, 6, 12
+    Q, _ = np.linalg.qr(rng.standard_normal((n, r0)))
+    mu = np.linspace(0.3, 0.95, r0)
+    star = rng.standard_normal(n)
+    a = rng.standard_normal(r0)
+    S = np.stack([star + Q @ (a * mu ** k) for k in range(M + 1)], axis=1)
+    rstar = dmd.snapshot_rank(S, 1e-10)
+    assert rstar == r0 + 1
+    psi_s, lam = dmd.dmd_steady_state(S, rstar)
+    assert abs(lam[0] - 1.0) < 1e-10
+    assert np.max(np.abs(psi_s - star)) <= 1e-9 * np.max(np.abs(star))
+    best, r, costs = dmd.dmd_extrapolate(S, lambda p: np.linalg.norm(p - star), 1e-10)
+    assert r == rstar and costs[r] < 1e-8
