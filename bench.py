@@ -1,0 +1,306 @@
+"""Benchmark: gradient evaluations per second of the adjoint-descent step (one evaluation =
+one descent step of one instance: residual r1 plus adjoint direction f plus update, §4).
+
+Workload (N=1): plane Couette flow, Re = 400, Lx = 2 pi/1.14, Lz = 2 pi/2.5, grid
+32 x 33 x 32 (Fourier x Chebyshev x Fourier, 2/3 dealiasing), 8 seeded streak/roll
+guesses (+0.02 noise), FP64, dt = dtau_hat = 0.25, dtau = 0.01.  A step advances all 8
+instances.  L2 is flushed (256 MB write) before every timed step.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this project: the paper
+ships no code) on the host cores, on a bounded sample of the same workload.
+Under torchrun (N>1) every rank runs its own 8 instances (replicas, weak scaling).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GRID = (32, 33, 32)
+BATCH = 8
+RE = 400.0
+DT = 0.25
+DTAU_HAT = 0.25
+DTAU = 0.01
+WORKLOAD = "PCF Re=400 box 2pi/1.14 x 2 x 2pi/2.5, 32x33x32, 8 streak/roll guesses, plain FP64 descent step"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def _fft_flops(L):
+    return 5.0 * L * math.log2(L)
+
+
+def kernel_flops(grid, batch):
+    """Algorithmic FP64 flops per launch of each kernel class (FFT counted as 5 L log2 L,
+    dense Chebyshev matrices with parity folding as 2 flops per multiply-add)."""
+    nx, ny, nz = grid
+    Kx, Kz = nx // 3 - 1, nz // 3 - 1
+    Mx, Mz = 2 * Kx + 1, Kz + 1
+    nm = Mx * Mz
+    N = ny - 1
+    H = N // 2 + 1
+    plane_fft = Mz * _fft_flops(nx) + (nx // 2) * _fft_flops(nz)
+    synth = batch * 11 * ny * plane_fft
+    prod_M = batch * 3 * ny * (plane_fft + nx * nz * 8.0)
+    prod_N = batch * 3 * ny * (plane_fft + nx * nz * 14.0)
+    cheb_fold = 2.0 * 2.0 * H * (2 * H - 1)            # per complex column, folded matvec
+    analysis = 3 * cheb_fold
+    synth_y = 5 * cheb_fold
+    solve = 2 * 2 * (8.0 * 3 * H + 6 * H) + 3 * 2 * (N + 1) * 4.0
+    mode_step = batch * nm * (analysis + solve + synth_y)
+    return {"xzsynth_u": synth, "xzsynth_q": synth, "prod_M": prod_M, "prod_N": prod_N,
+            "mode_phi": mode_step, "mode_psi": mode_step, "ysynth": batch * nm * synth_y}
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = max((num(r[2]) for r in rows if num(r[2])), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl" if os.environ.get("PCF_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+        return dist, dist.get_rank(), ws
+    return None, 0, 1
+
+
+def _oracle_sample(seconds, out_path):
+    """Runs in a fresh process: oracle descent steps on one streak/roll guess until `seconds`."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    os.environ.setdefault("MKL_NUM_THREADS", "1")
+    import numpy as np  # noqa: F401
+    import pcf_inputs as gi
+    from oracle import PCFOracle
+    o = PCFOracle(*GRID, Re=RE, dt=DT, dtau_hat=DTAU_HAT)
+    u = gi.streak_roll(*GRID, seed=0)
+    o.descent_step(u, DTAU)  # factorisation + warm-up, untimed
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        u, J, _, _ = o.descent_step(u, DTAU)
+        n += 1
+        if time.perf_counter() - t0 >= seconds and n >= 3:
+            break
+    dt = time.perf_counter() - t0
+    with open(out_path, "w") as f:
+        json.dump({"steps": n, "seconds": dt}, f)
+
+
+def cpu_baseline(seconds=15.0):
+    fd, path = tempfile.mkstemp(suffix=".json")
+    os.close(fd)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--_oracle-sample", str(seconds), path]
+    subprocess.run(cmd, check=True, env=env, cwd=ROOT)
+    with open(path) as f:
+        r = json.load(f)
+    os.unlink(path)
+    v = r["steps"] / r["seconds"]
+    return {"value": v, "unit": "gradient evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"{r['steps']} descent steps of 1 of the 8 guesses at 32x33x32 in {r['seconds']:.1f} s "
+                      "(numpy FFT + dense per-mode LU, 1 thread)"}
+
+
+def run_reference(args):
+    dist, rank, ws = _dist()
+    if rank != 0:
+        return
+    per = max(3.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
+    cb = cpu_baseline(seconds=per * max(1, args.steps))
+    line = {"impl": "reference", "metric": "gradient evals/s", "value": cb["value"], "unit": "gradient evals/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / cb["value"] * BATCH,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": list(GRID), "batch": BATCH},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "gradient evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2306_00165_gb300 as pcf
+    import pcf_inputs as gi
+
+    dist, rank, ws = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    seeds = list(range(rank * BATCH, rank * BATCH + BATCH))
+    u0 = gi.batch(gi.streak_roll, seeds, *GRID)
+    s = pcf.Solver(*GRID, batch=BATCH, Re=RE, dt=DT, dtau_hat=DTAU_HAT)
+    u = torch.from_numpy(u0).to(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        s.descent_step(u, DTAU, 1, hist=True)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = Clocks()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    hist = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        H = s.descent_step(u, DTAU, 1, hist=True)
+        ends[k].record(stream)
+        hist.append(H)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = BATCH * ws * args.steps / (ms * 1e-3)
+    J_last = torch.cat(hist).cpu().numpy()[-1]
+
+    # e2e: host buffers through the C ABI, copies inside the timed region
+    uh = torch.from_numpy(u0.copy()).pin_memory()
+    hh = torch.empty((1, BATCH), dtype=torch.float64).pin_memory()
+    for _ in range(3):
+        s.descent_step_host(uh, DTAU, 1, hh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ne = max(10, args.steps)
+    for _ in range(ne):
+        s.descent_step_host(uh, DTAU, 1, hh)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": BATCH * ws * ne / e2e_s, "unit": "gradient evals/s",
+           "h2d_bytes_per_step": uh.numel() * uh.element_size(),
+           "d2h_bytes_per_step": uh.numel() * uh.element_size() + hh.numel() * hh.element_size()}
+
+    # per-kernel CUDA-event timing (eager launches, same steps, same stream) for the roofline
+    s.set_kernel_timing(True)
+    nk = max(5, min(args.steps, 50))
+    for _ in range(nk):
+        flush.fill_(1.0)
+        s.descent_step(u, DTAU, 1, hist=True)
+    torch.cuda.synchronize()
+    kt = s.kernel_times()
+    s.set_kernel_timing(False)
+    flops = kernel_flops(GRID, BATCH)
+    total_ms = sum(v[0] for v in kt.values())
+    dom = max(kt, key=lambda k: kt[k][0])
+    dom_ms = kt[dom][0] / max(1, kt[dom][1])
+    fp64 = pcf.probe_fp64_peak()
+    achieved = flops[dom] / (dom_ms * 1e-3) / 1e12
+    peak_tf = fp64 / 1e3
+    roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_tf, 4), "unit": "TFLOP/s",
+            "frac": round(achieved / peak_tf, 4), "traffic": None, "kernel": dom,
+            "peak_source": "measured FP64 DFMA throughput (k_fp64_probe) on this GPU",
+            "kernel_share": round(kt[dom][0] / total_ms, 4),
+            "kernel_ms_per_launch": round(dom_ms, 5),
+            "per_kernel_ms_per_step": {k: round(v[0] / nk, 5) for k, v in kt.items()}}
+
+    if rank == 0:
+        line = {"metric": "gradient evals/s", "value": value, "unit": "gradient evals/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "grid": list(GRID), "batch_per_gpu": BATCH, "Re": RE,
+                           "dt": DT, "dtau_hat": DTAU_HAT, "dtau": DTAU,
+                           "l2": "flushed (256 MB write) before every timed step",
+                           "parallelism": f"replicas x{ws}"},
+                "e2e": e2e, "gpu_launches": (1 + s.launches_per_step()) * args.steps,
+                "roofline": roof, "clocks": ck, "wall_s": wall,
+                "J_after": [float(x) for x in J_last]}
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(15.0)
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "--_oracle-sample":
+        _oracle_sample(float(sys.argv[2]), sys.argv[3])
+        return
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

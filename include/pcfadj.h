@@ -1,0 +1,170 @@
+/*
+ * pcfadj.h - C ABI of the GB300 (sm_103a) adjoint-descent solver for equilibria of
+ * plane Couette flow (Ashtari & Schneider, arXiv 2306.00165).
+ *
+ * The library advances the constrained adjoint-descent dynamics of §3.4,
+ * Eq. (adjoint_evolution_divergence_free), with the five-step scheme of §4:
+ * (1) an influence-matrix Stokes step of the Navier-Stokes equations, Eq. (u_trick),
+ * (2) the finite-difference residual r1, Eq. (r1_approximation), (3) a Stokes step of
+ * the dummy dynamics for r1, Eq. (g_trick), (4) the finite-difference descent
+ * direction f, Eq. (f_approximation), and (5) the Euler update, Eq. (forward_Euler_update).
+ * DMD extrapolation follows §6.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Spectral field ("uhat" layout): the Fourier x Chebyshev x Fourier coefficients of
+ * §4, Eq. (Foureir_Chebyshev_Fourier), stored as interleaved complex doubles
+ * (re, im) in the order [batch][3][Mx][Mz][Ny] with Ny (Chebyshev index n) fastest.
+ * Component 0, 1, 2 = u, v, w.  x-modes are stored m = 0..Kx, -Kx..-1
+ * (Mx = 2 Kx + 1, Kx = nx/3 - 1); z-modes p = 0..Kz (Mz = Kz + 1, Kz = nz/3 - 1);
+ * the p < 0 half is the complex conjugate.  One instance holds 3*Mx*Mz*Ny complex
+ * values (pcf_state_len).  Inputs must be admissible: divergence-free and zero at
+ * y = +-1 (the state space of §3.1); the p = 0 plane conjugate-symmetric in m.
+ *
+ * Memory: unless an argument says "host", every pointer is a DEVICE pointer owned
+ * by the caller; the library never frees it.  The context owns its workspace and
+ * tables (allocated once in pcf_create).
+ *
+ * Streams: every call is enqueued on the stream given to pcf_create and returns
+ * without synchronising, except where noted (pcf_dmd_extrapolate and the *_host
+ * variants synchronise).  Errors are reported only by the return code: a call
+ * that returns anything but PCF_OK has enqueued no partial update of its outputs
+ * unless noted; nothing aborts the process.
+ *
+ * Grids: nx, nz in {16, 32, 48, 64, 96, 128} (products of 2, 3, 4), ny odd with
+ * 9 <= ny <= 129; batch >= 1.
+ */
+#ifndef PCFADJ_H
+#define PCFADJ_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PCF_ABI_VERSION 1
+
+typedef enum {
+  PCF_OK = 0,
+  PCF_EINVAL = 1,     /* bad size, pointer or parameter */
+  PCF_ECUDA = 2,      /* a CUDA runtime call failed */
+  PCF_ENOMEM = 3,     /* device or host allocation failed */
+  PCF_ENAN = 4,       /* a residual norm came out non-finite */
+  PCF_ETIMEOUT = 5,   /* a bounded device wait gave up */
+  PCF_ENOTCONV = 6,   /* no convergence within the step budget */
+  PCF_ENOTSUP = 7     /* valid request this build does not provide */
+} pcf_status;
+
+typedef enum { PCF_FP64 = 0, PCF_MIXED = 1 } pcf_precision;
+
+/* Problem description; all instances of a context share one grid.
+ * Re: Reynolds number (nu = 1/Re); Lx, Lz: box lengths; dt: physical step of the
+ * Navier-Stokes Stokes step (step 1 of §4); dtau_hat: step of the dummy dynamics
+ * (step 3 of §4).  The paper uses Re = 400, Lx = 2 pi/1.14, Lz = 2 pi/2.5,
+ * dt = dtau_hat = 0.25 (§5.1). */
+typedef struct pcf_params {
+  int nx, ny, nz;
+  int batch;
+  double Lx, Lz, Re;
+  double dt, dtau_hat;
+  int precision;        /* pcf_precision; PCF_FP64 for the plain method */
+  int modes_per_block;  /* tile of the per-mode kernels; 0 = library default */
+  int reserved[2];
+} pcf_params;
+
+typedef struct pcf_ctx pcf_ctx;
+
+/* Version of this ABI (PCF_ABI_VERSION). */
+int pcf_abi_version(void);
+
+/* Human-readable name of a status code; never NULL. */
+const char* pcf_status_str(pcf_status s);
+
+/* Number of complex values of one instance in the uhat layout: 3*Mx*Mz*ny.
+ * Returns 0 for an invalid grid. */
+long long pcf_state_len(int nx, int ny, int nz);
+
+/* Length of the real snapshot vector psi of §6.2 (minimum number of independent
+ * variables of a divergence-free Fourier-Chebyshev field): per independent mode
+ * 2(ny-4) + 2(ny-2) reals, plus 2(ny-2) for the mean u, w.  20218 at 32x31x32. */
+long long pcf_psi_len(int nx, int ny, int nz);
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL =
+ * default stream).  Builds the per-mode influence-matrix tables of the Stokes steps
+ * for dt and dtau_hat (§4) and allocates the workspace.  *out is set only on PCF_OK. */
+pcf_status pcf_create(const pcf_params* params, void* stream, pcf_ctx** out);
+
+/* Release a context (waits for its stream).  NULL is ignored. */
+void pcf_destroy(pcf_ctx* ctx);
+
+/* Steps 1-2 of §4: r1 = (Phi_dt(u) - u)/dt, Eq. (r1_approximation), where Phi_dt is
+ * one IMEX-Euler influence-matrix Stokes step of Eq. (u_trick) with
+ * M(u) = -(u_b.grad)u - (u.grad)u_b - (u.grad)u, u_b = (y, 0, 0).
+ * u_hat: batch instances in the uhat layout (input).  r_hat: same layout (output).
+ * r_norm: batch doubles (output, may be NULL): J = ||r1||, the volume-normalised L2
+ * norm with Clenshaw-Curtis weights in y. */
+pcf_status pcf_residual(pcf_ctx* ctx, const double* u_hat, double* r_hat, double* r_norm);
+
+/* Steps 3-4 of §4: f = -(Psi_dtauhat(r1) - r1)/dtau_hat, Eq. (f_approximation), where
+ * Psi is one Stokes step of the dummy dynamics Eq. (g_trick) with
+ * N(r1) = (grad r1)(u_b + u) - (grad(u_b + u))^T r1 (u frozen), taken in the
+ * diffusive direction of tau-hat.  u_hat, r_hat: inputs (r_hat normally from
+ * pcf_residual); f_hat: output; all in the uhat layout. */
+pcf_status pcf_adjoint_gradient(pcf_ctx* ctx, const double* u_hat, const double* r_hat, double* f_hat);
+
+/* One influence-matrix Stokes step alone (the solve used by steps 1 and 3 of §4):
+ * out solves (1/step - nu Lap) out + grad p = rhs, div out = 0, out(y=+-1) = 0, per
+ * Fourier mode with the Chebyshev-tau method (momentum on rows 0..ny-3, divergence
+ * on every row).  step must equal params.dt or params.dtau_hat (else PCF_EINVAL).
+ * rhs_hat, out_hat: uhat layout. */
+pcf_status pcf_influence_matrix_solve(pcf_ctx* ctx, const double* rhs_hat, double* out_hat, double step);
+
+/* nsteps descent steps of §4 (steps 1-5 each), in place on u_hat:
+ * u <- u + dtau f.  r_norm_hist: nsteps*batch doubles ([step][instance], J before
+ * each step) or NULL.  Launched as a captured CUDA graph. */
+pcf_status pcf_descent_step(pcf_ctx* ctx, double* u_hat, double dtau, int nsteps, double* r_norm_hist);
+
+/* Same as pcf_descent_step with HOST buffers: copies u_hat (host, batch states) to
+ * the device, runs nsteps steps, copies the updated state and the norm history
+ * (host, nsteps*batch doubles, may be NULL) back, then synchronises. */
+pcf_status pcf_descent_step_host(pcf_ctx* ctx, double* u_hat_host, double dtau, int nsteps, double* r_norm_hist_host);
+
+/* Snapshot vector of §6.2 for every instance: psi[batch][pcf_psi_len] (device,
+ * output) from u_hat (input).  Coordinates: Chebyshev coefficients 0..ny-5 of v and
+ * 0..ny-3 of eta = i kz u - i kx w per independent mode (re, im), then the mean u,
+ * w coefficients 0..ny-3. */
+pcf_status pcf_snapshot(pcf_ctx* ctx, const double* u_hat, double* psi);
+
+/* Inverse of pcf_snapshot: completes the wall conditions and rebuilds u_hat. */
+pcf_status pcf_from_snapshot(pcf_ctx* ctx, const double* psi, double* u_hat);
+
+/* DMD steady-state extrapolation of §6 for instance `inst`.
+ * snapshots: device, (M+1) columns of pcf_psi_len doubles, column-major (column k =
+ * snapshot k, oldest first); the M pairs are (s_k, s_{k+1}).  Householder QR of the
+ * snapshot matrix on the device; SVD, eigen-decomposition and amplitudes of the
+ * small projected problem on the host; for each truncation rank r = r*..1 (r* = number
+ * of singular values above rank_tol * sigma_1) the steady mode b_1 phi_1 (|ln lambda|
+ * smallest) is rebuilt and its residual norm evaluated; the r with the smallest norm
+ * is kept.  u_out_hat: device, one instance (output).  rank_used, j_out: host
+ * (outputs, may be NULL).  Synchronises.  PCF_ENAN if no candidate has a finite norm. */
+pcf_status pcf_dmd_extrapolate(pcf_ctx* ctx, const double* snapshots, int M, double rank_tol,
+                               double* u_out_hat, int* rank_used, double* j_out);
+
+/* Measures the FP64 FMA throughput of the current device with a dependent-chain-free
+ * DFMA loop (used for the ALU roofline).  gflops: host output.  Synchronises. */
+pcf_status pcf_probe_fp64_peak(void* stream, double* gflops);
+
+/* Enables (1) or disables (0) per-kernel CUDA-event timing on the context stream for
+ * subsequent eager (non-graph) calls; pcf_kernel_times returns the accumulated
+ * milliseconds and launch counts per kernel class (host arrays of length n).
+ * Kernel classes: 0 ysynth, 1 xzsynth_u, 2 prod_M, 3 mode_phi, 4 xzsynth_q,
+ * 5 prod_N, 6 mode_psi. */
+pcf_status pcf_set_kernel_timing(pcf_ctx* ctx, int enable);
+pcf_status pcf_kernel_times(pcf_ctx* ctx, double* ms, long long* launches, int n);
+
+/* Number of kernel launches one descent step issues (for launch accounting). */
+int pcf_launches_per_step(pcf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCFADJ_H */

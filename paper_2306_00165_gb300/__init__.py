@@ -1,0 +1,196 @@
+"""Thin Python binding of libpcfadj (the GB300 adjoint-descent solver for plane Couette flow).
+
+Argument marshalling only: every step of the method runs in the library's CUDA kernels.
+PyTorch provides device memory and the current stream.  There is no CPU fallback: if the
+compiled library is missing, importing the bindings raises.
+
+Names follow the C ABI (include/pcfadj.h): residual, adjoint_gradient,
+influence_matrix_solve, descent_step, dmd_extrapolate.
+"""
+import ctypes
+import math
+import os
+
+from . import build as _build
+
+__all__ = ["Solver", "load_library", "state_shape", "psi_len", "probe_fp64_peak", "PCFError"]
+
+LX_PAPER = 2.0 * math.pi / 1.14
+LZ_PAPER = 2.0 * math.pi / 2.5
+
+_lib = None
+
+
+class PCFError(RuntimeError):
+    pass
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("batch", ctypes.c_int),
+                ("Lx", ctypes.c_double), ("Lz", ctypes.c_double), ("Re", ctypes.c_double),
+                ("dt", ctypes.c_double), ("dtau_hat", ctypes.c_double),
+                ("precision", ctypes.c_int), ("modes_per_block", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
+
+
+def load_library(path=None):
+    """Load the in-tree libpcfadj.so (built by ``build.build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise PCFError(f"libpcfadj.so not found at {path}; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.c_double
+    I = ctypes.c_int
+    sigs = {
+        "pcf_abi_version": (I, []),
+        "pcf_status_str": (ctypes.c_char_p, [I]),
+        "pcf_state_len": (ctypes.c_longlong, [I, I, I]),
+        "pcf_psi_len": (ctypes.c_longlong, [I, I, I]),
+        "pcf_create": (I, [ctypes.POINTER(_Params), P, ctypes.POINTER(P)]),
+        "pcf_destroy": (None, [P]),
+        "pcf_residual": (I, [P, P, P, P]),
+        "pcf_adjoint_gradient": (I, [P, P, P, P]),
+        "pcf_influence_matrix_solve": (I, [P, P, P, D]),
+        "pcf_descent_step": (I, [P, P, D, I, P]),
+        "pcf_descent_step_host": (I, [P, P, D, I, P]),
+        "pcf_snapshot": (I, [P, P, P]),
+        "pcf_from_snapshot": (I, [P, P, P]),
+        "pcf_dmd_extrapolate": (I, [P, P, I, D, P, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "pcf_probe_fp64_peak": (I, [P, ctypes.POINTER(D)]),
+        "pcf_set_kernel_timing": (I, [P, I]),
+        "pcf_kernel_times": (I, [P, P, P, I]),
+        "pcf_launches_per_step": (I, [P]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st):
+    if st != 0:
+        raise PCFError(f"pcfadj: {_lib.pcf_status_str(st).decode()} (status {st})")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def state_shape(nx, ny, nz, batch=1):
+    Kx, Kz = nx // 3 - 1, nz // 3 - 1
+    return (batch, 3, 2 * Kx + 1, Kz + 1, ny)
+
+
+def psi_len(nx, ny, nz):
+    return int(load_library().pcf_psi_len(nx, ny, nz))
+
+
+def probe_fp64_peak():
+    """Measured FP64 FMA throughput of the current GPU in GFLOP/s."""
+    lib = load_library()
+    g = ctypes.c_double()
+    _check(lib.pcf_probe_fp64_peak(_stream(), ctypes.byref(g)))
+    return g.value
+
+
+class Solver:
+    """One grid, ``batch`` instances; all tensors are complex128 on the current CUDA device,
+    shaped [batch, 3, Mx, Mz, ny] (see include/pcfadj.h for the layout)."""
+
+    KERNEL_CLASSES = ["ysynth", "xzsynth_u", "prod_M", "mode_phi", "xzsynth_q", "prod_N", "mode_psi"]
+
+    def __init__(self, nx, ny, nz, batch=1, Lx=LX_PAPER, Lz=LZ_PAPER, Re=400.0, dt=0.25, dtau_hat=0.25,
+                 precision=0, modes_per_block=0):
+        import torch
+        self.lib = load_library()
+        self.shape = state_shape(nx, ny, nz, batch)
+        self.nx, self.ny, self.nz, self.batch = nx, ny, nz, batch
+        self.dt, self.dtau_hat = dt, dtau_hat
+        p = _Params(nx, ny, nz, batch, Lx, Lz, Re, dt, dtau_hat, precision, modes_per_block, (ctypes.c_int * 2)(0, 0))
+        h = ctypes.c_void_p()
+        _check(self.lib.pcf_create(ctypes.byref(p), _stream(), ctypes.byref(h)))
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.pcf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, t):
+        import torch
+        if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != self.shape:
+            raise PCFError(f"expected contiguous complex128 CUDA tensor of shape {self.shape}, got "
+                           f"{t.dtype} {tuple(t.shape)} on {t.device}")
+        return t
+
+    def empty(self):
+        import torch
+        return torch.empty(self.shape, dtype=torch.complex128, device=self.device)
+
+    def residual(self, u, r=None, with_norm=True):
+        """Steps 1-2 of §4: returns (r1, J) with J a float64 tensor of length batch."""
+        import torch
+        self._chk(u)
+        r = self.empty() if r is None else self._chk(r)
+        J = torch.empty(self.batch, dtype=torch.float64, device=self.device) if with_norm else None
+        _check(self.lib.pcf_residual(self._h, _ptr(u), _ptr(r), _ptr(J)))
+        return r, J
+
+    def adjoint_gradient(self, u, r, f=None):
+        """Steps 3-4 of §4: the descent direction f."""
+        self._chk(u)
+        self._chk(r)
+        f = self.empty() if f is None else self._chk(f)
+        _check(self.lib.pcf_adjoint_gradient(self._h, _ptr(u), _ptr(r), _ptr(f)))
+        return f
+
+    def influence_matrix_solve(self, rhs, step, out=None):
+        """One influence-matrix Stokes step: (1/step - nu Lap) out + grad p = rhs."""
+        self._chk(rhs)
+        out = self.empty() if out is None else self._chk(out)
+        _check(self.lib.pcf_influence_matrix_solve(self._h, _ptr(rhs), _ptr(out), float(step)))
+        return out
+
+    def descent_step(self, u, dtau, nsteps=1, hist=True):
+        """nsteps descent steps in place on u; returns the J history [nsteps, batch] (or None)."""
+        import torch
+        self._chk(u)
+        H = torch.empty((nsteps, self.batch), dtype=torch.float64, device=self.device) if hist else None
+        _check(self.lib.pcf_descent_step(self._h, _ptr(u), float(dtau), int(nsteps), _ptr(H)))
+        return H
+
+    def descent_step_host(self, u_host, dtau, nsteps=1, hist_host=None):
+        """Same as descent_step with host (CPU, ideally pinned) complex128 tensors; synchronises."""
+        _check(self.lib.pcf_descent_step_host(self._h, _ptr(u_host), float(dtau), int(nsteps),
+                                              _ptr(hist_host)))
+
+    def set_kernel_timing(self, enable):
+        _check(self.lib.pcf_set_kernel_timing(self._h, 1 if enable else 0))
+
+    def kernel_times(self):
+        n = len(self.KERNEL_CLASSES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        _check(self.lib.pcf_kernel_times(self._h, ms, cnt, n))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(self.KERNEL_CLASSES)}
+
+    def launches_per_step(self):
+        return int(self.lib.pcf_launches_per_step(self._h))

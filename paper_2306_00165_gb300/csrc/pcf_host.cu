@@ -1,0 +1,700 @@
+// Host side of the pcfadj library: per-grid tables, context, launch sequences, C ABI.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "pcf_kernels.cuh"
+
+using namespace pcf;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+thread_local char g_last_error[256] = "";
+
+#define PCF_CUDA(call)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      snprintf(g_last_error, sizeof(g_last_error), "%s: %s", #call, cudaGetErrorString(e_)); \
+      return PCF_ECUDA;                                                                    \
+    }                                                                                      \
+  } while (0)
+
+bool grid_ok(int nx, int ny, int nz) {
+  auto ok_fft = [](int n) {
+    if (n < 16 || n > 128 || (n % 2)) return false;
+    int m = n;
+    while (m % 2 == 0) m /= 2;
+    while (m % 3 == 0) m /= 3;
+    return m == 1;
+  };
+  return ok_fft(nx) && ok_fft(nz) && ny >= 9 && ny <= 129 && (ny % 2 == 1);
+}
+
+void radix_plan(int L, int* r, int* nr) {
+  int n = 0;
+  while (L % 4 == 0) { r[n++] = 4; L /= 4; }
+  while (L % 2 == 0) { r[n++] = 2; L /= 2; }
+  while (L % 3 == 0) { r[n++] = 3; L /= 3; }
+  *nr = n;
+}
+
+// cos(pi a / N) with the argument reduced exactly in integers
+double cospi_frac(long long a, int N) {
+  long long m = a % (2LL * N);
+  if (m < 0) m += 2LL * N;
+  return std::cos(kPi * (double)m / (double)N);
+}
+
+// T'_n(cos(pi j/N))
+double cheb_dvalue(int n, int j, int N) {
+  if (j == 0) return (double)n * n;
+  if (j == N) return ((n + 1) % 2 ? -1.0 : 1.0) * (double)n * n;
+  const double th = kPi * (double)j / (double)N;
+  long long m = ((long long)n * j) % (2LL * N);
+  return (double)n * std::sin(kPi * (double)m / (double)N) / std::sin(th);
+}
+
+// Cinv_{n j}: coefficient n of the interpolant of the values at y_j (DCT-I inverse).
+double cinv(int n, int j, int N) {
+  const double cn = (n == 0 || n == N) ? 2.0 : 1.0;
+  const double cj = (j == 0 || j == N) ? 2.0 : 1.0;
+  return 2.0 / ((double)N * cn * cj) * cospi_frac((long long)n * j, N);
+}
+
+std::vector<double> make_cheb(int N) {
+  const ChebLayout CL(N);
+  const int H = CL.H;
+  std::vector<double> t(CL.total(), 0.0);
+  for (int j = 0; j < H; ++j)
+    for (int k = 0; k < H; ++k) {
+      t[CL.Ce() + j * H + k] = cospi_frac((long long)j * (2 * k), N);
+      t[CL.De() + j * H + k] = cheb_dvalue(2 * k, j, N);
+      if (k < H - 1) {
+        t[CL.Co() + j * H + k] = cospi_frac((long long)j * (2 * k + 1), N);
+        t[CL.Do() + j * H + k] = cheb_dvalue(2 * k + 1, j, N);
+      }
+    }
+  for (int k = 0; k < H; ++k)
+    for (int j = 0; j < H; ++j) {
+      t[CL.Ae() + k * H + j] = cinv(2 * k, j, N);
+      if (k < H - 1) t[CL.Ao() + k * H + j] = cinv(2 * k + 1, j, N);
+    }
+  return t;
+}
+
+std::vector<double> make_rco(int N) {
+  const RcoLayout RL(N);
+  const int Mh = N / 2 + 1;
+  std::vector<double> t(RL.total(), 0.0);
+  for (int par = 0; par < 2; ++par) {
+    const int Mc = (N - par) / 2 + 1;
+    for (int i = 0; i < Mc; ++i) {
+      const int n = par + 2 * i;
+      const double dn = n;
+      if (i >= 1) {
+        const double cm2 = (n - 2 == 0) ? 2.0 : 1.0;
+        t[RL.off(par, 0) + i] = -cm2 / (4.0 * dn * (dn - 1.0));
+        t[RL.off(par, 1) + i] = (n <= N - 2) ? 1.0 / (2.0 * (dn * dn - 1.0)) : 0.0;
+        t[RL.off(par, 2) + i] = (n + 2 <= N - 2) ? -1.0 / (4.0 * dn * (dn + 1.0)) : 0.0;
+      }
+      t[RL.off(par, 3) + i] = dn * dn;
+      t[RL.off(par, 4) + i] = 2.0 * dn;
+    }
+    (void)Mh;
+  }
+  return t;
+}
+
+// Sweep coefficients of the quasi-tridiagonal tau system (lambda, par), see tau_solve.
+void solver_coefs(int N, int par, double lam, const std::vector<double>& rco, double* dst) {
+  const RcoLayout RL(N);
+  const int Mh = N / 2 + 1;
+  const int Mc = (N - par) / 2 + 1;
+  double* c = dst;
+  double* inv = dst + Mh;
+  double* beta = dst + 2 * Mh;
+  double* B = dst + 3 * Mh;
+  for (int i = 0; i < 4 * Mh + 2; ++i) dst[i] = 0.0;
+  const double* ra = rco.data() + RL.off(par, 0);
+  const double* rb = rco.data() + RL.off(par, 1);
+  const double* rc = rco.data() + RL.off(par, 2);
+  double bnext = 0.0;
+  for (int i = Mc - 1; i >= 1; --i) {
+    const double a = lam * ra[i], bb = 1.0 + lam * rb[i], cc = lam * rc[i];
+    const double den = bb + cc * bnext;
+    c[i] = cc;
+    inv[i] = 1.0 / den;
+    beta[i] = -a / den;
+    bnext = beta[i];
+  }
+  B[0] = 1.0;
+  double sum = 1.0;
+  for (int i = 1; i < Mc; ++i) {
+    B[i] = beta[i] * B[i - 1];
+    sum += B[i];
+  }
+  dst[4 * Mh] = 1.0 / sum;
+}
+
+// Homogeneous responses and 2x2 influence matrix of group g (see mode_chain).
+void group_tables(int N, int g, double k2, double sigma, const double* tab, const std::vector<double>& rco,
+                  double* dst) {
+  const TabLayout TL(N);
+  const RcoLayout RL(N);
+  const int Mh = N / 2 + 1;
+  const int pv = g, pP = 1 - g;
+  const int McP = (N - pP) / 2 + 1, McV = (N - pv) / 2 + 1;
+  const double lamH = sigma + k2;
+  std::vector<double> P(Mh), T(Mh), V(Mh), R(Mh), unit(Mh);
+  double F1[2], F2[2];
+  std::vector<double> vh[2];
+  for (int h = 0; h < 2; ++h) {
+    std::fill(R.begin(), R.end(), 0.0);
+    double bc = 0.0;
+    if (h == 0) {
+      bc = 1.0;  // Dirichlet value of the pressure class
+    } else {
+      std::fill(unit.begin(), unit.end(), 0.0);
+      unit[McV - 1] = 1.0;  // T_N (g = 0) or T_{N-1} (g = 1)
+      class_deriv(N, pv, unit.data(), rco.data() + RL.off(pv, 4), T.data());
+      for (int i = 0; i < McP; ++i) R[i] = -T[i];
+    }
+    const double* s = tab + TL.solver(0, pP);
+    tau_solve(McP, s, s + Mh, s + 2 * Mh, s + 3 * Mh, s[4 * Mh], rco.data() + RL.off(pP, 0),
+              rco.data() + RL.off(pP, 1), rco.data() + RL.off(pP, 2), R.data(), bc, P.data());
+    class_deriv(N, pP, P.data(), rco.data() + RL.off(pP, 4), T.data());
+    for (int i = 0; i < McV; ++i) R[i] = -T[i];
+    s = tab + TL.solver(1, pv);
+    tau_solve(McV, s, s + Mh, s + 2 * Mh, s + 3 * Mh, s[4 * Mh], rco.data() + RL.off(pv, 0),
+              rco.data() + RL.off(pv, 1), rco.data() + RL.off(pv, 2), R.data(), 0.0, V.data());
+    double f1 = 0.0;
+    for (int i = 0; i < McV; ++i) f1 += rco[RL.off(pv, 3) + i] * V[i];
+    double f2 = lamH * V[McV - 1];
+    if (g == 1) f2 += 2.0 * N * P[McP - 1];
+    if (h == 1) f2 -= 1.0;
+    F1[h] = f1;
+    F2[h] = f2;
+    vh[h] = V;
+  }
+  for (int i = 0; i < 2 * Mh + 4; ++i) dst[i] = 0.0;
+  for (int i = 0; i < McV; ++i) {
+    dst[i] = vh[0][i];
+    dst[Mh + i] = vh[1][i];
+  }
+  const double det = F1[0] * F2[1] - F1[1] * F2[0];
+  dst[2 * Mh + 0] = F2[1] / det;
+  dst[2 * Mh + 1] = -F1[1] / det;
+  dst[2 * Mh + 2] = -F2[0] / det;
+  dst[2 * Mh + 3] = F1[0] / det;
+}
+
+std::vector<double> make_mode_tables(int N, const std::vector<double>& kx, const std::vector<double>& kz,
+                                     double sigma, const std::vector<double>& rco) {
+  const TabLayout TL(N);
+  const int Mx = (int)kx.size(), Mz = (int)kz.size();
+  const int PM = TL.per_mode();
+  std::vector<double> t((size_t)Mx * Mz * PM, 0.0);
+  for (int i = 0; i < Mx; ++i)
+    for (int p = 0; p < Mz; ++p) {
+      double* d = t.data() + ((size_t)i * Mz + p) * PM;
+      const double k2 = kx[i] * kx[i] + kz[p] * kz[p];
+      for (int par = 0; par < 2; ++par) {
+        solver_coefs(N, par, k2, rco, d + TL.solver(0, par));
+        solver_coefs(N, par, sigma + k2, rco, d + TL.solver(1, par));
+      }
+      if (k2 > 0.0)
+        for (int g = 0; g < 2; ++g) group_tables(N, g, k2, sigma, d, rco, d + TL.group(g));
+    }
+  return t;
+}
+
+// Interpolatory (Clenshaw-Curtis) weights: w_j = sum_n Cinv_{n j} int_{-1}^{1} T_n dy.
+std::vector<double> make_ccw(int N) {
+  std::vector<double> w(N + 1, 0.0);
+  for (int j = 0; j <= N; ++j) {
+    double s = 0.0;
+    for (int n = 0; n <= N; n += 2) s += cinv(n, j, N) * (2.0 / (1.0 - (double)n * n));
+    w[j] = s;
+  }
+  return w;
+}
+
+std::vector<double2> make_twiddles(int L) {
+  std::vector<double2> w(L);
+  for (int k = 0; k < L; ++k) {
+    const double a = -2.0 * kPi * (double)k / (double)L;
+    w[k] = make_double2(std::cos(a), std::sin(a));
+  }
+  return w;
+}
+
+template <class T>
+cudaError_t upload(const std::vector<T>& h, T** d) {
+  cudaError_t e = cudaMalloc((void**)d, h.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+struct pcf_ctx {
+  pcf_params prm;
+  int N, Kx, Kz, Mx, Mz, nm, B, mpc;
+  long long state_len;  // complex values per instance
+  cudaStream_t user = nullptr, cs = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<void*> allocs;
+  std::vector<Inst> hinst;
+  Inst* dinst = nullptr;
+  // prefix arrays
+  int* pre_synth11 = nullptr;
+  int* pre_synth3 = nullptr;
+  int* pre_prod = nullptr;
+  int* pre_mode = nullptr;
+  int* pre_inst = nullptr;
+  int cta_synth11 = 0, cta_synth3 = 0, cta_prod = 0, cta_mode = 0;
+  size_t sm_synth = 0, sm_prod = 0, sm_mode = 0;
+  double2* r_int = nullptr;    // internal r1 buffer for descent
+  double2* u_dev = nullptr;    // device state for the *_host entry point
+  double* hist_dev = nullptr;
+  int hist_cap = 0;
+  int* active = nullptr;
+  std::map<int, cudaGraphExec_t> graphs;
+  // timing
+  int timing = 0;
+  double kms[kNumKernelClasses] = {0};
+  long long kcount[kNumKernelClasses] = {0};
+  std::vector<cudaEvent_t> evpool;
+};
+
+namespace {
+
+template <class T>
+cudaError_t ctx_alloc(pcf_ctx* c, T** p, size_t n) {
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e == cudaSuccess) c->allocs.push_back((void*)*p);
+  return e;
+}
+
+pcf_status push_descriptors(pcf_ctx* c) {
+  PCF_CUDA(cudaMemcpyAsync(c->dinst, c->hinst.data(), sizeof(Inst) * c->hinst.size(), cudaMemcpyHostToDevice, c->cs));
+  return PCF_OK;
+}
+
+LaunchInfo li_of(pcf_ctx* c, const int* pre) { return LaunchInfo{c->dinst, pre, c->B}; }
+
+// kernel launch with optional per-class event timing
+template <class F>
+pcf_status timed(pcf_ctx* c, int cls, F&& launch) {
+  if (!c->timing) {
+    launch();
+    return PCF_OK;
+  }
+  cudaEvent_t a, b;
+  PCF_CUDA(cudaEventCreate(&a));
+  PCF_CUDA(cudaEventCreate(&b));
+  PCF_CUDA(cudaEventRecord(a, c->cs));
+  launch();
+  PCF_CUDA(cudaEventRecord(b, c->cs));
+  PCF_CUDA(cudaEventSynchronize(b));
+  float ms = 0.f;
+  PCF_CUDA(cudaEventElapsedTime(&ms, a, b));
+  c->kms[cls] += ms;
+  c->kcount[cls] += 1;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return PCF_OK;
+}
+
+pcf_status launch_mode(pcf_ctx* c, int op, int sig, int step_index) {
+  return timed(c, op == MODE_PHI ? 3 : (op == MODE_SYNTH_ONLY ? 0 : 6), [&] {
+    k_mode<<<c->cta_mode, 128, c->sm_mode, c->cs>>>(li_of(c, c->pre_mode), op, sig, c->mpc, step_index);
+  });
+}
+pcf_status launch_synth(pcf_ctx* c, int slot, int nf) {
+  const int* pre = nf == kFieldsSynth ? c->pre_synth11 : c->pre_synth3;
+  const int ctas = nf == kFieldsSynth ? c->cta_synth11 : c->cta_synth3;
+  return timed(c, slot == 0 ? 1 : 4,
+               [&] { k_xzsynth<<<ctas, 128, c->sm_synth, c->cs>>>(li_of(c, pre), slot, nf); });
+}
+pcf_status launch_prodM(pcf_ctx* c) {
+  return timed(c, 2, [&] { k_prod_M<<<c->cta_prod, 128, c->sm_prod, c->cs>>>(li_of(c, c->pre_prod)); });
+}
+pcf_status launch_prodN(pcf_ctx* c) {
+  return timed(c, 5, [&] { k_prod_N<<<c->cta_prod, 128, c->sm_prod, c->cs>>>(li_of(c, c->pre_prod)); });
+}
+
+pcf_status check_launch() {
+  PCF_CUDA(cudaGetLastError());
+  return PCF_OK;
+}
+
+#define PCF_TRY(x)              \
+  do {                          \
+    pcf_status s_ = (x);        \
+    if (s_ != PCF_OK) return s_; \
+  } while (0)
+
+pcf_status enter(pcf_ctx* c) {
+  PCF_CUDA(cudaEventRecord(c->ev_in, c->user));
+  PCF_CUDA(cudaStreamWaitEvent(c->cs, c->ev_in, 0));
+  return PCF_OK;
+}
+pcf_status leave(pcf_ctx* c) {
+  PCF_CUDA(cudaEventRecord(c->ev_out, c->cs));
+  PCF_CUDA(cudaStreamWaitEvent(c->user, c->ev_out, 0));
+  return PCF_OK;
+}
+
+void set_pointers(pcf_ctx* c, const double* u, const double* r, double* f) {
+  for (int b = 0; b < c->B; ++b) {
+    Inst& I = c->hinst[b];
+    I.uhat = u ? (double2*)u + (size_t)b * c->state_len : nullptr;
+    I.rhat = r ? (double2*)r + (size_t)b * c->state_len : nullptr;
+    I.fhat = f ? (double2*)f + (size_t)b * c->state_len : nullptr;
+    I.hist = nullptr;
+    I.active = nullptr;
+    I.tol = 0.0;
+  }
+}
+
+pcf_status step_body(pcf_ctx* c, int s) {
+  PCF_TRY(launch_synth(c, 0, kFieldsSynth));
+  PCF_TRY(launch_prodM(c));
+  PCF_TRY(launch_mode(c, MODE_PHI, 0, s));
+  PCF_TRY(launch_synth(c, 1, kFieldsSynth));
+  PCF_TRY(launch_prodN(c));
+  PCF_TRY(launch_mode(c, MODE_PSI_UPDATE, 1, s));
+  return PCF_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI
+extern "C" {
+
+int pcf_abi_version(void) { return PCF_ABI_VERSION; }
+
+const char* pcf_status_str(pcf_status s) {
+  switch (s) {
+    case PCF_OK: return "ok";
+    case PCF_EINVAL: return "invalid argument";
+    case PCF_ECUDA: return g_last_error[0] ? g_last_error : "CUDA error";
+    case PCF_ENOMEM: return "out of memory";
+    case PCF_ENAN: return "non-finite residual norm";
+    case PCF_ETIMEOUT: return "bounded device wait timed out";
+    case PCF_ENOTCONV: return "not converged";
+    case PCF_ENOTSUP: return "not supported by this build";
+  }
+  return "unknown status";
+}
+
+long long pcf_state_len(int nx, int ny, int nz) {
+  if (!grid_ok(nx, ny, nz)) return 0;
+  const int Kx = nx / 3 - 1, Kz = nz / 3 - 1;
+  return 3LL * (2 * Kx + 1) * (Kz + 1) * ny;
+}
+
+long long pcf_psi_len(int nx, int ny, int nz) {
+  if (nx < 6 || nz < 6 || ny < 5) return 0;
+  const int Kx = nx / 3 - 1, Kz = nz / 3 - 1;
+  const long long indep = ((long long)(2 * Kx + 1) * (2 * Kz + 1) - 1) / 2;
+  return indep * (2LL * (ny - 4) + 2LL * (ny - 2)) + 2LL * (ny - 2);
+}
+
+pcf_status pcf_create(const pcf_params* prm, void* stream, pcf_ctx** out) {
+  if (!prm || !out) return PCF_EINVAL;
+  if (!grid_ok(prm->nx, prm->ny, prm->nz) || prm->batch < 1 || !(prm->Re > 0) || !(prm->dt > 0) ||
+      !(prm->dtau_hat > 0) || !(prm->Lx > 0) || !(prm->Lz > 0))
+    return PCF_EINVAL;
+  if (prm->precision != PCF_FP64) return PCF_ENOTSUP;
+  pcf_ctx* c = new pcf_ctx();
+  c->prm = *prm;
+  c->N = prm->ny - 1;
+  c->Kx = prm->nx / 3 - 1;
+  c->Kz = prm->nz / 3 - 1;
+  c->Mx = 2 * c->Kx + 1;
+  c->Mz = c->Kz + 1;
+  c->nm = c->Mx * c->Mz;
+  c->B = prm->batch;
+  c->state_len = 3LL * c->nm * prm->ny;
+  c->user = (cudaStream_t)stream;
+  auto fail = [&](pcf_status s) {
+    pcf_destroy(c);
+    return s;
+  };
+  if (cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking) != cudaSuccess) return fail(PCF_ECUDA);
+  if (cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess) return fail(PCF_ECUDA);
+  if (cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) return fail(PCF_ECUDA);
+
+  const int N = c->N, nx = prm->nx, ny = prm->ny, nz = prm->nz;
+  const double nu = 1.0 / prm->Re;
+  std::vector<double> kx(c->Mx), kz(c->Mz), yg(ny);
+  for (int i = 0; i < c->Mx; ++i) {
+    const int m = i <= c->Kx ? i : i - c->Mx;
+    kx[i] = 2.0 * kPi * m / prm->Lx;
+  }
+  for (int p = 0; p < c->Mz; ++p) kz[p] = 2.0 * kPi * p / prm->Lz;
+  for (int j = 0; j < ny; ++j) yg[j] = cospi_frac(j, N);
+  const std::vector<double> cheb = make_cheb(N), rco = make_rco(N), ccw = make_ccw(N);
+  const double sig[2] = {1.0 / (nu * prm->dt), 1.0 / (nu * prm->dtau_hat)};
+  std::vector<double> tabs[2];
+  tabs[0] = make_mode_tables(N, kx, kz, sig[0], rco);
+  if (prm->dtau_hat == prm->dt) tabs[1] = tabs[0];
+  else tabs[1] = make_mode_tables(N, kx, kz, sig[1], rco);
+  const std::vector<double2> twx = make_twiddles(nx), twz = make_twiddles(nz);
+
+  double *d_cheb, *d_rco, *d_ccw, *d_kx, *d_kz, *d_y, *d_tab0, *d_tab1;
+  double2 *d_twx, *d_twz;
+  if (upload(cheb, &d_cheb) || upload(rco, &d_rco) || upload(ccw, &d_ccw) || upload(kx, &d_kx) ||
+      upload(kz, &d_kz) || upload(yg, &d_y) || upload(twx, &d_twx) || upload(twz, &d_twz) ||
+      upload(tabs[0], &d_tab0))
+    return fail(PCF_ECUDA);
+  for (void* p : {(void*)d_cheb, (void*)d_rco, (void*)d_ccw, (void*)d_kx, (void*)d_kz, (void*)d_y, (void*)d_twx,
+                  (void*)d_twz, (void*)d_tab0})
+    c->allocs.push_back(p);
+  if (prm->dtau_hat == prm->dt) {
+    d_tab1 = d_tab0;
+  } else {
+    if (upload(tabs[1], &d_tab1)) return fail(PCF_ECUDA);
+    c->allocs.push_back(d_tab1);
+  }
+
+  // per-instance workspace
+  const int B = c->B;
+  const size_t yv_n = 2ULL * kFieldsY * ny * c->nm, ph_n = 2ULL * kFieldsSynth * ny * nx * nz;
+  const size_t xz_n = 3ULL * ny * c->nm, np_n = 3ULL * ny;
+  double2 *yv, *xz;
+  double *ph, *np;
+  if (ctx_alloc(c, &yv, yv_n * B) || ctx_alloc(c, &ph, ph_n * B) || ctx_alloc(c, &xz, xz_n * B) ||
+      ctx_alloc(c, &np, np_n * B) || ctx_alloc(c, &c->r_int, (size_t)c->state_len * B) ||
+      ctx_alloc(c, &c->active, (size_t)B))
+    return fail(PCF_ENOMEM);
+  c->hinst.resize(B);
+  for (int b = 0; b < B; ++b) {
+    Inst& I = c->hinst[b];
+    memset(&I, 0, sizeof(I));
+    I.nx = nx; I.ny = ny; I.nz = nz; I.N = N; I.Kx = c->Kx; I.Kz = c->Kz; I.Mx = c->Mx; I.Mz = c->Mz;
+    I.nmodes = c->nm;
+    radix_plan(nx, I.rx, &I.nrx);
+    radix_plan(nz, I.rz, &I.nrz);
+    I.nu = nu; I.dt = prm->dt; I.dtau_hat = prm->dtau_hat; I.dtau = 0.0;
+    I.inv_nxnz = 1.0 / ((double)nx * nz);
+    I.cheb = d_cheb; I.rco = d_rco; I.ygrid = d_y; I.ccw = d_ccw; I.kx = d_kx; I.kz = d_kz;
+    I.twx = d_twx; I.twz = d_twz;
+    I.tab[0] = d_tab0; I.tab[1] = d_tab1;
+    I.sigma[0] = sig[0]; I.sigma[1] = sig[1];
+    I.yv = yv + yv_n * b; I.phys = ph + ph_n * b; I.xz = xz + xz_n * b; I.normpart = np + np_n * b;
+    I.hist_stride = B;
+  }
+  if (ctx_alloc(c, &c->dinst, (size_t)B)) return fail(PCF_ENOMEM);
+  // modes per CTA: keep the shared memory of the mode kernel near 100 KB
+  int mpc = prm->modes_per_block > 0 ? prm->modes_per_block : 4;
+  while (mpc > 1 && smem_mode(c->hinst[0], mpc) > 110 * 1024) --mpc;
+  if (smem_mode(c->hinst[0], mpc) > 227 * 1024) return fail(PCF_ENOTSUP);
+  c->mpc = mpc;
+  c->sm_mode = smem_mode(c->hinst[0], mpc);
+  c->sm_synth = smem_xzsynth(c->hinst[0]);
+  c->sm_prod = smem_prod(c->hinst[0]);
+  // CTA prefix arrays (uniform batch)
+  auto prefix = [&](int per, int** dst, int* total) -> bool {
+    std::vector<int> pre(B + 1);
+    for (int b = 0; b <= B; ++b) pre[b] = b * per;
+    *total = B * per;
+    if (upload(pre, dst) != cudaSuccess) return false;
+    c->allocs.push_back(*dst);
+    return true;
+  };
+  int dummy;
+  if (!prefix(kFieldsSynth * ny, &c->pre_synth11, &c->cta_synth11) || !prefix(3 * ny, &c->pre_synth3, &c->cta_synth3) ||
+      !prefix(3 * ny, &c->pre_prod, &c->cta_prod) || !prefix((c->nm + mpc - 1) / mpc, &c->pre_mode, &c->cta_mode) ||
+      !prefix(1, &c->pre_inst, &dummy))
+    return fail(PCF_ECUDA);
+  if (cudaFuncSetAttribute(k_mode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->sm_mode) ||
+      cudaFuncSetAttribute(k_xzsynth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->sm_synth) ||
+      cudaFuncSetAttribute(k_prod_M, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->sm_prod) ||
+      cudaFuncSetAttribute(k_prod_N, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->sm_prod))
+    return fail(PCF_ECUDA);
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(PCF_ECUDA);
+  *out = c;
+  return PCF_OK;
+}
+
+void pcf_destroy(pcf_ctx* c) {
+  if (!c) return;
+  if (c->cs) cudaStreamSynchronize(c->cs);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->u_dev) cudaFree(c->u_dev);
+  if (c->hist_dev) cudaFree(c->hist_dev);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->cs) cudaStreamDestroy(c->cs);
+  delete c;
+}
+
+pcf_status pcf_residual(pcf_ctx* c, const double* u, double* r, double* rnorm) {
+  if (!c || !u || !r) return PCF_EINVAL;
+  set_pointers(c, u, r, nullptr);
+  PCF_TRY(enter(c));
+  PCF_TRY(push_descriptors(c));
+  PCF_TRY(launch_mode(c, MODE_SYNTH_ONLY, 0, 0));
+  PCF_TRY(launch_synth(c, 0, kFieldsSynth));
+  PCF_TRY(launch_prodM(c));
+  PCF_TRY(launch_mode(c, MODE_PHI, 0, 0));
+  if (rnorm) {
+    PCF_TRY(launch_synth(c, 1, 3));
+    k_norm_planes<<<c->cta_synth3, 128, 0, c->cs>>>(li_of(c, c->pre_synth3));
+    k_norm_final<<<1, 32, 0, c->cs>>>(li_of(c, c->pre_inst), rnorm);
+  }
+  PCF_TRY(check_launch());
+  return leave(c);
+}
+
+pcf_status pcf_adjoint_gradient(pcf_ctx* c, const double* u, const double* r, double* f) {
+  if (!c || !u || !r || !f) return PCF_EINVAL;
+  set_pointers(c, u, r, f);
+  PCF_TRY(enter(c));
+  PCF_TRY(push_descriptors(c));
+  PCF_TRY(launch_mode(c, MODE_SYNTH_ONLY, 0, 0));
+  PCF_TRY(launch_mode(c, MODE_SYNTH_ONLY, 1, 0));
+  PCF_TRY(launch_synth(c, 0, kFieldsSynth));
+  PCF_TRY(launch_synth(c, 1, kFieldsSynth));
+  PCF_TRY(launch_prodN(c));
+  PCF_TRY(launch_mode(c, MODE_PSI_GRAD, 1, 0));
+  PCF_TRY(check_launch());
+  return leave(c);
+}
+
+pcf_status pcf_influence_matrix_solve(pcf_ctx* c, const double* rhs, double* out, double step) {
+  if (!c || !rhs || !out) return PCF_EINVAL;
+  int sig;
+  if (step == c->prm.dt) sig = 0;
+  else if (step == c->prm.dtau_hat) sig = 1;
+  else return PCF_EINVAL;
+  set_pointers(c, nullptr, rhs, out);
+  PCF_TRY(enter(c));
+  PCF_TRY(push_descriptors(c));
+  PCF_TRY(launch_mode(c, MODE_SOLVE, sig, 0));
+  PCF_TRY(check_launch());
+  return leave(c);
+}
+
+pcf_status pcf_descent_step(pcf_ctx* c, double* u, double dtau, int nsteps, double* hist) {
+  if (!c || !u || nsteps < 0 || !(dtau >= 0)) return PCF_EINVAL;
+  if (nsteps == 0) return PCF_OK;
+  set_pointers(c, u, (const double*)c->r_int, nullptr);
+  for (int b = 0; b < c->B; ++b) {
+    c->hinst[b].dtau = dtau;
+    c->hinst[b].hist = hist ? hist + b : nullptr;
+  }
+  PCF_TRY(enter(c));
+  PCF_TRY(push_descriptors(c));
+  if (c->timing) {
+    PCF_TRY(launch_mode(c, MODE_SYNTH_ONLY, 0, 0));
+    for (int s = 0; s < nsteps; ++s) PCF_TRY(step_body(c, s));
+    PCF_TRY(check_launch());
+    return leave(c);
+  }
+  auto it = c->graphs.find(nsteps);
+  if (it == c->graphs.end()) {
+    cudaGraph_t g;
+    PCF_CUDA(cudaStreamBeginCapture(c->cs, cudaStreamCaptureModeThreadLocal));
+    pcf_status st = launch_mode(c, MODE_SYNTH_ONLY, 0, 0);
+    for (int s = 0; s < nsteps && st == PCF_OK; ++s) st = step_body(c, s);
+    cudaError_t e = cudaStreamEndCapture(c->cs, &g);
+    if (st != PCF_OK) return st;
+    PCF_CUDA(e);
+    cudaGraphExec_t ex;
+    PCF_CUDA(cudaGraphInstantiate(&ex, g, 0));
+    cudaGraphDestroy(g);
+    it = c->graphs.emplace(nsteps, ex).first;
+  }
+  PCF_CUDA(cudaGraphLaunch(it->second, c->cs));
+  return leave(c);
+}
+
+pcf_status pcf_descent_step_host(pcf_ctx* c, double* u_host, double dtau, int nsteps, double* hist_host) {
+  if (!c || !u_host || nsteps < 0) return PCF_EINVAL;
+  const size_t bytes = sizeof(double2) * (size_t)c->state_len * c->B;
+  if (!c->u_dev) PCF_CUDA(cudaMalloc(&c->u_dev, bytes));
+  if (hist_host && c->hist_cap < nsteps) {
+    if (c->hist_dev) cudaFree(c->hist_dev);
+    c->hist_dev = nullptr;
+    PCF_CUDA(cudaMalloc(&c->hist_dev, sizeof(double) * (size_t)nsteps * c->B));
+    c->hist_cap = nsteps;
+  }
+  PCF_CUDA(cudaMemcpyAsync(c->u_dev, u_host, bytes, cudaMemcpyHostToDevice, c->user));
+  PCF_TRY(pcf_descent_step(c, (double*)c->u_dev, dtau, nsteps, hist_host ? c->hist_dev : nullptr));
+  PCF_CUDA(cudaMemcpyAsync(u_host, c->u_dev, bytes, cudaMemcpyDeviceToHost, c->user));
+  if (hist_host)
+    PCF_CUDA(cudaMemcpyAsync(hist_host, c->hist_dev, sizeof(double) * (size_t)nsteps * c->B,
+                             cudaMemcpyDeviceToHost, c->user));
+  PCF_CUDA(cudaStreamSynchronize(c->user));
+  return PCF_OK;
+}
+
+pcf_status pcf_set_kernel_timing(pcf_ctx* c, int enable) {
+  if (!c) return PCF_EINVAL;
+  c->timing = enable ? 1 : 0;
+  for (int i = 0; i < kNumKernelClasses; ++i) {
+    c->kms[i] = 0.0;
+    c->kcount[i] = 0;
+  }
+  return PCF_OK;
+}
+
+pcf_status pcf_kernel_times(pcf_ctx* c, double* ms, long long* launches, int n) {
+  if (!c || n < 0) return PCF_EINVAL;
+  for (int i = 0; i < n && i < kNumKernelClasses; ++i) {
+    if (ms) ms[i] = c->kms[i];
+    if (launches) launches[i] = c->kcount[i];
+  }
+  return PCF_OK;
+}
+
+int pcf_launches_per_step(pcf_ctx* c) { return c ? 6 : 0; }
+
+pcf_status pcf_probe_fp64_peak(void* stream, double* gflops) {
+  if (!gflops) return PCF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, nsm = 0;
+  PCF_CUDA(cudaGetDevice(&dev));
+  PCF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  double* d;
+  PCF_CUDA(cudaMalloc(&d, sizeof(double) * 4096));
+  const int blocks = nsm * 8, threads = 256, iters = 4096;
+  k_fp64_probe<<<blocks, threads, 0, s>>>(d, iters);  // warm-up
+  cudaEvent_t a, b;
+  PCF_CUDA(cudaEventCreate(&a));
+  PCF_CUDA(cudaEventCreate(&b));
+  float best = 1e30f;
+  for (int rep = 0; rep < 5; ++rep) {
+    PCF_CUDA(cudaEventRecord(a, s));
+    k_fp64_probe<<<blocks, threads, 0, s>>>(d, iters);
+    PCF_CUDA(cudaEventRecord(b, s));
+    PCF_CUDA(cudaEventSynchronize(b));
+    float ms;
+    PCF_CUDA(cudaEventElapsedTime(&ms, a, b));
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(d);
+  const double flops = 2.0 * 8.0 * (double)iters * blocks * threads;
+  *gflops = flops / (best * 1e-3) / 1e9;
+  return PCF_OK;
+}
+
+pcf_status pcf_snapshot(pcf_ctx*, const double*, double*) { return PCF_ENOTSUP; }
+pcf_status pcf_from_snapshot(pcf_ctx*, const double*, double*) { return PCF_ENOTSUP; }
+pcf_status pcf_dmd_extrapolate(pcf_ctx*, const double*, int, double, double*, int*, double*) { return PCF_ENOTSUP; }
+
+}  // extern "C"
