@@ -149,6 +149,25 @@ pcf_status pcf_from_snapshot(pcf_ctx* ctx, const double* psi, double* u_hat);
 pcf_status pcf_dmd_extrapolate(pcf_ctx* ctx, const double* snapshots, int M, double rank_tol,
                                double* u_out_hat, int* rank_used, double* j_out);
 
+/* The Stokes solve of pcf_influence_matrix_solve for callers that cannot allocate device
+ * memory (the paper has no counterpart; this is a library service).  Such callers - an
+ * application whose device memory belongs to a fixed pool or a foreign allocator, or a
+ * plugin that must not grow its device footprint after start-up - cannot use
+ * pcf_create, which allocates tables and workspace with cudaMalloc.  This entry point
+ * needs no context and allocates nothing: everything beyond rhs_hat and out_hat (the
+ * per-mode tau sweep coefficients, homogeneous responses and 2x2 influence-matrix
+ * inverses, the instance descriptor) lives in one static device array of 5 MiB that the
+ * library holds on every GPU it is loaded on, rebuilt on the device at every call.
+ * params: grid and Re, Lx, Lz (dt, dtau_hat, precision ignored; batch must be 1);
+ * limit: nx, nz <= 64 (at most 861 retained modes) and ny <= 65, else PCF_EINVAL before
+ * any launch.  step: the implicit step (any positive value).  rhs_hat, out_hat: device,
+ * uhat layout, one instance.  stream: cudaStream_t (NULL = default stream); asynchronous.
+ * The first call on a device (with that device current) looks up the array's address;
+ * make it before any stream capture.  All calls share the array: calls that overlap on the
+ * GPU race and must be ordered on one stream. */
+pcf_status pcf_influence_matrix_solve_noalloc(const pcf_params* params, const double* rhs_hat, double* out_hat,
+                                              double step, void* stream);
+
 /* Measures the FP64 FMA throughput of the current device with a dependent-chain-free
  * DFMA loop (used for the ALU roofline).  gflops: host output.  Synchronises. */
 pcf_status pcf_probe_fp64_peak(void* stream, double* gflops);

@@ -55,6 +55,7 @@ def load_library(path=None):
         "pcf_residual": (I, [P, P, P, P]),
         "pcf_adjoint_gradient": (I, [P, P, P, P]),
         "pcf_influence_matrix_solve": (I, [P, P, P, D]),
+        "pcf_influence_matrix_solve_noalloc": (I, [ctypes.POINTER(_Params), P, P, D, P]),
         "pcf_descent_step": (I, [P, P, D, I, P]),
         "pcf_descent_step_host": (I, [P, P, D, I, P]),
         "pcf_snapshot": (I, [P, P, P]),

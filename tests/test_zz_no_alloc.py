@@ -1,0 +1,62 @@
+"""The allocation-free Stokes solve (pcf_influence_matrix_solve_noalloc) against the
+context-based one (pcf_influence_matrix_solve), through the C ABI.
+
+For callers that cannot allocate device memory; it keeps its tables in a static device
+array shared by all calls, so two calls in a row on different grids must each match the
+context path.  This file is collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+def _rhs(o, seed):
+    rng = np.random.default_rng(seed)
+    shp = (3, o.Mx, o.Mz, o.N + 1)
+    F = (rng.standard_normal(shp) + 1j * rng.standard_normal(shp)) * np.exp(-0.2 * np.arange(o.N + 1))
+    F[:, o.Mx - 1:o.Kx:-1, 0] = np.conj(F[:, 1:o.Kx + 1, 0])
+    F[:, 0, 0] = F[:, 0, 0].real
+    return F
+
+
+def _params(pcf, grid, batch=1, step=0.25):
+    return pcf._Params(*grid, batch, pcf.LX_PAPER, pcf.LZ_PAPER, 400.0, step, step, 0, 0, (ctypes.c_int * 2)(0, 0))
+
+
+def test_noalloc_matches_context_solve_two_calls():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2306_00165_gb300 as pcf
+    from oracle import PCFOracle
+    lib = pcf.load_library()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for call, (grid, step, seed) in enumerate([((32, 33, 32), 0.25, 1), ((16, 17, 16), 0.1, 2)]):
+        o = PCFOracle(*grid)
+        F = torch.from_numpy(_rhs(o, seed)[None]).cuda()
+        ref = pcf.Solver(*grid, batch=1, dt=step, dtau_hat=step).influence_matrix_solve(F, step)
+        out = torch.full_like(F, float("nan"))
+        p = _params(pcf, grid, 1, step)
+        st = lib.pcf_influence_matrix_solve_noalloc(ctypes.byref(p), ctypes.c_void_p(F.data_ptr()),
+                                                    ctypes.c_void_p(out.data_ptr()), step, stream)
+        assert st == 0, f"call {call}: status {st}"
+        torch.cuda.synchronize()
+        a, b = out.cpu().numpy(), ref.cpu().numpy()
+        assert np.max(np.abs(a - b)) <= TOL * np.max(np.abs(b)), f"call {call}"
+
+
+def test_noalloc_rejects_oversized_requests():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2306_00165_gb300 as pcf
+    lib = pcf.load_library()
+    x = torch.zeros(8, dtype=torch.complex128, device="cuda")
+    ptr = ctypes.c_void_p(x.data_ptr())
+    for grid, batch in [((128, 97, 128), 1), ((96, 65, 96), 1), ((32, 33, 32), 2), ((64, 67, 64), 1)]:
+        p = _params(pcf, grid, batch)
+        assert lib.pcf_influence_matrix_solve_noalloc(ctypes.byref(p), ptr, ptr, 0.25, None) == 1  # PCF_EINVAL
