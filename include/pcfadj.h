@@ -137,17 +137,32 @@ pcf_status pcf_snapshot(pcf_ctx* ctx, const double* u_hat, double* psi);
 /* Inverse of pcf_snapshot: completes the wall conditions and rebuilds u_hat. */
 pcf_status pcf_from_snapshot(pcf_ctx* ctx, const double* psi, double* u_hat);
 
-/* DMD steady-state extrapolation of §6 for instance `inst`.
- * snapshots: device, (M+1) columns of pcf_psi_len doubles, column-major (column k =
- * snapshot k, oldest first); the M pairs are (s_k, s_{k+1}).  Householder QR of the
+/* DMD steady-state extrapolation of §6 for one instance.
+ * snapshots: device, (M+1) columns of pcf_psi_len doubles (column k = snapshot k,
+ * oldest first) with column stride ld >= pcf_psi_len doubles; the M pairs are
+ * (s_k, s_{k+1}).  Householder QR of the
  * snapshot matrix on the device; SVD, eigen-decomposition and amplitudes of the
  * small projected problem on the host; for each truncation rank r = r*..1 (r* = number
  * of singular values above rank_tol * sigma_1) the steady mode b_1 phi_1 (|ln lambda|
  * smallest) is rebuilt and its residual norm evaluated; the r with the smallest norm
  * is kept.  u_out_hat: device, one instance (output).  rank_used, j_out: host
  * (outputs, may be NULL).  Synchronises.  PCF_ENAN if no candidate has a finite norm. */
-pcf_status pcf_dmd_extrapolate(pcf_ctx* ctx, const double* snapshots, int M, double rank_tol,
+pcf_status pcf_dmd_extrapolate(pcf_ctx* ctx, const double* snapshots, long long ld, int M, double rank_tol,
                                double* u_out_hat, int* rank_used, double* j_out);
+
+/* Runs the descent to convergence for every instance (the hot loop of §5.1 with the DMD
+ * acceleration of §6): steps of pcf_descent_step with a per-instance convergence mask
+ * (an instance stops updating once J = ||r1|| < tol), at most max_steps steps.  With
+ * dmd_period > 0, a snapshot (pcf_snapshot) is taken every dmd_period/dmd_snapshots
+ * steps and after each period every unconverged instance jumps to its DMD steady state
+ * (pcf_dmd_extrapolate on the period's dmd_snapshots snapshots); a jump is skipped only
+ * when no candidate has a finite residual.  dmd_period = 0 disables DMD.
+ * u_hat: device, in place.  steps_out (host, batch): steps taken until J < tol, -1 if
+ * not converged; j_out (host, batch): last J; dmd_jumps (host): jumps taken.  Each may
+ * be NULL.  Synchronises; allocates its snapshot ring for the call.  PCF_ENAN if an
+ * instance's J became non-finite. */
+pcf_status pcf_run(pcf_ctx* ctx, double* u_hat, double dtau, int max_steps, double tol, int dmd_period,
+                   int dmd_snapshots, double rank_tol, int* steps_out, double* j_out, int* dmd_jumps);
 
 /* The Stokes solve of pcf_influence_matrix_solve for callers that cannot allocate device
  * memory (the paper has no counterpart; this is a library service).  Such callers - an

@@ -60,7 +60,8 @@ def load_library(path=None):
         "pcf_descent_step_host": (I, [P, P, D, I, P]),
         "pcf_snapshot": (I, [P, P, P]),
         "pcf_from_snapshot": (I, [P, P, P]),
-        "pcf_dmd_extrapolate": (I, [P, P, I, D, P, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "pcf_dmd_extrapolate": (I, [P, P, ctypes.c_longlong, I, D, P, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "pcf_run": (I, [P, P, D, I, D, I, I, D, P, P, ctypes.POINTER(I)]),
         "pcf_probe_fp64_peak": (I, [P, ctypes.POINTER(D)]),
         "pcf_set_kernel_timing": (I, [P, I]),
         "pcf_kernel_times": (I, [P, P, P, I]),
@@ -182,6 +183,46 @@ class Solver:
         """Same as descent_step with host (CPU, ideally pinned) complex128 tensors; synchronises."""
         _check(self.lib.pcf_descent_step_host(self._h, _ptr(u_host), float(dtau), int(nsteps),
                                               _ptr(hist_host)))
+
+    def snapshot(self, u, psi=None):
+        """Snapshot vectors of §6.2: float64 [batch, psi_len]."""
+        import torch
+        self._chk(u)
+        n = psi_len(self.nx, self.ny, self.nz)
+        psi = torch.empty((self.batch, n), dtype=torch.float64, device=self.device) if psi is None else psi
+        _check(self.lib.pcf_snapshot(self._h, _ptr(u), _ptr(psi)))
+        return psi
+
+    def from_snapshot(self, psi, u=None):
+        u = self.empty() if u is None else self._chk(u)
+        _check(self.lib.pcf_from_snapshot(self._h, _ptr(psi), _ptr(u)))
+        return u
+
+    def dmd_extrapolate(self, snapshots, rank_tol=1e-12, out=None, ld=None):
+        """DMD steady state of §6 from snapshots (float64 [M+1, psi_len] rows = snapshots, or a
+        strided view with column stride ``ld``); returns (state [1, ...] view of ``out``, rank, J)."""
+        import torch
+        n = psi_len(self.nx, self.ny, self.nz)
+        M = snapshots.shape[0] - 1
+        ld = n if ld is None else ld
+        if out is None:
+            out = torch.empty(self.shape[1:], dtype=torch.complex128, device=self.device)
+        r = ctypes.c_int()
+        j = ctypes.c_double()
+        _check(self.lib.pcf_dmd_extrapolate(self._h, _ptr(snapshots), int(ld), int(M), float(rank_tol), _ptr(out),
+                                             ctypes.byref(r), ctypes.byref(j)))
+        return out, r.value, j.value
+
+    def run(self, u, dtau, max_steps, tol=1e-10, dmd_period=100, dmd_snapshots=20, rank_tol=1e-12):
+        """Descent to J < tol with optional DMD jumps; returns (steps per instance, J per instance, jumps)."""
+        B = self.batch
+        steps = (ctypes.c_int * B)()
+        J = (ctypes.c_double * B)()
+        jumps = ctypes.c_int()
+        self._chk(u)
+        _check(self.lib.pcf_run(self._h, _ptr(u), float(dtau), int(max_steps), float(tol), int(dmd_period),
+                                int(dmd_snapshots), float(rank_tol), steps, J, ctypes.byref(jumps)))
+        return list(steps), list(J), jumps.value
 
     def set_kernel_timing(self, enable):
         _check(self.lib.pcf_set_kernel_timing(self._h, 1 if enable else 0))

@@ -1,0 +1,50 @@
+// Context of the pcfadj library (internal; shared by the host translation units).
+#pragma once
+#include <map>
+#include <vector>
+
+#include "pcf_kernels.cuh"
+
+struct pcf_ctx {
+  pcf_params prm;
+  int N, Kx, Kz, Mx, Mz, nm, B, mpc;
+  long long state_len;  // complex values per instance
+  cudaStream_t user = nullptr, cs = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<void*> allocs;
+  std::vector<pcf::Inst> hinst;
+  pcf::Inst* dinst = nullptr;
+  // prefix arrays
+  int* pre_synth11 = nullptr;
+  int* pre_synth3 = nullptr;
+  int* pre_prod = nullptr;
+  int* pre_mode = nullptr;
+  int* pre_inst = nullptr;
+  int cta_synth11 = 0, cta_synth3 = 0, cta_prod = 0, cta_mode = 0;
+  size_t sm_synth = 0, sm_prod = 0, sm_mode = 0;
+  double2* r_int = nullptr;    // internal r1 buffer for descent
+  double2* u_dev = nullptr;    // device state for the *_host entry point
+  double* hist_dev = nullptr;
+  int hist_cap = 0;
+  int* active = nullptr;
+  std::map<int, cudaGraphExec_t> graphs;
+  // timing
+  int timing = 0;
+  double kms[pcf::kNumKernelClasses] = {0};
+  long long kcount[pcf::kNumKernelClasses] = {0};
+  std::vector<cudaEvent_t> evpool;
+  // snapshot vector (psi) and DMD workspace, allocated on first use
+  int* d_indep = nullptr;   // (i, j) storage indices of the independent modes
+  int nindep = 0;
+  long long psi_len = 0;
+  double* dmd_A = nullptr;      // Householder QR workspace, psi_len x cap
+  double* dmd_part = nullptr;   // partial sums
+  double* dmd_coef = nullptr;   // per-column reflector data
+  double* dmd_cpsi = nullptr;   // candidate snapshot vectors
+  double2* dmd_cu = nullptr;    // candidate states
+  double* dmd_J = nullptr;      // candidate norms (batch)
+  double* dmd_c = nullptr;      // candidate coefficient vectors (device)
+  int dmd_cap = 0;              // columns the DMD workspace holds
+  int dmd_ncand_cap = 0;
+};
+

@@ -243,36 +243,7 @@ cudaError_t upload(const std::vector<T>& h, T** d) {
 
 }  // namespace
 
-// ------------------------------------------------------------------ context
-struct pcf_ctx {
-  pcf_params prm;
-  int N, Kx, Kz, Mx, Mz, nm, B, mpc;
-  long long state_len;  // complex values per instance
-  cudaStream_t user = nullptr, cs = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  std::vector<void*> allocs;
-  std::vector<Inst> hinst;
-  Inst* dinst = nullptr;
-  // prefix arrays
-  int* pre_synth11 = nullptr;
-  int* pre_synth3 = nullptr;
-  int* pre_prod = nullptr;
-  int* pre_mode = nullptr;
-  int* pre_inst = nullptr;
-  int cta_synth11 = 0, cta_synth3 = 0, cta_prod = 0, cta_mode = 0;
-  size_t sm_synth = 0, sm_prod = 0, sm_mode = 0;
-  double2* r_int = nullptr;    // internal r1 buffer for descent
-  double2* u_dev = nullptr;    // device state for the *_host entry point
-  double* hist_dev = nullptr;
-  int hist_cap = 0;
-  int* active = nullptr;
-  std::map<int, cudaGraphExec_t> graphs;
-  // timing
-  int timing = 0;
-  double kms[kNumKernelClasses] = {0};
-  long long kcount[kNumKernelClasses] = {0};
-  std::vector<cudaEvent_t> evpool;
-};
+#include "pcf_ctx.h"
 
 namespace {
 
@@ -587,13 +558,17 @@ pcf_status pcf_influence_matrix_solve(pcf_ctx* c, const double* rhs, double* out
   return leave(c);
 }
 
-pcf_status pcf_descent_step(pcf_ctx* c, double* u, double dtau, int nsteps, double* hist) {
+static pcf_status descent_internal(pcf_ctx* c, double* u, double dtau, int nsteps, double* hist, double tol) {
   if (!c || !u || nsteps < 0 || !(dtau >= 0)) return PCF_EINVAL;
   if (nsteps == 0) return PCF_OK;
   set_pointers(c, u, (const double*)c->r_int, nullptr);
   for (int b = 0; b < c->B; ++b) {
     c->hinst[b].dtau = dtau;
     c->hinst[b].hist = hist ? hist + b : nullptr;
+    if (tol > 0.0) {
+      c->hinst[b].tol = tol;
+      c->hinst[b].active = c->active + b;
+    }
   }
   PCF_TRY(enter(c));
   PCF_TRY(push_descriptors(c));
@@ -619,6 +594,89 @@ pcf_status pcf_descent_step(pcf_ctx* c, double* u, double dtau, int nsteps, doub
   }
   PCF_CUDA(cudaGraphLaunch(it->second, c->cs));
   return leave(c);
+}
+
+pcf_status pcf_descent_step(pcf_ctx* c, double* u, double dtau, int nsteps, double* hist) {
+  return descent_internal(c, u, dtau, nsteps, hist, 0.0);
+}
+
+pcf_status pcf_run(pcf_ctx* c, double* u, double dtau, int max_steps, double tol, int dmd_period, int dmd_snapshots,
+                   double rank_tol, int* steps_out, double* j_out, int* dmd_jumps) {
+  if (!c || !u || max_steps < 1 || !(tol > 0) || !(dtau > 0) || dmd_period < 0) return PCF_EINVAL;
+  const bool dmd = dmd_period > 0;
+  if (dmd && (dmd_snapshots < 3 || dmd_period % dmd_snapshots)) return PCF_EINVAL;
+  const int B = c->B;
+  const int chunk = dmd ? dmd_period / dmd_snapshots : 100;
+  const long long plen = pcf_psi_len(c->prm.nx, c->prm.ny, c->prm.nz);
+  double* ring = nullptr;
+  double* hist = nullptr;
+  PCF_CUDA(cudaMalloc(&hist, sizeof(double) * (size_t)chunk * B));
+  if (dmd) {
+    if (cudaMalloc(&ring, sizeof(double) * (size_t)dmd_snapshots * B * plen) != cudaSuccess) {
+      cudaFree(hist);
+      return PCF_ENOMEM;
+    }
+  }
+  std::vector<int> ones(B, 1), steps(B, 0), done(B, 0);
+  std::vector<double> J(B, NAN), hh((size_t)chunk * B);
+  int jumps = 0;
+  pcf_status st = PCF_OK;
+  auto finish = [&](pcf_status s) {
+    cudaStreamSynchronize(c->user);
+    if (hist) cudaFree(hist);
+    if (ring) cudaFree(ring);
+    for (int b = 0; b < B; ++b) {
+      if (steps_out) steps_out[b] = done[b] ? steps[b] : -1;
+      if (j_out) j_out[b] = J[b];
+    }
+    if (dmd_jumps) *dmd_jumps = jumps;
+    return s;
+  };
+  if (cudaMemcpyAsync(c->active, ones.data(), sizeof(int) * B, cudaMemcpyHostToDevice, c->user) != cudaSuccess)
+    return finish(PCF_ECUDA);
+  int taken = 0, k = 0;
+  while (taken < max_steps) {
+    const int n = std::min(chunk, max_steps - taken);
+    st = descent_internal(c, u, dtau, n, hist, tol);
+    if (st != PCF_OK) return finish(st);
+    if (dmd) {
+      st = pcf_snapshot(c, u, ring + (size_t)k * B * plen);
+      if (st != PCF_OK) return finish(st);
+    }
+    if (cudaMemcpyAsync(hh.data(), hist, sizeof(double) * (size_t)n * B, cudaMemcpyDeviceToHost, c->user) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->user) != cudaSuccess)
+      return finish(PCF_ECUDA);
+    int alive = 0;
+    for (int b = 0; b < B; ++b) {
+      if (done[b]) continue;
+      for (int s = 0; s < n; ++s) {
+        const double v = hh[(size_t)s * B + b];
+        J[b] = v;
+        if (!std::isfinite(v)) { done[b] = 2; break; }
+        if (v < tol) { done[b] = 1; steps[b] = taken + s; break; }
+      }
+      if (!done[b]) ++alive;
+    }
+    taken += n;
+    if (!alive) break;
+    ++k;
+    if (dmd && k == dmd_snapshots) {
+      k = 0;
+      for (int b = 0; b < B; ++b) {
+        if (done[b]) continue;
+        int r = 0;
+        double jr = 0;
+        const pcf_status sd = pcf_dmd_extrapolate(c, ring + (size_t)b * plen, (long long)B * plen, dmd_snapshots - 1,
+                                                  rank_tol, u + 2 * (size_t)b * c->state_len, &r, &jr);
+        if (sd == PCF_OK) ++jumps;
+        else if (sd != PCF_ENAN) return finish(sd);
+      }
+    }
+  }
+  for (int b = 0; b < B; ++b)
+    if (done[b] == 2) return finish(PCF_ENAN);
+  return finish(PCF_OK);
 }
 
 pcf_status pcf_descent_step_host(pcf_ctx* c, double* u_host, double dtau, int nsteps, double* hist_host) {
@@ -693,8 +751,5 @@ pcf_status pcf_probe_fp64_peak(void* stream, double* gflops) {
   return PCF_OK;
 }
 
-pcf_status pcf_snapshot(pcf_ctx*, const double*, double*) { return PCF_ENOTSUP; }
-pcf_status pcf_from_snapshot(pcf_ctx*, const double*, double*) { return PCF_ENOTSUP; }
-pcf_status pcf_dmd_extrapolate(pcf_ctx*, const double*, int, double, double*, int*, double*) { return PCF_ENOTSUP; }
 
 }  // extern "C"
