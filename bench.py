@@ -168,8 +168,8 @@ def run_reference(args):
     dist, rank, ws = _dist()
     if rank != 0:
         return
-    per = max(3.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
-    cb = cpu_baseline(seconds=per * max(1, args.steps))
+    # a bounded sample of the workload (about a minute of oracle steps), whatever K and W are
+    cb = cpu_baseline(seconds=float(os.environ.get("PCF_REFERENCE_SECONDS", "60")))
     line = {"impl": "reference", "metric": "gradient evals/s", "value": cb["value"], "unit": "gradient evals/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / cb["value"] * BATCH,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -194,6 +194,7 @@ def run_ours(args):
     u0 = gi.batch(gi.streak_roll, seeds, *GRID)
     s = pcf.Solver(*GRID, batch=BATCH, Re=RE, dt=DT, dtau_hat=DTAU_HAT)
     u = torch.from_numpy(u0).to(dev)
+    J0 = s.residual(u)[1].cpu().numpy()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream()
     for _ in range(max(3, args.warmup)):
@@ -242,6 +243,22 @@ def run_ours(args):
            "h2d_bytes_per_step": uh.numel() * uh.element_size(),
            "d2h_bytes_per_step": uh.numel() * uh.element_size() + hh.numel() * hh.element_size()}
 
+    # time to ||r1|| < 1e-10 (or 20k steps) with DMD every 100 steps from 20 snapshots, and without
+    ttc = {}
+    if not args.no_ttc:
+        for name, period in (("dmd", 100), ("no_dmd", 0)):
+            ut = torch.from_numpy(u0.copy()).to(dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            steps, J, jumps = s.run(ut, DTAU, args.ttc_steps, tol=1e-10, dmd_period=period, dmd_snapshots=20,
+                                    rank_tol=1e-12)
+            torch.cuda.synchronize()
+            wt = time.perf_counter() - t0
+            ttc[name] = {"wall_s": round(wt, 3), "max_steps": args.ttc_steps, "tol": 1e-10,
+                         "converged": sum(1 for x in steps if x >= 0), "of": BATCH, "steps": steps,
+                         "J_final": [float(x) for x in J], "dmd_jumps": jumps,
+                         "J_reduction_geomean": float(np.exp(np.mean(np.log(np.array(J) / np.array(J0)))))}
+
     # per-kernel CUDA-event timing (eager launches, same steps, same stream) for the roofline
     s.set_kernel_timing(True)
     nk = max(5, min(args.steps, 50))
@@ -275,6 +292,7 @@ def run_ours(args):
                            "l2": "flushed (256 MB write) before every timed step",
                            "parallelism": f"replicas x{ws}"},
                 "e2e": e2e, "gpu_launches": (1 + s.launches_per_step()) * args.steps,
+                "time_to_converge": ttc,
                 "roofline": roof, "clocks": ck, "wall_s": wall,
                 "J_after": [float(x) for x in J_last]}
         if ws == 1 and not args.no_cpu_baseline:
@@ -295,6 +313,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttc", action="store_true", help="skip the time-to-converge runs")
+    ap.add_argument("--ttc-steps", type=int, default=20000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -93,6 +93,24 @@ long long pcf_psi_len(int nx, int ny, int nz);
  * for dt and dtau_hat (§4) and allocates the workspace.  *out is set only on PCF_OK. */
 pcf_status pcf_create(const pcf_params* params, void* stream, pcf_ctx** out);
 
+/* Create a context over a batch of instances whose grids (and Re, box, step sizes) may
+ * differ: list[k] describes list[k].batch instances (the batched form of the method:
+ * many initial guesses of uneven grid sizes advanced by the same kernel launches, each
+ * step captured in one CUDA graph, with per-instance convergence masks in pcf_run).
+ * Instance states are stored back to back in the order given; pcf_state_offset gives
+ * each one's offset.  Tables are shared between instances on the same problem.  With
+ * list[0].modes_per_block = 0 an autotuner times the mode kernel for several tiles on
+ * the batch and keeps the fastest (pcf_mode_tile).  DMD entry points require every
+ * instance on one problem (PCF_ENOTSUP otherwise). */
+pcf_status pcf_batch_create(const pcf_params* list, int n, void* stream, pcf_ctx** out);
+
+/* Offset, in complex values, of instance `instance`'s state in the batch layout
+ * (instance = batch gives the total); -1 for an invalid instance. */
+long long pcf_state_offset(const pcf_ctx* ctx, int instance);
+
+/* Fourier modes per CTA chosen for the per-mode kernel (by the autotuner or the caller). */
+int pcf_mode_tile(const pcf_ctx* ctx);
+
 /* Release a context (waits for its stream).  NULL is ignored. */
 void pcf_destroy(pcf_ctx* ctx);
 

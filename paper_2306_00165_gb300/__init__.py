@@ -52,6 +52,9 @@ def load_library(path=None):
         "pcf_psi_len": (ctypes.c_longlong, [I, I, I]),
         "pcf_create": (I, [ctypes.POINTER(_Params), P, ctypes.POINTER(P)]),
         "pcf_destroy": (None, [P]),
+        "pcf_batch_create": (I, [ctypes.POINTER(_Params), I, P, ctypes.POINTER(P)]),
+        "pcf_state_offset": (ctypes.c_longlong, [P, I]),
+        "pcf_mode_tile": (I, [P]),
         "pcf_residual": (I, [P, P, P, P]),
         "pcf_adjoint_gradient": (I, [P, P, P, P]),
         "pcf_influence_matrix_solve": (I, [P, P, P, D]),
@@ -108,7 +111,10 @@ def probe_fp64_peak():
 
 class Solver:
     """One grid, ``batch`` instances; all tensors are complex128 on the current CUDA device,
-    shaped [batch, 3, Mx, Mz, ny] (see include/pcfadj.h for the layout)."""
+    shaped [batch, 3, Mx, Mz, ny] (see include/pcfadj.h for the layout).
+
+    ``Solver.batched([(nx, ny, nz, count), ...])`` builds a heterogeneous batch instead; its
+    states are one flat complex128 tensor (``flat_len`` values, instance views via ``view``)."""
 
     KERNEL_CLASSES = ["ysynth", "xzsynth_u", "prod_M", "mode_phi", "xzsynth_q", "prod_N", "mode_psi"]
 
@@ -124,6 +130,38 @@ class Solver:
         _check(self.lib.pcf_create(ctypes.byref(p), _stream(), ctypes.byref(h)))
         self._h = h
         self.device = torch.device("cuda", torch.cuda.current_device())
+        self.flat = False
+
+    @classmethod
+    def batched(cls, grids, Lx=LX_PAPER, Lz=LZ_PAPER, Re=400.0, dt=0.25, dtau_hat=0.25, modes_per_block=0):
+        """grids: list of (nx, ny, nz, count)."""
+        import torch
+        self = cls.__new__(cls)
+        self.lib = load_library()
+        arr = (_Params * len(grids))()
+        for k, (nx, ny, nz, cnt) in enumerate(grids):
+            arr[k] = _Params(nx, ny, nz, cnt, Lx, Lz, Re, dt, dtau_hat, 0, modes_per_block if k == 0 else 0,
+                             (ctypes.c_int * 2)(0, 0))
+        h = ctypes.c_void_p()
+        _check(self.lib.pcf_batch_create(arr, len(grids), _stream(), ctypes.byref(h)))
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.grids = [g for g in grids for _ in range(g[3])]
+        self.batch = len(self.grids)
+        self.offsets = [int(self.lib.pcf_state_offset(h, b)) for b in range(self.batch + 1)]
+        self.flat_len = self.offsets[-1]
+        self.shape = (self.flat_len,)
+        self.flat = True
+        self.dt, self.dtau_hat = dt, dtau_hat
+        return self
+
+    def view(self, flat, b):
+        """Instance b of a flat batch tensor as [3, Mx, Mz, ny]."""
+        nx, ny, nz, _ = self.grids[b]
+        return flat[self.offsets[b]:self.offsets[b + 1]].view(state_shape(nx, ny, nz, 1)[1:])
+
+    def mode_tile(self):
+        return int(self.lib.pcf_mode_tile(self._h))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -8,7 +8,11 @@
 struct pcf_ctx {
   pcf_params prm;
   int N, Kx, Kz, Mx, Mz, nm, B, mpc;
-  long long state_len;  // complex values per instance
+  long long state_len;  // complex values per instance (instance 0; all instances when uniform)
+  std::vector<long long> state_off;  // complex offset of each instance's state, [B+1]
+  long long total_state = 0;
+  bool uniform = true;   // every instance on the same problem
+  double tuned_ms = 0.0; // autotuner: time of the chosen mode-kernel launch
   cudaStream_t user = nullptr, cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   std::vector<void*> allocs;

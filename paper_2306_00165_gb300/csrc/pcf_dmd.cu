@@ -322,6 +322,7 @@ extern "C" {
 
 pcf_status pcf_snapshot(pcf_ctx* c, const double* u_hat, double* psi) {
   if (!c || !u_hat || !psi) return PCF_EINVAL;
+  if (!c->uniform) return PCF_ENOTSUP;
   DMD_TRY(ensure_indep(c));
   DMD_TRY(sync_in(c));
   const long long total = (long long)(c->nindep + 1) * c->prm.ny * c->B;
@@ -334,6 +335,7 @@ pcf_status pcf_snapshot(pcf_ctx* c, const double* u_hat, double* psi) {
 
 pcf_status pcf_from_snapshot(pcf_ctx* c, const double* psi, double* u_hat) {
   if (!c || !u_hat || !psi) return PCF_EINVAL;
+  if (!c->uniform) return PCF_ENOTSUP;
   if (c->prm.ny > 129) return PCF_EINVAL;
   DMD_TRY(ensure_indep(c));
   DMD_TRY(sync_in(c));
@@ -348,6 +350,7 @@ pcf_status pcf_from_snapshot(pcf_ctx* c, const double* psi, double* u_hat) {
 pcf_status pcf_dmd_extrapolate(pcf_ctx* c, const double* S, long long ld, int M, double rank_tol, double* u_out,
                                int* rank_used, double* j_out) {
   if (!c || !S || !u_out || M < 1 || !(rank_tol >= 0)) return PCF_EINVAL;
+  if (!c->uniform) return PCF_ENOTSUP;
   DMD_TRY(ensure_indep(c));
   if (ld < c->psi_len) return PCF_EINVAL;
   const int ncol = M + 1;

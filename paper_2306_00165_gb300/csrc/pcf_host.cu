@@ -327,9 +327,9 @@ pcf_status leave(pcf_ctx* c) {
 void set_pointers(pcf_ctx* c, const double* u, const double* r, double* f) {
   for (int b = 0; b < c->B; ++b) {
     Inst& I = c->hinst[b];
-    I.uhat = u ? (double2*)u + (size_t)b * c->state_len : nullptr;
-    I.rhat = r ? (double2*)r + (size_t)b * c->state_len : nullptr;
-    I.fhat = f ? (double2*)f + (size_t)b * c->state_len : nullptr;
+    I.uhat = u ? (double2*)u + c->state_off[b] : nullptr;
+    I.rhat = r ? (double2*)r + c->state_off[b] : nullptr;
+    I.fhat = f ? (double2*)f + c->state_off[b] : nullptr;
     I.hist = nullptr;
     I.active = nullptr;
     I.tol = 0.0;
@@ -380,22 +380,137 @@ long long pcf_psi_len(int nx, int ny, int nz) {
   return indep * (2LL * (ny - 4) + 2LL * (ny - 2)) + 2LL * (ny - 2);
 }
 
-pcf_status pcf_create(const pcf_params* prm, void* stream, pcf_ctx** out) {
-  if (!prm || !out) return PCF_EINVAL;
-  if (!grid_ok(prm->nx, prm->ny, prm->nz) || prm->batch < 1 || !(prm->Re > 0) || !(prm->dt > 0) ||
-      !(prm->dtau_hat > 0) || !(prm->Lx > 0) || !(prm->Lz > 0))
-    return PCF_EINVAL;
-  if (prm->precision != PCF_FP64) return PCF_ENOTSUP;
+static bool params_ok(const pcf_params* prm) {
+  return grid_ok(prm->nx, prm->ny, prm->nz) && prm->batch >= 1 && prm->Re > 0 && prm->dt > 0 &&
+         prm->dtau_hat > 0 && prm->Lx > 0 && prm->Lz > 0;
+}
+
+// Device tables of one grid (shared by every instance on that grid).
+struct GridTables {
+  double *cheb, *rco, *ccw, *kx, *kz, *y, *tab0, *tab1;
+  double2 *twx, *twz;
+  double sig[2];
+};
+
+static pcf_status build_tables(pcf_ctx* c, const pcf_params* prm, GridTables* g) {
+  const int N = prm->ny - 1, nx = prm->nx, ny = prm->ny, nz = prm->nz;
+  const int Kx = nx / 3 - 1, Kz = nz / 3 - 1, Mx = 2 * Kx + 1, Mz = Kz + 1;
+  const double nu = 1.0 / prm->Re;
+  std::vector<double> kx(Mx), kz(Mz), yg(ny);
+  for (int i = 0; i < Mx; ++i) kx[i] = 2.0 * kPi * (i <= Kx ? i : i - Mx) / prm->Lx;
+  for (int p = 0; p < Mz; ++p) kz[p] = 2.0 * kPi * p / prm->Lz;
+  for (int j = 0; j < ny; ++j) yg[j] = cospi_frac(j, N);
+  const std::vector<double> cheb = make_cheb(N), rco = make_rco(N), ccw = make_ccw(N);
+  g->sig[0] = 1.0 / (nu * prm->dt);
+  g->sig[1] = 1.0 / (nu * prm->dtau_hat);
+  const std::vector<double> tab0 = make_mode_tables(N, kx, kz, g->sig[0], rco);
+  const std::vector<double2> twx = make_twiddles(nx), twz = make_twiddles(nz);
+  if (upload(cheb, &g->cheb) || upload(rco, &g->rco) || upload(ccw, &g->ccw) || upload(kx, &g->kx) ||
+      upload(kz, &g->kz) || upload(yg, &g->y) || upload(twx, &g->twx) || upload(twz, &g->twz) ||
+      upload(tab0, &g->tab0))
+    return PCF_ECUDA;
+  for (void* p : {(void*)g->cheb, (void*)g->rco, (void*)g->ccw, (void*)g->kx, (void*)g->kz, (void*)g->y,
+                  (void*)g->twx, (void*)g->twz, (void*)g->tab0})
+    c->allocs.push_back(p);
+  if (prm->dtau_hat == prm->dt) {
+    g->tab1 = g->tab0;
+  } else {
+    if (upload(make_mode_tables(N, kx, kz, g->sig[1], rco), &g->tab1)) return PCF_ECUDA;
+    c->allocs.push_back(g->tab1);
+  }
+  return PCF_OK;
+}
+
+static pcf_status upload_prefix(pcf_ctx* c, const std::vector<int>& per, int** dst, int* total) {
+  std::vector<int> pre(per.size() + 1, 0);
+  for (size_t b = 0; b < per.size(); ++b) pre[b + 1] = pre[b] + per[b];
+  *total = pre.back();
+  if (*dst) {
+    PCF_CUDA(cudaMemcpy(*dst, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice));
+    return PCF_OK;
+  }
+  PCF_CUDA(upload(pre, dst));
+  c->allocs.push_back(*dst);
+  return PCF_OK;
+}
+
+// Mode tile of every instance (capped so the mode kernel's shared memory stays near 110 KB)
+// and the derived launch geometry.
+static pcf_status set_mode_tiles(pcf_ctx* c, int want) {
+  std::vector<int> per(c->B);
+  size_t sm = 0;
+  for (int b = 0; b < c->B; ++b) {
+    Inst& I = c->hinst[b];
+    int mpc = want;
+    while (mpc > 1 && smem_mode(I, mpc) > 110 * 1024) --mpc;
+    if (smem_mode(I, mpc) > 227 * 1024) return PCF_ENOTSUP;
+    I.mpc = mpc;
+    per[b] = (I.nmodes + mpc - 1) / mpc;
+    sm = std::max(sm, smem_mode(I, mpc));
+  }
+  c->mpc = want;
+  c->sm_mode = sm;
+  PCF_TRY(upload_prefix(c, per, &c->pre_mode, &c->cta_mode));
+  PCF_CUDA(cudaFuncSetAttribute(k_mode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->sm_mode));
+  return PCF_OK;
+}
+
+// Autotuner: time the Stokes-step mode kernel on the batch (laminar input) for each
+// candidate tile and keep the fastest.
+static pcf_status autotune_tiles(pcf_ctx* c) {
+  const int cand[] = {1, 2, 3, 4, 6, 8};
+  double2* z = nullptr;
+  PCF_CUDA(cudaMalloc(&z, sizeof(double2) * (size_t)c->total_state));
+  PCF_CUDA(cudaMemset(z, 0, sizeof(double2) * (size_t)c->total_state));
+  set_pointers(c, (const double*)z, (const double*)c->r_int, nullptr);
+  PCF_TRY(push_descriptors(c));
+  cudaEvent_t a, b;
+  PCF_CUDA(cudaEventCreate(&a));
+  PCF_CUDA(cudaEventCreate(&b));
+  int best = 4;
+  float best_ms = 1e30f;
+  for (int mpc : cand) {
+    if (set_mode_tiles(c, mpc) != PCF_OK) continue;
+    PCF_TRY(push_descriptors(c));
+    k_mode<<<c->cta_mode, 128, c->sm_mode, c->cs>>>(li_of(c, c->pre_mode), MODE_PHI, 0, mpc, 0);
+    PCF_CUDA(cudaEventRecord(a, c->cs));
+    for (int r = 0; r < 3; ++r)
+      k_mode<<<c->cta_mode, 128, c->sm_mode, c->cs>>>(li_of(c, c->pre_mode), MODE_PHI, 0, mpc, 0);
+    PCF_CUDA(cudaEventRecord(b, c->cs));
+    PCF_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    PCF_CUDA(cudaEventElapsedTime(&ms, a, b));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = mpc;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(z);
+  c->tuned_ms = best_ms / 3.0;
+  return set_mode_tiles(c, best);
+}
+
+static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, pcf_ctx** out) {
+  if (!list || nlist < 1 || !out) return PCF_EINVAL;
+  int B = 0;
+  for (int k = 0; k < nlist; ++k) {
+    if (!params_ok(&list[k])) return PCF_EINVAL;
+    if (list[k].precision != PCF_FP64) return PCF_ENOTSUP;
+    B += list[k].batch;
+  }
   pcf_ctx* c = new pcf_ctx();
-  c->prm = *prm;
-  c->N = prm->ny - 1;
-  c->Kx = prm->nx / 3 - 1;
-  c->Kz = prm->nz / 3 - 1;
+  c->prm = list[0];
+  c->prm.batch = B;
+  c->N = list[0].ny - 1;
+  c->Kx = list[0].nx / 3 - 1;
+  c->Kz = list[0].nz / 3 - 1;
   c->Mx = 2 * c->Kx + 1;
   c->Mz = c->Kz + 1;
   c->nm = c->Mx * c->Mz;
-  c->B = prm->batch;
-  c->state_len = 3LL * c->nm * prm->ny;
+  c->B = B;
+  c->state_len = 3LL * c->nm * list[0].ny;
   c->user = (cudaStream_t)stream;
   auto fail = [&](pcf_status s) {
     pcf_destroy(c);
@@ -405,98 +520,120 @@ pcf_status pcf_create(const pcf_params* prm, void* stream, pcf_ctx** out) {
   if (cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess) return fail(PCF_ECUDA);
   if (cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) return fail(PCF_ECUDA);
 
-  const int N = c->N, nx = prm->nx, ny = prm->ny, nz = prm->nz;
-  const double nu = 1.0 / prm->Re;
-  std::vector<double> kx(c->Mx), kz(c->Mz), yg(ny);
-  for (int i = 0; i < c->Mx; ++i) {
-    const int m = i <= c->Kx ? i : i - c->Mx;
-    kx[i] = 2.0 * kPi * m / prm->Lx;
-  }
-  for (int p = 0; p < c->Mz; ++p) kz[p] = 2.0 * kPi * p / prm->Lz;
-  for (int j = 0; j < ny; ++j) yg[j] = cospi_frac(j, N);
-  const std::vector<double> cheb = make_cheb(N), rco = make_rco(N), ccw = make_ccw(N);
-  const double sig[2] = {1.0 / (nu * prm->dt), 1.0 / (nu * prm->dtau_hat)};
-  std::vector<double> tabs[2];
-  tabs[0] = make_mode_tables(N, kx, kz, sig[0], rco);
-  if (prm->dtau_hat == prm->dt) tabs[1] = tabs[0];
-  else tabs[1] = make_mode_tables(N, kx, kz, sig[1], rco);
-  const std::vector<double2> twx = make_twiddles(nx), twz = make_twiddles(nz);
-
-  double *d_cheb, *d_rco, *d_ccw, *d_kx, *d_kz, *d_y, *d_tab0, *d_tab1;
-  double2 *d_twx, *d_twz;
-  if (upload(cheb, &d_cheb) || upload(rco, &d_rco) || upload(ccw, &d_ccw) || upload(kx, &d_kx) ||
-      upload(kz, &d_kz) || upload(yg, &d_y) || upload(twx, &d_twx) || upload(twz, &d_twz) ||
-      upload(tabs[0], &d_tab0))
-    return fail(PCF_ECUDA);
-  for (void* p : {(void*)d_cheb, (void*)d_rco, (void*)d_ccw, (void*)d_kx, (void*)d_kz, (void*)d_y, (void*)d_twx,
-                  (void*)d_twz, (void*)d_tab0})
-    c->allocs.push_back(p);
-  if (prm->dtau_hat == prm->dt) {
-    d_tab1 = d_tab0;
-  } else {
-    if (upload(tabs[1], &d_tab1)) return fail(PCF_ECUDA);
-    c->allocs.push_back(d_tab1);
+  // one table set per distinct problem
+  std::vector<GridTables> gts;
+  std::vector<int> grid_of(nlist);
+  c->uniform = true;
+  for (int k = 0; k < nlist; ++k) {
+    int found = -1;
+    for (int q = 0; q < k; ++q) {
+      const pcf_params &a = list[k], &p = list[q];
+      if (a.nx == p.nx && a.ny == p.ny && a.nz == p.nz && a.Lx == p.Lx && a.Lz == p.Lz && a.Re == p.Re &&
+          a.dt == p.dt && a.dtau_hat == p.dtau_hat) {
+        found = grid_of[q];
+        break;
+      }
+    }
+    if (found < 0) {
+      GridTables g;
+      pcf_status st = build_tables(c, &list[k], &g);
+      if (st != PCF_OK) return fail(st);
+      gts.push_back(g);
+      found = (int)gts.size() - 1;
+    }
+    grid_of[k] = found;
+    if (found != 0) c->uniform = false;
   }
 
-  // per-instance workspace
-  const int B = c->B;
-  const size_t yv_n = 2ULL * kFieldsY * ny * c->nm, ph_n = 2ULL * kFieldsSynth * ny * nx * nz;
-  const size_t xz_n = 3ULL * ny * c->nm, np_n = 3ULL * ny;
+  // per-instance workspace, one allocation per buffer kind
+  size_t n_yv = 0, n_ph = 0, n_xz = 0, n_np = 0;
+  c->state_off.assign(B + 1, 0);
+  {
+    int b = 0;
+    for (int k = 0; k < nlist; ++k)
+      for (int r = 0; r < list[k].batch; ++r, ++b) {
+        const pcf_params& p = list[k];
+        const long long nm = (long long)(2 * (p.nx / 3 - 1) + 1) * (p.nz / 3);
+        n_yv += 2ULL * kFieldsY * p.ny * nm;
+        n_ph += 2ULL * kFieldsSynth * p.ny * p.nx * p.nz;
+        n_xz += 3ULL * p.ny * nm;
+        n_np += 3ULL * p.ny;
+        c->state_off[b + 1] = c->state_off[b] + 3LL * nm * p.ny;
+      }
+  }
+  c->total_state = c->state_off[B];
   double2 *yv, *xz;
   double *ph, *np;
-  if (ctx_alloc(c, &yv, yv_n * B) || ctx_alloc(c, &ph, ph_n * B) || ctx_alloc(c, &xz, xz_n * B) ||
-      ctx_alloc(c, &np, np_n * B) || ctx_alloc(c, &c->r_int, (size_t)c->state_len * B) ||
-      ctx_alloc(c, &c->active, (size_t)B))
+  if (ctx_alloc(c, &yv, n_yv) || ctx_alloc(c, &ph, n_ph) || ctx_alloc(c, &xz, n_xz) || ctx_alloc(c, &np, n_np) ||
+      ctx_alloc(c, &c->r_int, (size_t)c->total_state) || ctx_alloc(c, &c->active, (size_t)B))
     return fail(PCF_ENOMEM);
   c->hinst.resize(B);
-  for (int b = 0; b < B; ++b) {
-    Inst& I = c->hinst[b];
-    memset(&I, 0, sizeof(I));
-    I.nx = nx; I.ny = ny; I.nz = nz; I.N = N; I.Kx = c->Kx; I.Kz = c->Kz; I.Mx = c->Mx; I.Mz = c->Mz;
-    I.nmodes = c->nm;
-    radix_plan(nx, I.rx, &I.nrx);
-    radix_plan(nz, I.rz, &I.nrz);
-    I.nu = nu; I.dt = prm->dt; I.dtau_hat = prm->dtau_hat; I.dtau = 0.0;
-    I.inv_nxnz = 1.0 / ((double)nx * nz);
-    I.cheb = d_cheb; I.rco = d_rco; I.ygrid = d_y; I.ccw = d_ccw; I.kx = d_kx; I.kz = d_kz;
-    I.twx = d_twx; I.twz = d_twz;
-    I.tab[0] = d_tab0; I.tab[1] = d_tab1;
-    I.sigma[0] = sig[0]; I.sigma[1] = sig[1];
-    I.yv = yv + yv_n * b; I.phys = ph + ph_n * b; I.xz = xz + xz_n * b; I.normpart = np + np_n * b;
-    I.hist_stride = B;
-  }
+  std::vector<int> per11(B), per3(B), per1(B, 1);
+  size_t o_yv = 0, o_ph = 0, o_xz = 0, o_np = 0;
+  int b = 0;
+  for (int k = 0; k < nlist; ++k)
+    for (int r = 0; r < list[k].batch; ++r, ++b) {
+      const pcf_params& p = list[k];
+      const GridTables& g = gts[grid_of[k]];
+      Inst& I = c->hinst[b];
+      memset(&I, 0, sizeof(I));
+      I.nx = p.nx; I.ny = p.ny; I.nz = p.nz; I.N = p.ny - 1;
+      I.Kx = p.nx / 3 - 1; I.Kz = p.nz / 3 - 1; I.Mx = 2 * I.Kx + 1; I.Mz = I.Kz + 1;
+      I.nmodes = I.Mx * I.Mz;
+      radix_plan(p.nx, I.rx, &I.nrx);
+      radix_plan(p.nz, I.rz, &I.nrz);
+      I.nu = 1.0 / p.Re; I.dt = p.dt; I.dtau_hat = p.dtau_hat; I.dtau = 0.0;
+      I.inv_nxnz = 1.0 / ((double)p.nx * p.nz);
+      I.cheb = g.cheb; I.rco = g.rco; I.ygrid = g.y; I.ccw = g.ccw; I.kx = g.kx; I.kz = g.kz;
+      I.twx = g.twx; I.twz = g.twz;
+      I.tab[0] = g.tab0; I.tab[1] = g.tab1;
+      I.sigma[0] = g.sig[0]; I.sigma[1] = g.sig[1];
+      I.yv = yv + o_yv; I.phys = ph + o_ph; I.xz = xz + o_xz; I.normpart = np + o_np;
+      o_yv += 2ULL * kFieldsY * p.ny * I.nmodes;
+      o_ph += 2ULL * kFieldsSynth * p.ny * p.nx * p.nz;
+      o_xz += 3ULL * p.ny * I.nmodes;
+      o_np += 3ULL * p.ny;
+      I.hist_stride = B;
+      per11[b] = kFieldsSynth * p.ny;
+      per3[b] = 3 * p.ny;
+      c->sm_synth = std::max(c->sm_synth, smem_xzsynth(I));
+      c->sm_prod = std::max(c->sm_prod, smem_prod(I));
+    }
   if (ctx_alloc(c, &c->dinst, (size_t)B)) return fail(PCF_ENOMEM);
-  // modes per CTA: keep the shared memory of the mode kernel near 100 KB
-  int mpc = prm->modes_per_block > 0 ? prm->modes_per_block : 4;
-  while (mpc > 1 && smem_mode(c->hinst[0], mpc) > 110 * 1024) --mpc;
-  if (smem_mode(c->hinst[0], mpc) > 227 * 1024) return fail(PCF_ENOTSUP);
-  c->mpc = mpc;
-  c->sm_mode = smem_mode(c->hinst[0], mpc);
-  c->sm_synth = smem_xzsynth(c->hinst[0]);
-  c->sm_prod = smem_prod(c->hinst[0]);
-  // CTA prefix arrays (uniform batch)
-  auto prefix = [&](int per, int** dst, int* total) -> bool {
-    std::vector<int> pre(B + 1);
-    for (int b = 0; b <= B; ++b) pre[b] = b * per;
-    *total = B * per;
-    if (upload(pre, dst) != cudaSuccess) return false;
-    c->allocs.push_back(*dst);
-    return true;
-  };
   int dummy;
-  if (!prefix(kFieldsSynth * ny, &c->pre_synth11, &c->cta_synth11) || !prefix(3 * ny, &c->pre_synth3, &c->cta_synth3) ||
-      !prefix(3 * ny, &c->pre_prod, &c->cta_prod) || !prefix((c->nm + mpc - 1) / mpc, &c->pre_mode, &c->cta_mode) ||
-      !prefix(1, &c->pre_inst, &dummy))
-    return fail(PCF_ECUDA);
-  if (cudaFuncSetAttribute(k_mode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->sm_mode) ||
-      cudaFuncSetAttribute(k_xzsynth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->sm_synth) ||
+  pcf_status st;
+  if ((st = upload_prefix(c, per11, &c->pre_synth11, &c->cta_synth11)) != PCF_OK ||
+      (st = upload_prefix(c, per3, &c->pre_synth3, &c->cta_synth3)) != PCF_OK ||
+      (st = upload_prefix(c, per3, &c->pre_prod, &c->cta_prod)) != PCF_OK ||
+      (st = upload_prefix(c, per1, &c->pre_inst, &dummy)) != PCF_OK)
+    return fail(st);
+  if (cudaFuncSetAttribute(k_xzsynth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->sm_synth) ||
       cudaFuncSetAttribute(k_prod_M, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->sm_prod) ||
       cudaFuncSetAttribute(k_prod_N, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->sm_prod))
     return fail(PCF_ECUDA);
+  const int want = list[0].modes_per_block;
+  st = want > 0 ? set_mode_tiles(c, want) : (c->uniform ? set_mode_tiles(c, 4) : autotune_tiles(c));
+  if (st != PCF_OK) return fail(st);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(PCF_ECUDA);
   *out = c;
   return PCF_OK;
 }
+
+pcf_status pcf_create(const pcf_params* prm, void* stream, pcf_ctx** out) {
+  if (!prm || !out) return PCF_EINVAL;
+  return create_batch(prm, 1, stream, out);
+}
+
+pcf_status pcf_batch_create(const pcf_params* list, int n, void* stream, pcf_ctx** out) {
+  return create_batch(list, n, stream, out);
+}
+
+long long pcf_state_offset(const pcf_ctx* c, int instance) {
+  if (!c || instance < 0 || instance > c->B) return -1;
+  return c->state_off[instance];
+}
+
+int pcf_mode_tile(const pcf_ctx* c) { return c ? c->mpc : 0; }
 
 void pcf_destroy(pcf_ctx* c) {
   if (!c) return;
@@ -604,6 +741,7 @@ pcf_status pcf_run(pcf_ctx* c, double* u, double dtau, int max_steps, double tol
                    double rank_tol, int* steps_out, double* j_out, int* dmd_jumps) {
   if (!c || !u || max_steps < 1 || !(tol > 0) || !(dtau > 0) || dmd_period < 0) return PCF_EINVAL;
   const bool dmd = dmd_period > 0;
+  if (dmd && !c->uniform) return PCF_ENOTSUP;
   if (dmd && (dmd_snapshots < 3 || dmd_period % dmd_snapshots)) return PCF_EINVAL;
   const int B = c->B;
   const int chunk = dmd ? dmd_period / dmd_snapshots : 100;
@@ -668,7 +806,7 @@ pcf_status pcf_run(pcf_ctx* c, double* u, double dtau, int max_steps, double tol
         int r = 0;
         double jr = 0;
         const pcf_status sd = pcf_dmd_extrapolate(c, ring + (size_t)b * plen, (long long)B * plen, dmd_snapshots - 1,
-                                                  rank_tol, u + 2 * (size_t)b * c->state_len, &r, &jr);
+                                                  rank_tol, u + 2 * (size_t)c->state_off[b], &r, &jr);
         if (sd == PCF_OK) ++jumps;
         else if (sd != PCF_ENAN) return finish(sd);
       }
@@ -681,7 +819,7 @@ pcf_status pcf_run(pcf_ctx* c, double* u, double dtau, int max_steps, double tol
 
 pcf_status pcf_descent_step_host(pcf_ctx* c, double* u_host, double dtau, int nsteps, double* hist_host) {
   if (!c || !u_host || nsteps < 0) return PCF_EINVAL;
-  const size_t bytes = sizeof(double2) * (size_t)c->state_len * c->B;
+  const size_t bytes = sizeof(double2) * (size_t)c->total_state;
   if (!c->u_dev) PCF_CUDA(cudaMalloc(&c->u_dev, bytes));
   if (hist_host && c->hist_cap < nsteps) {
     if (c->hist_dev) cudaFree(c->hist_dev);

@@ -63,6 +63,7 @@ struct ChebLayout {
 // ------------------------------------------------------------------ instance descriptor
 struct Inst {
   int nx, ny, nz, N, Kx, Kz, Mx, Mz, nmodes;
+  int mpc;  // Fourier modes per CTA of the mode kernel (0: use the launch argument)
   int nrx, nrz;
   int rx[kMaxRadix], rz[kMaxRadix];
   double nu, dt, dtau_hat, dtau, inv_nxnz, tol;

@@ -380,11 +380,12 @@ size_t smem_mode(const Inst& I, int mpc) {
   return d * sizeof(double);
 }
 
-__global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, int mpc, int step_index) {
+__global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, int mpc_arg, int step_index) {
   extern __shared__ double smd[];
   int local;
   const int b = find_inst(li, blockIdx.x, &local);
   const Inst& I = li.insts[b];
+  const int mpc = I.mpc > 0 ? I.mpc : mpc_arg;
   const int N = I.N, Mh = N / 2 + 1, H = Mh, L2 = 2 * Mh, ny = I.ny;
   const int nm = I.nmodes, Mz = I.Mz;
   const int m0 = local * mpc;

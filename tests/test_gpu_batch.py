@@ -1,0 +1,109 @@
+"""Batched form: many guesses on uneven grids advanced by the same launches (CUDA graph per
+step), per-instance convergence masks, an autotuned mode tile.  Every instance is compared
+with the FP64 oracle at 1e-11, as in the single-grid tests."""
+import numpy as np
+import pytest
+
+import pcf_inputs as gi
+from oracle import PCFOracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def pcf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2306_00165_gb300 as m
+    m.load_library()
+    return m
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _flat(states):
+    return torch.from_numpy(np.concatenate([s.ravel() for s in states])).cuda()
+
+
+MIXED = [(16, 17, 16, 2), (32, 33, 32, 2), (48, 49, 48, 1)]
+
+
+def _mixed_inputs():
+    us, seeds = [], iter(range(100))
+    for (nx, ny, nz, cnt) in MIXED:
+        for _ in range(cnt):
+            us.append(gi.random_perturbation(nx, ny, nz, 0.1, next(seeds)))
+    return us
+
+
+def test_mixed_batch_residual_gradient_steps(pcf):
+    us = _mixed_inputs()
+    s = pcf.Solver.batched(MIXED)
+    assert s.mode_tile() in (1, 2, 3, 4, 6, 8)
+    u = _flat(us)
+    r, J = s.residual(u)
+    f = s.adjoint_gradient(u, r)
+    H = s.descent_step(u, 0.01, 5).cpu().numpy()
+    for b, g in enumerate(s.grids):
+        o = PCFOracle(*g[:3])
+        r_ref, J_ref = o.residual(us[b])
+        f_ref = o.adjoint_direction(us[b], r_ref)
+        assert _rel(s.view(r, b).cpu().numpy(), r_ref) <= TOL
+        assert abs(float(J[b]) - J_ref) <= TOL * J_ref
+        assert _rel(s.view(f, b).cpu().numpy(), f_ref) <= TOL
+        ref, Href = o.run(us[b], 0.01, 5)
+        assert np.max(np.abs(H[:, b] - Href) / Href) <= TOL
+        assert _rel(s.view(u, b).cpu().numpy(), ref) <= TOL
+
+
+def test_results_do_not_depend_on_the_tile(pcf):
+    us = _mixed_inputs()
+    outs = []
+    for mpc in (1, 3, 6):
+        s = pcf.Solver.batched(MIXED, modes_per_block=mpc)
+        u = _flat(us)
+        s.descent_step(u, 0.01, 3)
+        outs.append(u.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_mixed_batch_convergence_masks(pcf):
+    us = _mixed_inputs()
+    hists = [PCFOracle(*g[:3]).run(us[b], 0.01, 40)[1] for b, g in
+             enumerate([g for g in MIXED for _ in range(g[3])])]
+    # a tolerance strictly between two steps of every instance (no rounding-level ties)
+    cand = sorted(np.sqrt(h[k] * h[k + 1]) for h in hists for k in range(20, 30))
+    allh = np.concatenate(hists)
+    tol = next(t for t in cand[len(cand) // 2:] if np.min(np.abs(allh - t) / t) > 1e-6)
+    want = [int(np.argmax(h < tol)) if np.any(h < tol) else -1 for h in hists]
+    s = pcf.Solver.batched(MIXED)
+    u = _flat(us)
+    steps, J, jumps = s.run(u, 0.01, 40, tol=tol, dmd_period=0)
+    assert steps == want
+
+
+def test_uneven_64_instance_batch(pcf):
+    """24 x 32x33x32 + 24 x 48x49x48 + 16 x 64x65x64 in one context: every instance stays
+    admissible, and one instance of each grid matches the oracle after one step."""
+    grids = [(32, 33, 32, 24), (48, 49, 48, 24), (64, 65, 64, 16)]
+    s = pcf.Solver.batched(grids)
+    us = []
+    k = 0
+    for (nx, ny, nz, cnt) in grids:
+        for _ in range(cnt):
+            us.append(gi.streak_roll(nx, ny, nz, seed=k))
+            k += 1
+    u = _flat(us)
+    H = s.descent_step(u, 0.01, 1).cpu().numpy()[0]
+    assert np.all(np.isfinite(H)) and np.all(H > 0)
+    for b in (0, 24, 63):
+        g = s.grids[b][:3]
+        o = PCFOracle(*g)
+        ref, Href = o.run(us[b], 0.01, 1)
+        got = s.view(u, b).cpu().numpy()
+        assert abs(H[b] - Href[0]) <= TOL * Href[0]
+        assert _rel(got, ref) <= TOL
