@@ -68,7 +68,8 @@ typedef struct pcf_params {
   double dt, dtau_hat;
   int precision;        /* pcf_precision; PCF_FP64 for the plain method */
   int modes_per_block;  /* tile of the per-mode kernels; 0 = library default */
-  int reserved[2];
+  int solve_kind;       /* 0: dense per-mode operators when ny <= 65, else sweeps; 1: banded sweeps */
+  int reserved;
 } pcf_params;
 
 typedef struct pcf_ctx pcf_ctx;

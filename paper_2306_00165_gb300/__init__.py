@@ -30,7 +30,7 @@ class _Params(ctypes.Structure):
                 ("Lx", ctypes.c_double), ("Lz", ctypes.c_double), ("Re", ctypes.c_double),
                 ("dt", ctypes.c_double), ("dtau_hat", ctypes.c_double),
                 ("precision", ctypes.c_int), ("modes_per_block", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("solve_kind", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 def load_library(path=None):
@@ -119,13 +119,13 @@ class Solver:
     KERNEL_CLASSES = ["ysynth", "xzsynth_u", "prod_M", "mode_phi", "xzsynth_q", "prod_N", "mode_psi"]
 
     def __init__(self, nx, ny, nz, batch=1, Lx=LX_PAPER, Lz=LZ_PAPER, Re=400.0, dt=0.25, dtau_hat=0.25,
-                 precision=0, modes_per_block=0):
+                 precision=0, modes_per_block=0, solve_kind=0):
         import torch
         self.lib = load_library()
         self.shape = state_shape(nx, ny, nz, batch)
         self.nx, self.ny, self.nz, self.batch = nx, ny, nz, batch
         self.dt, self.dtau_hat = dt, dtau_hat
-        p = _Params(nx, ny, nz, batch, Lx, Lz, Re, dt, dtau_hat, precision, modes_per_block, (ctypes.c_int * 2)(0, 0))
+        p = _Params(nx, ny, nz, batch, Lx, Lz, Re, dt, dtau_hat, precision, modes_per_block, solve_kind, 0)
         h = ctypes.c_void_p()
         _check(self.lib.pcf_create(ctypes.byref(p), _stream(), ctypes.byref(h)))
         self._h = h
@@ -140,8 +140,7 @@ class Solver:
         self.lib = load_library()
         arr = (_Params * len(grids))()
         for k, (nx, ny, nz, cnt) in enumerate(grids):
-            arr[k] = _Params(nx, ny, nz, cnt, Lx, Lz, Re, dt, dtau_hat, 0, modes_per_block if k == 0 else 0,
-                             (ctypes.c_int * 2)(0, 0))
+            arr[k] = _Params(nx, ny, nz, cnt, Lx, Lz, Re, dt, dtau_hat, 0, modes_per_block if k == 0 else 0, 0, 0)
         h = ctypes.c_void_p()
         _check(self.lib.pcf_batch_create(arr, len(grids), _stream(), ctypes.byref(h)))
         self._h = h

@@ -214,6 +214,72 @@ std::vector<double> make_mode_tables(int N, const std::vector<double>& kx, const
   return t;
 }
 
+// Dense per-mode operators: the chain of mode_chain applied to unit inputs (no correction
+// shortcut: the same arithmetic as the sweep path, one column at a time).
+std::vector<double> make_dense_tables(int N, const std::vector<double>& kx, const std::vector<double>& kz,
+                                      double sigma, const std::vector<double>& rco, const std::vector<double>& tabs) {
+  const TabLayout TL(N);
+  const RcoLayout RL(N);
+  const DenseLayout DL(N);
+  const int Mx = (int)kx.size(), Mz = (int)kz.size(), Mh = N / 2 + 1, L2 = 2 * Mh;
+  std::vector<double> out((size_t)Mx * Mz * DL.per_mode(), 0.0);
+  std::vector<double> Fr(6 * L2), sc(6 * Mh);
+  for (int i = 0; i < Mx; ++i)
+    for (int p = 0; p < Mz; ++p) {
+      const size_t m = (size_t)i * Mz + p;
+      const double* tab = tabs.data() + m * TL.per_mode();
+      double* d = out.data() + m * DL.per_mode();
+      const double k2 = kx[i] * kx[i] + kz[p] * kz[p];
+      for (int g = 0; g < 2; ++g) {
+        const int pv = g, pP = 1 - g;
+        const int McV = (N - pv) / 2 + 1, McP = (N - pP) / 2 + 1;
+        if (k2 == 0.0) {
+          const int Mc = (N - g) / 2 + 1;
+          const double* s = tab + TL.solver(1, g);
+          std::vector<double> e(Mh), y(Mh);
+          for (int j = 0; j < Mc; ++j) {
+            std::fill(e.begin(), e.end(), 0.0);
+            e[j] = 1.0;
+            tau_solve(Mc, s, s + Mh, s + 2 * Mh, s + 3 * Mh, s[4 * Mh], rco.data() + RL.off(g, 0),
+                      rco.data() + RL.off(g, 1), rco.data() + RL.off(g, 2), e.data(), 0.0, y.data());
+            for (int r = 0; r < Mc; ++r) d[DL.block(g, 4) + r * Mh + j] = y[r];
+          }
+          continue;
+        }
+        // columns for f_v (class pv) and g (class pP), taken through the real-part chain
+        // (rho = 0, where g enters as -(kx f_u + kz f_w) built from the imaginary parts)
+        for (int src = 0; src < 2; ++src) {
+          const int nc = src == 0 ? McV : McP;
+          for (int j = 0; j < nc; ++j) {
+            std::fill(Fr.begin(), Fr.end(), 0.0);
+            if (src == 0) {
+              Fr[(1 * 2 + 0) * L2 + pv * Mh + j] = 1.0;
+            } else {
+              // rho = 0: g_re = -(kx Im f_u + kz Im f_w); choose Im f_u so that g_re = e_j
+              if (kx[i] != 0.0) Fr[(0 * 2 + 1) * L2 + pP * Mh + j] = -1.0 / kx[i];
+              else Fr[(2 * 2 + 1) * L2 + pP * Mh + j] = -1.0 / kz[p];
+            }
+            std::fill(sc.begin(), sc.end(), 0.0);
+            mode_chain(N, g, 0, kx[i], kz[p], sigma + k2, tab, rco.data(), Fr.data(), L2, sc.data());
+            for (int r = 0; r < McV; ++r) d[DL.block(g, src == 0 ? 0 : 1) + r * Mh + j] = sc[2 * Mh + r];
+            for (int r = 0; r < McP; ++r) d[DL.block(g, src == 0 ? 2 : 3) + r * Mh + j] = sc[3 * Mh + r];
+          }
+        }
+        // eta: inverse Helmholtz of class pP
+        const double* s = tab + TL.solver(1, pP);
+        std::vector<double> e(Mh), y(Mh);
+        for (int j = 0; j < McP; ++j) {
+          std::fill(e.begin(), e.end(), 0.0);
+          e[j] = 1.0;
+          tau_solve(McP, s, s + Mh, s + 2 * Mh, s + 3 * Mh, s[4 * Mh], rco.data() + RL.off(pP, 0),
+                    rco.data() + RL.off(pP, 1), rco.data() + RL.off(pP, 2), e.data(), 0.0, y.data());
+          for (int r = 0; r < McP; ++r) d[DL.block(g, 4) + r * Mh + j] = y[r];
+        }
+      }
+    }
+  return out;
+}
+
 // Interpolatory (Clenshaw-Curtis) weights: w_j = sum_n Cinv_{n j} int_{-1}^{1} T_n dy.
 std::vector<double> make_ccw(int N) {
   std::vector<double> w(N + 1, 0.0);
@@ -387,7 +453,7 @@ static bool params_ok(const pcf_params* prm) {
 
 // Device tables of one grid (shared by every instance on that grid).
 struct GridTables {
-  double *cheb, *rco, *ccw, *kx, *kz, *y, *tab0, *tab1;
+  double *cheb, *rco, *ccw, *kx, *kz, *y, *tab0, *tab1, *dense0, *dense1;
   double2 *twx, *twz;
   double sig[2];
 };
@@ -412,11 +478,25 @@ static pcf_status build_tables(pcf_ctx* c, const pcf_params* prm, GridTables* g)
   for (void* p : {(void*)g->cheb, (void*)g->rco, (void*)g->ccw, (void*)g->kx, (void*)g->kz, (void*)g->y,
                   (void*)g->twx, (void*)g->twz, (void*)g->tab0})
     c->allocs.push_back(p);
+  std::vector<double> tab1;
   if (prm->dtau_hat == prm->dt) {
     g->tab1 = g->tab0;
   } else {
-    if (upload(make_mode_tables(N, kx, kz, g->sig[1], rco), &g->tab1)) return PCF_ECUDA;
+    tab1 = make_mode_tables(N, kx, kz, g->sig[1], rco);
+    if (upload(tab1, &g->tab1)) return PCF_ECUDA;
     c->allocs.push_back(g->tab1);
+  }
+  g->dense0 = g->dense1 = nullptr;
+  const bool dense = N <= kDenseMaxN && prm->solve_kind != 1;
+  if (dense) {
+    if (upload(make_dense_tables(N, kx, kz, g->sig[0], rco, tab0), &g->dense0)) return PCF_ECUDA;
+    c->allocs.push_back(g->dense0);
+    if (prm->dtau_hat == prm->dt) {
+      g->dense1 = g->dense0;
+    } else {
+      if (upload(make_dense_tables(N, kx, kz, g->sig[1], rco, tab1), &g->dense1)) return PCF_ECUDA;
+      c->allocs.push_back(g->dense1);
+    }
   }
   return PCF_OK;
 }
@@ -529,7 +609,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
     for (int q = 0; q < k; ++q) {
       const pcf_params &a = list[k], &p = list[q];
       if (a.nx == p.nx && a.ny == p.ny && a.nz == p.nz && a.Lx == p.Lx && a.Lz == p.Lz && a.Re == p.Re &&
-          a.dt == p.dt && a.dtau_hat == p.dtau_hat) {
+          a.dt == p.dt && a.dtau_hat == p.dtau_hat && a.solve_kind == p.solve_kind) {
         found = grid_of[q];
         break;
       }
@@ -587,6 +667,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       I.cheb = g.cheb; I.rco = g.rco; I.ygrid = g.y; I.ccw = g.ccw; I.kx = g.kx; I.kz = g.kz;
       I.twx = g.twx; I.twz = g.twz;
       I.tab[0] = g.tab0; I.tab[1] = g.tab1;
+      I.dense[0] = g.dense0; I.dense[1] = g.dense1;
       I.sigma[0] = g.sig[0]; I.sigma[1] = g.sig[1];
       I.yv = yv + o_yv; I.phys = ph + o_ph; I.xz = xz + o_xz; I.normpart = np + o_np;
       o_yv += 2ULL * kFieldsY * p.ny * I.nmodes;
@@ -612,7 +693,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       cudaFuncSetAttribute(k_prod_N, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->sm_prod))
     return fail(PCF_ECUDA);
   const int want = list[0].modes_per_block;
-  st = want > 0 ? set_mode_tiles(c, want) : (c->uniform ? set_mode_tiles(c, 4) : autotune_tiles(c));
+  st = want > 0 ? set_mode_tiles(c, want) : autotune_tiles(c);
   if (st != PCF_OK) return fail(st);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(PCF_ECUDA);
   *out = c;

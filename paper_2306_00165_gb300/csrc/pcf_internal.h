@@ -31,6 +31,20 @@ struct TabLayout {
   PCF_HD int per_mode() const { return 4 * (4 * Mh + 2) + 2 * (2 * Mh + 4); }
 };
 
+// Dense form of the same per-mode solve (used for N <= kDenseMaxN): for each parity group g
+// five Mh x Mh row-major blocks mapping the group's inputs to its outputs,
+//   v  = Av f_v + Ag g,   xi = Xv f_v + Xg g,   eta = Eh h,
+// with f_v the v right-hand side (class g), g = Re/Im part of i(kx f_u + kz f_w) and
+// h = Re/Im part of i(kz f_u - kx f_w) (class 1-g).  For the mean mode, Eh of group g is
+// the inverse Dirichlet Helmholtz operator of class g (applied to f_u and f_w).
+constexpr int kDenseMaxN = 64;
+struct DenseLayout {
+  int Mh;
+  PCF_HD DenseLayout(int N) : Mh(N / 2 + 1) {}
+  PCF_HD int block(int g, int k) const { return (g * 5 + k) * Mh * Mh; }  // k: 0 Av 1 Ag 2 Xv 3 Xg 4 Eh
+  PCF_HD int per_mode() const { return 10 * Mh * Mh; }
+};
+
 // Shared (N-dependent) coefficient table, doubles, each array of length Mh:
 //   for par: ra, rb, rc (tau right-hand-side combination), nsq (n^2 of the class
 //   element), two_n (2 n of the class element)
@@ -77,6 +91,7 @@ struct Inst {
   const double2* twx; // e^{-2 pi i k/nx}, k < nx
   const double2* twz; // e^{-2 pi i k/nz}, k < nz
   const double* tab[2];  // per-mode solver tables: [0] sigma = 1/(nu dt), [1] sigma = 1/(nu dtau_hat)
+  const double* dense[2];  // per-mode dense solve operators (DenseLayout) or null
   double sigma[2];
   // buffers (device), uhat layout unless noted
   double2* uhat;

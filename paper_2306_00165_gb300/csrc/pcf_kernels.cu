@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
   for (int t = threadIdx.x; t < CL.total(); t += blockDim.x) cheb[t] = I.cheb[t];
   for (int t = threadIdx.x; t < RL.total(); t += blockDim.x) rco[t] = I.rco[t];
   const double* tabg = solve ? I.tab[sig] : nullptr;
-  if (solve)
+  if (solve && !I.dense[sig])
     for (int t = threadIdx.x; t < nmod * PM; t += blockDim.x) tabs[t] = tabg[(size_t)m0 * PM + t];
 
   // state coefficients of the input (u for PHI/SYNTH, r1 for PSI, rhs for SOLVE), class-split
@@ -487,26 +487,92 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
     }
     __syncthreads();
 
-    // Stokes step: 4 chains per mode (group x part)
     const double sigma = I.sigma[sig];
-    for (int t = threadIdx.x; t < nmod * 4; t += blockDim.x) {
-      const int mm = t >> 2, g = (t >> 1) & 1, rho = t & 1;
-      const int m = m0 + mm, i = m / Mz, p = m - i * Mz;
-      const double kx = I.kx[i], kz = I.kz[p];
-      const double k2 = kx * kx + kz * kz;
-      const double* tab = tabs + (size_t)mm * PM;
-      const double* fr = Fr + (size_t)mm * 6 * L2;
-      double* sc = Ch + ((size_t)mm * 4 + g * 2 + rho) * 6 * Mh;
-      if (k2 == 0.0) {
-        // mean mode: v = 0, Dirichlet Helmholtz problems for u and w (class g, part rho)
-        const int Mc = (N - g) / 2 + 1;
-        const double* s = tab + TL.solver(1, g);
-        for (int c = 0; c < 3; c += 2) {
-          tau_solve(Mc, s, s + Mh, s + 2 * Mh, s + 3 * Mh, s[4 * Mh], rco + RL.off(g, 0), rco + RL.off(g, 1),
-                    rco + RL.off(g, 2), fr + (c * 2 + rho) * L2 + g * Mh, 0.0, sc + (c == 0 ? 0 : Mh));
+    const double* dn = I.dense[sig];
+    if (dn) {
+      // Stokes step with the dense per-mode operators: inputs g, h per (mode, group, part)
+      const DenseLayout DL(N);
+      for (int t = threadIdx.x; t < nmod * 4 * Mh; t += blockDim.x) {
+        const int i = t % Mh, c4 = t / Mh, mm = c4 >> 2, g = (c4 >> 1) & 1, rho = c4 & 1;
+        const int pP = 1 - g, McP = (N - pP) / 2 + 1;
+        const int m = m0 + mm, ix = m / Mz, p = m - ix * Mz;
+        const double kx = I.kx[ix], kz = I.kz[p];
+        if (i >= McP || (kx == 0.0 && kz == 0.0)) continue;
+        const double* fr = Fr + (size_t)mm * 6 * L2;
+        const double fu = fr[(0 * 2 + (1 - rho)) * L2 + pP * Mh + i];
+        const double fw = fr[(2 * 2 + (1 - rho)) * L2 + pP * Mh + i];
+        const double sgn = rho == 0 ? -1.0 : 1.0;
+        double* sc = Ch + ((size_t)mm * 4 + g * 2 + rho) * 6 * Mh;
+        sc[i] = sgn * fma(kx, fu, kz * fw);
+        sc[Mh + i] = sgn * fma(kz, fu, -kx * fw);
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < nmod * 4 * 3 * Mh; t += blockDim.x) {
+        const int r = t % Mh, q = t / Mh, which = q % 3, c4 = q / 3, mm = c4 >> 2, g = (c4 >> 1) & 1,
+                  rho = c4 & 1;
+        const int pv = g, pP = 1 - g, McV = (N - pv) / 2 + 1, McP = (N - pP) / 2 + 1;
+        const int m = m0 + mm, ix = m / Mz, p = m - ix * Mz;
+        const double kx = I.kx[ix], kz = I.kz[p];
+        const double* D = dn + (size_t)m * DL.per_mode();
+        const double* fr = Fr + (size_t)mm * 6 * L2;
+        double* sc = Ch + ((size_t)mm * 4 + g * 2 + rho) * 6 * Mh;
+        if (kx == 0.0 && kz == 0.0) {
+          // mean mode: u (which 0) and w (which 1) of class g
+          const int Mc = (N - g) / 2 + 1;
+          if (which == 2 || r >= Mc) continue;
+          const double* row = D + DL.block(g, 4) + r * Mh;
+          const double* f = fr + ((which == 0 ? 0 : 2) * 2 + rho) * L2 + g * Mh;
+          double a = 0.0;
+          for (int j = 0; j < Mc; ++j) a = fma(__ldg(row + j), f[j], a);
+          sc[(which == 0 ? 0 : Mh) + r] = a;
+          continue;
         }
-      } else {
-        mode_chain(N, g, rho, kx, kz, sigma + k2, tab, rco, fr, L2, sc);
+        const double* fv = fr + (1 * 2 + rho) * L2 + pv * Mh;
+        if (which == 0) {
+          if (r >= McV) continue;
+          const double* ra = D + DL.block(g, 0) + r * Mh;
+          const double* rg = D + DL.block(g, 1) + r * Mh;
+          double a = 0.0;
+          for (int j = 0; j < McV; ++j) a = fma(__ldg(ra + j), fv[j], a);
+          for (int j = 0; j < McP; ++j) a = fma(__ldg(rg + j), sc[j], a);
+          sc[2 * Mh + r] = a;
+        } else if (which == 1) {
+          if (r >= McP) continue;
+          const double* ra = D + DL.block(g, 2) + r * Mh;
+          const double* rg = D + DL.block(g, 3) + r * Mh;
+          double a = 0.0;
+          for (int j = 0; j < McV; ++j) a = fma(__ldg(ra + j), fv[j], a);
+          for (int j = 0; j < McP; ++j) a = fma(__ldg(rg + j), sc[j], a);
+          sc[3 * Mh + r] = a;
+        } else {
+          if (r >= McP) continue;
+          const double* re = D + DL.block(g, 4) + r * Mh;
+          double a = 0.0;
+          for (int j = 0; j < McP; ++j) a = fma(__ldg(re + j), sc[Mh + j], a);
+          sc[4 * Mh + r] = a;
+        }
+      }
+    } else {
+    // Stokes step: 4 chains per mode (group x part)
+      for (int t = threadIdx.x; t < nmod * 4; t += blockDim.x) {
+        const int mm = t >> 2, g = (t >> 1) & 1, rho = t & 1;
+        const int m = m0 + mm, i = m / Mz, p = m - i * Mz;
+        const double kx = I.kx[i], kz = I.kz[p];
+        const double k2 = kx * kx + kz * kz;
+        const double* tab = tabs + (size_t)mm * PM;
+        const double* fr = Fr + (size_t)mm * 6 * L2;
+        double* sc = Ch + ((size_t)mm * 4 + g * 2 + rho) * 6 * Mh;
+        if (k2 == 0.0) {
+          // mean mode: v = 0, Dirichlet Helmholtz problems for u and w (class g, part rho)
+          const int Mc = (N - g) / 2 + 1;
+          const double* s = tab + TL.solver(1, g);
+          for (int c = 0; c < 3; c += 2) {
+            tau_solve(Mc, s, s + Mh, s + 2 * Mh, s + 3 * Mh, s[4 * Mh], rco + RL.off(g, 0), rco + RL.off(g, 1),
+                      rco + RL.off(g, 2), fr + (c * 2 + rho) * L2 + g * Mh, 0.0, sc + (c == 0 ? 0 : Mh));
+          }
+        } else {
+          mode_chain(N, g, rho, kx, kz, sigma + k2, tab, rco, fr, L2, sc);
+        }
       }
     }
     __syncthreads();

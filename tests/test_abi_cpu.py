@@ -50,7 +50,7 @@ def test_host_only_queries(lib):
 def test_create_rejects_bad_params_without_gpu(lib):
     import paper_2306_00165_gb300 as pcf
     pcf.load_library()
-    p = pcf._Params(32, 32, 32, 1, 1.0, 1.0, 400.0, 0.25, 0.25, 0, 0, (ctypes.c_int * 2)(0, 0))
+    p = pcf._Params(32, 32, 32, 1, 1.0, 1.0, 400.0, 0.25, 0.25, 0, 0, 0, 0)
     h = ctypes.c_void_p()
     assert pcf._lib.pcf_create(ctypes.byref(p), None, ctypes.byref(h)) == 1   # PCF_EINVAL, before any CUDA call
     assert not h.value

@@ -26,7 +26,7 @@ def _rhs(o, seed):
 
 
 def _params(pcf, grid, batch=1, step=0.25):
-    return pcf._Params(*grid, batch, pcf.LX_PAPER, pcf.LZ_PAPER, 400.0, step, step, 0, 0, (ctypes.c_int * 2)(0, 0))
+    return pcf._Params(*grid, batch, pcf.LX_PAPER, pcf.LZ_PAPER, 400.0, step, step, 0, 0, 0, 0)
 
 
 def test_noalloc_matches_context_solve_two_calls():
