@@ -12,6 +12,7 @@ struct pcf_ctx {
   std::vector<long long> state_off;  // complex offset of each instance's state, [B+1]
   long long total_state = 0;
   bool uniform = true;   // every instance on the same problem
+  bool mixed = false;    // mixed-precision form (FP32 planes, split-BF16 Chebyshev, FP64 solves)
   double tuned_ms = 0.0; // autotuner: time of the chosen mode-kernel launch
   cudaStream_t user = nullptr, cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -24,8 +25,10 @@ struct pcf_ctx {
   int* pre_prod = nullptr;
   int* pre_mode = nullptr;
   int* pre_inst = nullptr;
-  int cta_synth11 = 0, cta_synth3 = 0, cta_prod = 0, cta_mode = 0;
-  size_t sm_synth = 0, sm_prod = 0, sm_mode = 0;
+  int* pre_tcs = nullptr;   // tensor-core synthesis (mixed form)
+  int* pre_tca = nullptr;   // tensor-core analysis (mixed form)
+  int cta_synth11 = 0, cta_synth3 = 0, cta_prod = 0, cta_mode = 0, cta_tcs = 0, cta_tca = 0;
+  size_t sm_synth = 0, sm_prod = 0, sm_mode = 0, sm_tc = 0;
   double2* r_int = nullptr;    // internal r1 buffer for descent
   double2* u_dev = nullptr;    // device state for the *_host entry point
   double* hist_dev = nullptr;

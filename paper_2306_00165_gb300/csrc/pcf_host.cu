@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <thread>
 #include <vector>
 
 #include "pcf_kernels.cuh"
@@ -223,8 +224,9 @@ std::vector<double> make_dense_tables(int N, const std::vector<double>& kx, cons
   const DenseLayout DL(N);
   const int Mx = (int)kx.size(), Mz = (int)kz.size(), Mh = N / 2 + 1, L2 = 2 * Mh;
   std::vector<double> out((size_t)Mx * Mz * DL.per_mode(), 0.0);
+  auto work = [&](int i0, int i1) {
   std::vector<double> Fr(6 * L2), sc(6 * Mh);
-  for (int i = 0; i < Mx; ++i)
+  for (int i = i0; i < i1; ++i)
     for (int p = 0; p < Mz; ++p) {
       const size_t m = (size_t)i * Mz + p;
       const double* tab = tabs.data() + m * TL.per_mode();
@@ -277,6 +279,12 @@ std::vector<double> make_dense_tables(int N, const std::vector<double>& kx, cons
         }
       }
     }
+  };
+  // x-mode rows are independent: split them over host threads
+  const int nt = std::max(1, std::min<int>(Mx, (int)std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t) pool.emplace_back(work, Mx * t / nt, Mx * (t + 1) / nt);
+  for (auto& th : pool) th.join();
   return out;
 }
 
@@ -289,6 +297,46 @@ std::vector<double> make_ccw(int N) {
     w[j] = s;
   }
   return w;
+}
+
+uint16_t f2bf(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+float bf2f(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+}
+
+// Split-BF16 copies of the full Chebyshev matrices for the tensor-core transforms:
+// [C hi, C lo, C' hi, C' lo, Cinv hi, Cinv lo], each P x P row-major, zero padded.
+std::vector<uint16_t> make_tc_matrices(int N) {
+  const int ny = N + 1, P = (ny + 15) & ~15;
+  std::vector<uint16_t> t((size_t)6 * P * P, 0);
+  auto put = [&](int mat, int r, int c, double v) {
+    const float f = (float)v;
+    const uint16_t hi = f2bf(f);
+    t[((size_t)2 * mat) * P * P + (size_t)r * P + c] = hi;
+    t[((size_t)2 * mat + 1) * P * P + (size_t)r * P + c] = f2bf(f - bf2f(hi));
+  };
+  for (int j = 0; j < ny; ++j)
+    for (int n = 0; n < ny; ++n) {
+      put(0, j, n, cospi_frac((long long)j * n, N));
+      put(1, j, n, cheb_dvalue(n, j, N));
+      put(2, n, j, cinv(n, j, N));
+    }
+  return t;
+}
+
+std::vector<float2> to_float2(const std::vector<double2>& v) {
+  std::vector<float2> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = make_float2((float)v[i].x, (float)v[i].y);
+  return o;
 }
 
 std::vector<double2> make_twiddles(int L) {
@@ -359,13 +407,25 @@ pcf_status launch_synth(pcf_ctx* c, int slot, int nf) {
   const int* pre = nf == kFieldsSynth ? c->pre_synth11 : c->pre_synth3;
   const int ctas = nf == kFieldsSynth ? c->cta_synth11 : c->cta_synth3;
   return timed(c, slot == 0 ? 1 : 4,
-               [&] { k_xzsynth<<<ctas, 128, c->sm_synth, c->cs>>>(li_of(c, pre), slot, nf); });
+               [&] { launch_xzsynth(c->mixed, ctas, c->sm_synth, c->cs, li_of(c, pre), slot, nf); });
 }
 pcf_status launch_prodM(pcf_ctx* c) {
-  return timed(c, 2, [&] { k_prod_M<<<c->cta_prod, 128, c->sm_prod, c->cs>>>(li_of(c, c->pre_prod)); });
+  return timed(c, 2, [&] { launch_prod(c->mixed, false, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod)); });
 }
 pcf_status launch_prodN(pcf_ctx* c) {
-  return timed(c, 5, [&] { k_prod_N<<<c->cta_prod, 128, c->sm_prod, c->cs>>>(li_of(c, c->pre_prod)); });
+  return timed(c, 5, [&] { launch_prod(c->mixed, true, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod)); });
+}
+
+pcf_status launch_tc_synth(pcf_ctx* c, int slot) {
+  return timed(c, 0, [&] { launch_cheb_synth_tc(c->cta_tcs, c->sm_tc, c->cs, li_of(c, c->pre_tcs), slot); });
+}
+pcf_status launch_tc_analysis(pcf_ctx* c) {
+  return timed(c, 0, [&] { launch_cheb_analysis_tc(c->cta_tca, c->sm_tc, c->cs, li_of(c, c->pre_tca)); });
+}
+// y-synthesis of the state (slot 0) or of r1 (slot 1) in either form
+pcf_status launch_ysynth(pcf_ctx* c, int slot) {
+  if (c->mixed) return launch_tc_synth(c, slot);
+  return launch_mode(c, MODE_SYNTH_ONLY, slot, 0);
 }
 
 pcf_status check_launch() {
@@ -403,6 +463,19 @@ void set_pointers(pcf_ctx* c, const double* u, const double* r, double* f) {
 }
 
 pcf_status step_body(pcf_ctx* c, int s) {
+  if (c->mixed) {
+    if (s > 0) PCF_TRY(launch_tc_synth(c, 0));
+    PCF_TRY(launch_synth(c, 0, kFieldsSynth));
+    PCF_TRY(launch_prodM(c));
+    PCF_TRY(launch_tc_analysis(c));
+    PCF_TRY(launch_mode(c, MODE_PHI, 0, s));
+    PCF_TRY(launch_tc_synth(c, 1));
+    PCF_TRY(launch_synth(c, 1, kFieldsSynth));
+    PCF_TRY(launch_prodN(c));
+    PCF_TRY(launch_tc_analysis(c));
+    PCF_TRY(launch_mode(c, MODE_PSI_UPDATE, 1, s));
+    return PCF_OK;
+  }
   PCF_TRY(launch_synth(c, 0, kFieldsSynth));
   PCF_TRY(launch_prodM(c));
   PCF_TRY(launch_mode(c, MODE_PHI, 0, s));
@@ -455,6 +528,8 @@ static bool params_ok(const pcf_params* prm) {
 struct GridTables {
   double *cheb, *rco, *ccw, *kx, *kz, *y, *tab0, *tab1, *dense0, *dense1;
   double2 *twx, *twz;
+  float2 *twxf = nullptr, *twzf = nullptr;
+  uint16_t* tcA = nullptr;
   double sig[2];
 };
 
@@ -485,6 +560,14 @@ static pcf_status build_tables(pcf_ctx* c, const pcf_params* prm, GridTables* g)
     tab1 = make_mode_tables(N, kx, kz, g->sig[1], rco);
     if (upload(tab1, &g->tab1)) return PCF_ECUDA;
     c->allocs.push_back(g->tab1);
+  }
+  if (prm->precision == PCF_MIXED) {
+    if (upload(to_float2(twx), &g->twxf) || upload(to_float2(twz), &g->twzf) ||
+        upload(make_tc_matrices(N), &g->tcA))
+      return PCF_ECUDA;
+    c->allocs.push_back(g->twxf);
+    c->allocs.push_back(g->twzf);
+    c->allocs.push_back(g->tcA);
   }
   g->dense0 = g->dense1 = nullptr;
   const bool dense = N <= kDenseMaxN && prm->solve_kind != 1;
@@ -577,7 +660,9 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
   int B = 0;
   for (int k = 0; k < nlist; ++k) {
     if (!params_ok(&list[k])) return PCF_EINVAL;
-    if (list[k].precision != PCF_FP64) return PCF_ENOTSUP;
+    if (list[k].precision != PCF_FP64 && list[k].precision != PCF_MIXED) return PCF_ENOTSUP;
+    if (list[k].precision != list[0].precision) return PCF_EINVAL;
+    if (list[k].precision == PCF_MIXED && list[k].ny > 113) return PCF_ENOTSUP;
     B += list[k].batch;
   }
   pcf_ctx* c = new pcf_ctx();
@@ -592,6 +677,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
   c->B = B;
   c->state_len = 3LL * c->nm * list[0].ny;
   c->user = (cudaStream_t)stream;
+  c->mixed = list[0].precision == PCF_MIXED;
   auto fail = [&](pcf_status s) {
     pcf_destroy(c);
     return s;
@@ -642,13 +728,20 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       }
   }
   c->total_state = c->state_off[B];
-  double2 *yv, *xz;
-  double *ph, *np;
-  if (ctx_alloc(c, &yv, n_yv) || ctx_alloc(c, &ph, n_ph) || ctx_alloc(c, &xz, n_xz) || ctx_alloc(c, &np, n_np) ||
-      ctx_alloc(c, &c->r_int, (size_t)c->total_state) || ctx_alloc(c, &c->active, (size_t)B))
+  double2 *yv = nullptr, *xz = nullptr;
+  double *ph = nullptr, *np = nullptr;
+  float2 *yvf = nullptr, *xzf = nullptr, *xzc = nullptr;
+  float* phf = nullptr;
+  if (ctx_alloc(c, &np, n_np) || ctx_alloc(c, &c->r_int, (size_t)c->total_state) || ctx_alloc(c, &c->active, (size_t)B))
     return fail(PCF_ENOMEM);
+  if (c->mixed) {
+    if (ctx_alloc(c, &yvf, n_yv) || ctx_alloc(c, &phf, n_ph) || ctx_alloc(c, &xzf, n_xz) || ctx_alloc(c, &xzc, n_xz))
+      return fail(PCF_ENOMEM);
+  } else {
+    if (ctx_alloc(c, &yv, n_yv) || ctx_alloc(c, &ph, n_ph) || ctx_alloc(c, &xz, n_xz)) return fail(PCF_ENOMEM);
+  }
   c->hinst.resize(B);
-  std::vector<int> per11(B), per3(B), per1(B, 1);
+  std::vector<int> per11(B), per3(B), per1(B, 1), per_tcs(B), per_tca(B);
   size_t o_yv = 0, o_ph = 0, o_xz = 0, o_np = 0;
   int b = 0;
   for (int k = 0; k < nlist; ++k)
@@ -669,7 +762,13 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       I.tab[0] = g.tab0; I.tab[1] = g.tab1;
       I.dense[0] = g.dense0; I.dense[1] = g.dense1;
       I.sigma[0] = g.sig[0]; I.sigma[1] = g.sig[1];
-      I.yv = yv + o_yv; I.phys = ph + o_ph; I.xz = xz + o_xz; I.normpart = np + o_np;
+      I.normpart = np + o_np;
+      if (c->mixed) {
+        I.yvf = yvf + o_yv; I.physf = phf + o_ph; I.xzf = xzf + o_xz; I.xzc = xzc + o_xz;
+        I.twxf = g.twxf; I.twzf = g.twzf; I.tcA = g.tcA; I.mixed = 1;
+      } else {
+        I.yv = yv + o_yv; I.phys = ph + o_ph; I.xz = xz + o_xz;
+      }
       o_yv += 2ULL * kFieldsY * p.ny * I.nmodes;
       o_ph += 2ULL * kFieldsSynth * p.ny * p.nx * p.nz;
       o_xz += 3ULL * p.ny * I.nmodes;
@@ -677,8 +776,12 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       I.hist_stride = B;
       per11[b] = kFieldsSynth * p.ny;
       per3[b] = 3 * p.ny;
-      c->sm_synth = std::max(c->sm_synth, smem_xzsynth(I));
-      c->sm_prod = std::max(c->sm_prod, smem_prod(I));
+      per_tcs[b] = kFieldsY * cheb_tc_tiles(I.nmodes);
+      per_tca[b] = 3 * cheb_tc_tiles(I.nmodes);
+      const int elem = c->mixed ? (int)sizeof(float2) : (int)sizeof(double2);
+      c->sm_synth = std::max(c->sm_synth, smem_plane(I, elem));
+      c->sm_prod = std::max(c->sm_prod, smem_plane(I, elem));
+      if (c->mixed) c->sm_tc = std::max(c->sm_tc, smem_cheb_tc(p.ny));
     }
   if (ctx_alloc(c, &c->dinst, (size_t)B)) return fail(PCF_ENOMEM);
   int dummy;
@@ -686,11 +789,12 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
   if ((st = upload_prefix(c, per11, &c->pre_synth11, &c->cta_synth11)) != PCF_OK ||
       (st = upload_prefix(c, per3, &c->pre_synth3, &c->cta_synth3)) != PCF_OK ||
       (st = upload_prefix(c, per3, &c->pre_prod, &c->cta_prod)) != PCF_OK ||
-      (st = upload_prefix(c, per1, &c->pre_inst, &dummy)) != PCF_OK)
+      (st = upload_prefix(c, per1, &c->pre_inst, &dummy)) != PCF_OK ||
+      (st = upload_prefix(c, per_tcs, &c->pre_tcs, &c->cta_tcs)) != PCF_OK ||
+      (st = upload_prefix(c, per_tca, &c->pre_tca, &c->cta_tca)) != PCF_OK)
     return fail(st);
-  if (cudaFuncSetAttribute(k_xzsynth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->sm_synth) ||
-      cudaFuncSetAttribute(k_prod_M, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->sm_prod) ||
-      cudaFuncSetAttribute(k_prod_N, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->sm_prod))
+  if (c->mixed && set_cheb_tc_smem(c->sm_tc)) return fail(PCF_ECUDA);
+  if (set_plane_smem(c->mixed, c->sm_synth, c->sm_prod))
     return fail(PCF_ECUDA);
   const int want = list[0].modes_per_block;
   st = want > 0 ? set_mode_tiles(c, want) : autotune_tiles(c);
@@ -734,13 +838,15 @@ pcf_status pcf_residual(pcf_ctx* c, const double* u, double* r, double* rnorm) {
   set_pointers(c, u, r, nullptr);
   PCF_TRY(enter(c));
   PCF_TRY(push_descriptors(c));
-  PCF_TRY(launch_mode(c, MODE_SYNTH_ONLY, 0, 0));
+  PCF_TRY(launch_ysynth(c, 0));
   PCF_TRY(launch_synth(c, 0, kFieldsSynth));
   PCF_TRY(launch_prodM(c));
+  if (c->mixed) PCF_TRY(launch_tc_analysis(c));
   PCF_TRY(launch_mode(c, MODE_PHI, 0, 0));
   if (rnorm) {
+    if (c->mixed) PCF_TRY(launch_tc_synth(c, 1));
     PCF_TRY(launch_synth(c, 1, 3));
-    k_norm_planes<<<c->cta_synth3, 128, 0, c->cs>>>(li_of(c, c->pre_synth3));
+    launch_norm_planes(c->mixed, c->cta_synth3, c->cs, li_of(c, c->pre_synth3));
     k_norm_final<<<1, 32, 0, c->cs>>>(li_of(c, c->pre_inst), rnorm);
   }
   PCF_TRY(check_launch());
@@ -752,11 +858,12 @@ pcf_status pcf_adjoint_gradient(pcf_ctx* c, const double* u, const double* r, do
   set_pointers(c, u, r, f);
   PCF_TRY(enter(c));
   PCF_TRY(push_descriptors(c));
-  PCF_TRY(launch_mode(c, MODE_SYNTH_ONLY, 0, 0));
-  PCF_TRY(launch_mode(c, MODE_SYNTH_ONLY, 1, 0));
+  PCF_TRY(launch_ysynth(c, 0));
+  PCF_TRY(launch_ysynth(c, 1));
   PCF_TRY(launch_synth(c, 0, kFieldsSynth));
   PCF_TRY(launch_synth(c, 1, kFieldsSynth));
   PCF_TRY(launch_prodN(c));
+  if (c->mixed) PCF_TRY(launch_tc_analysis(c));
   PCF_TRY(launch_mode(c, MODE_PSI_GRAD, 1, 0));
   PCF_TRY(check_launch());
   return leave(c);
@@ -791,7 +898,7 @@ static pcf_status descent_internal(pcf_ctx* c, double* u, double dtau, int nstep
   PCF_TRY(enter(c));
   PCF_TRY(push_descriptors(c));
   if (c->timing) {
-    PCF_TRY(launch_mode(c, MODE_SYNTH_ONLY, 0, 0));
+    PCF_TRY(launch_ysynth(c, 0));
     for (int s = 0; s < nsteps; ++s) PCF_TRY(step_body(c, s));
     PCF_TRY(check_launch());
     return leave(c);
@@ -800,7 +907,7 @@ static pcf_status descent_internal(pcf_ctx* c, double* u, double dtau, int nstep
   if (it == c->graphs.end()) {
     cudaGraph_t g;
     PCF_CUDA(cudaStreamBeginCapture(c->cs, cudaStreamCaptureModeThreadLocal));
-    pcf_status st = launch_mode(c, MODE_SYNTH_ONLY, 0, 0);
+    pcf_status st = launch_ysynth(c, 0);
     for (int s = 0; s < nsteps && st == PCF_OK; ++s) st = step_body(c, s);
     cudaError_t e = cudaStreamEndCapture(c->cs, &g);
     if (st != PCF_OK) return st;
@@ -937,7 +1044,7 @@ pcf_status pcf_kernel_times(pcf_ctx* c, double* ms, long long* launches, int n) 
   return PCF_OK;
 }
 
-int pcf_launches_per_step(pcf_ctx* c) { return c ? 6 : 0; }
+int pcf_launches_per_step(pcf_ctx* c) { return c ? (c->mixed ? 10 : 6) : 0; }
 
 pcf_status pcf_probe_fp64_peak(void* stream, double* gflops) {
   if (!gflops) return PCF_EINVAL;

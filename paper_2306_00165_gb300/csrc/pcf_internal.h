@@ -37,7 +37,7 @@ struct TabLayout {
 // with f_v the v right-hand side (class g), g = Re/Im part of i(kx f_u + kz f_w) and
 // h = Re/Im part of i(kz f_u - kx f_w) (class 1-g).  For the mean mode, Eh of group g is
 // the inverse Dirichlet Helmholtz operator of class g (applied to f_u and f_w).
-constexpr int kDenseMaxN = 64;
+constexpr int kDenseMaxN = 128;
 struct DenseLayout {
   int Mh;
   PCF_HD DenseLayout(int N) : Mh(N / 2 + 1) {}
@@ -90,6 +90,8 @@ struct Inst {
   const double* kz;   // [Mz]
   const double2* twx; // e^{-2 pi i k/nx}, k < nx
   const double2* twz; // e^{-2 pi i k/nz}, k < nz
+  const float2* twxf; // FP32 copies for the mixed-precision form
+  const float2* twzf;
   const double* tab[2];  // per-mode solver tables: [0] sigma = 1/(nu dt), [1] sigma = 1/(nu dtau_hat)
   const double* dense[2];  // per-mode dense solve operators (DenseLayout) or null
   double sigma[2];
@@ -101,6 +103,13 @@ struct Inst {
   double* phys;       // [2][11][ny][nx][nz]: slot 0 for u, slot 1 for q
   double2* xz;        // [3][ny][Mx][Mz]
   double* normpart;   // [3][ny]
+  // mixed-precision form: FP32 plane data and Chebyshev coefficients of the products
+  float* physf;       // [2][11][ny][nx][nz]
+  float2* yvf;        // [2][5][ny][Mx][Mz]
+  float2* xzf;        // [3][ny][Mx][Mz]
+  float2* xzc;        // [3][ny][Mx][Mz]: Chebyshev coefficients of xzf (n in place of j)
+  int mixed;          // 1: the mode kernel reads xzc and leaves the synthesis to the tensor-core kernel
+  const void* tcA;    // bf16 [6][P][P], P = ny rounded up to 16: C hi/lo, C' hi/lo, Cinv hi/lo
   double* hist;       // J history base (may be null)
   int hist_stride;
   int* active;        // 1 = keep updating

@@ -18,15 +18,6 @@
 namespace pcf {
 
 // ------------------------------------------------------------------ helpers
-__device__ __forceinline__ int find_inst(const LaunchInfo& li, int cta, int* local) {
-  int lo = 0, hi = li.ninst - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (li.prefix[mid] <= cta) lo = mid; else hi = mid - 1;
-  }
-  *local = cta - li.prefix[lo];
-  return lo;
-}
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
@@ -37,47 +28,99 @@ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_doub
 // x-storage index i (m = i for i <= Kx, m = i - Mx otherwise) -> FFT bin
 __device__ __forceinline__ int xbin(int i, int Kx, int Mx, int nx) { return i <= Kx ? i : nx - (Mx - i); }
 
+// ------------------------------------------------------------------ complex helpers (FP64 / FP32)
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+template <class T> struct Cx;
+template <> struct Cx<double> {
+  using c = double2;
+  static __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+};
+template <> struct Cx<float> {
+  using c = float2;
+  static __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+};
+
+// typed views of an instance's plane buffers and twiddles
+template <class T> __device__ __forceinline__ T* phys_of(const Inst& I);
+template <> __device__ __forceinline__ double* phys_of<double>(const Inst& I) { return I.phys; }
+template <> __device__ __forceinline__ float* phys_of<float>(const Inst& I) { return I.physf; }
+template <class T> __device__ __forceinline__ const typename Cx<T>::c* yv_of(const Inst& I);
+template <> __device__ __forceinline__ const double2* yv_of<double>(const Inst& I) { return I.yv; }
+template <> __device__ __forceinline__ const float2* yv_of<float>(const Inst& I) { return I.yvf; }
+template <class T> __device__ __forceinline__ typename Cx<T>::c* xz_of(const Inst& I);
+template <> __device__ __forceinline__ double2* xz_of<double>(const Inst& I) { return I.xz; }
+template <> __device__ __forceinline__ float2* xz_of<float>(const Inst& I) { return I.xzf; }
+template <class T> __device__ __forceinline__ const typename Cx<T>::c* twx_of(const Inst& I);
+template <> __device__ __forceinline__ const double2* twx_of<double>(const Inst& I) { return I.twx; }
+template <> __device__ __forceinline__ const float2* twx_of<float>(const Inst& I) { return I.twxf; }
+template <class T> __device__ __forceinline__ const typename Cx<T>::c* twz_of(const Inst& I);
+template <> __device__ __forceinline__ const double2* twz_of<double>(const Inst& I) { return I.twz; }
+template <> __device__ __forceinline__ const float2* twz_of<float>(const Inst& I) { return I.twzf; }
+
 // ------------------------------------------------------------------ Stockham FFT in shared memory
-template <int R>
-__device__ __forceinline__ void butterfly(double2* v, bool inv);
+template <int R, class C>
+__device__ __forceinline__ void butterfly(C* v, bool inv);
 
 template <>
-__device__ __forceinline__ void butterfly<2>(double2* v, bool) {
+__device__ __forceinline__ void butterfly<2, double2>(double2* v, bool) {
   const double2 a = v[0], b = v[1];
   v[0] = cadd(a, b);
   v[1] = csub(a, b);
 }
-
 template <>
-__device__ __forceinline__ void butterfly<4>(double2* v, bool inv) {
-  const double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-  const double2 t2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+__device__ __forceinline__ void butterfly<2, float2>(float2* v, bool) {
+  const float2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <int R, class C>
+__device__ __forceinline__ void butterfly4(C* v, bool inv) {
+  const C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+  const C t2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
   // t3 = -i d (forward) or +i d (inverse)
-  const double2 t3 = inv ? make_double2(-d.y, d.x) : make_double2(d.y, -d.x);
+  C t3;
+  if (inv) { t3.x = -d.y; t3.y = d.x; } else { t3.x = d.y; t3.y = -d.x; }
   v[0] = cadd(t0, t2);
   v[2] = csub(t0, t2);
   v[1] = cadd(t1, t3);
   v[3] = csub(t1, t3);
 }
-
 template <>
-__device__ __forceinline__ void butterfly<3>(double2* v, bool inv) {
-  const double h = 0.86602540378443864676;  // sin(2 pi/3)
-  const double2 s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
-  const double2 y0 = cadd(v[0], s);
-  const double2 m = make_double2(fma(-0.5, s.x, v[0].x), fma(-0.5, s.y, v[0].y));
-  const double2 t = make_double2(h * d.x, h * d.y);
-  // forward: y1 = m - i t, y2 = m + i t
-  const double2 it = make_double2(-t.y, t.x);
+__device__ __forceinline__ void butterfly<4, double2>(double2* v, bool inv) { butterfly4<4, double2>(v, inv); }
+template <>
+__device__ __forceinline__ void butterfly<4, float2>(float2* v, bool inv) { butterfly4<4, float2>(v, inv); }
+
+template <class C>
+__device__ __forceinline__ void butterfly3(C* v, bool inv) {
+  using R = decltype(v[0].x);
+  const R h = (R)0.86602540378443864676;  // sin(2 pi/3)
+  const C s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+  const C y0 = cadd(v[0], s);
+  C m, it;
+  m.x = fma((R)-0.5, s.x, v[0].x);
+  m.y = fma((R)-0.5, s.y, v[0].y);
+  // forward: y1 = m - i t, y2 = m + i t with t = h d
+  it.x = -h * d.y;
+  it.y = h * d.x;
   v[0] = y0;
   v[1] = inv ? cadd(m, it) : csub(m, it);
   v[2] = inv ? csub(m, it) : cadd(m, it);
 }
+template <>
+__device__ __forceinline__ void butterfly<3, double2>(double2* v, bool inv) { butterfly3(v, inv); }
+template <>
+__device__ __forceinline__ void butterfly<3, float2>(float2* v, bool inv) { butterfly3(v, inv); }
 
 // One radix-R pass over nb contiguous batches of length L (Stockham autosort).
-template <int R>
-__device__ __forceinline__ void stockham_pass(const double2* __restrict__ a, double2* __restrict__ b, int L, int nb,
-                                              int Ns, const double2* __restrict__ tw, bool inv) {
+template <int R, class C>
+__device__ __forceinline__ void stockham_pass(const C* __restrict__ a, C* __restrict__ b, int L, int nb, int Ns,
+                                              const C* __restrict__ tw, bool inv) {
   const int nq = L / R;
   const int total = nq * nb;
   const int twstep = L / (Ns * R);
@@ -85,37 +128,37 @@ __device__ __forceinline__ void stockham_pass(const double2* __restrict__ a, dou
     const int bi = t / nq;
     const int j = t - bi * nq;
     const int k = j % Ns;
-    const double2* ab = a + bi * L;
-    double2 v[R];
+    const C* ab = a + bi * L;
+    C v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = ab[j + r * nq];
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        double2 w = tw[r * k * twstep];
+        C w = tw[r * k * twstep];
         if (inv) w.y = -w.y;
         v[r] = cmul(v[r], w);
       }
     }
-    butterfly<R>(v, inv);
+    butterfly<R, C>(v, inv);
     const int idx = (j / Ns) * Ns * R + k;
-    double2* bb = b + bi * L;
+    C* bb = b + bi * L;
 #pragma unroll
     for (int r = 0; r < R; ++r) bb[idx + r * Ns] = v[r];
   }
 }
 
 // Full transform of nb batches; a holds the input; returns the buffer with the result.
-__device__ double2* fft_run(double2* a, double2* b, int L, int nb, const int* radix, int nr, const double2* tw,
-                            bool inv) {
+template <class C>
+__device__ C* fft_run(C* a, C* b, int L, int nb, const int* radix, int nr, const C* tw, bool inv) {
   int Ns = 1;
   for (int s = 0; s < nr; ++s) {
     const int R = radix[s];
-    if (R == 4) stockham_pass<4>(a, b, L, nb, Ns, tw, inv);
-    else if (R == 2) stockham_pass<2>(a, b, L, nb, Ns, tw, inv);
-    else stockham_pass<3>(a, b, L, nb, Ns, tw, inv);
+    if (R == 4) stockham_pass<4, C>(a, b, L, nb, Ns, tw, inv);
+    else if (R == 2) stockham_pass<2, C>(a, b, L, nb, Ns, tw, inv);
+    else stockham_pass<3, C>(a, b, L, nb, Ns, tw, inv);
     __syncthreads();
-    double2* t = a;
+    C* t = a;
     a = b;
     b = t;
     Ns *= R;
@@ -123,17 +166,39 @@ __device__ double2* fft_run(double2* a, double2* b, int L, int nb, const int* ra
   return a;
 }
 
-__device__ __forceinline__ void load_twiddles(const Inst& I, double2* twx, double2* twz) {
-  for (int t = threadIdx.x; t < I.nx; t += blockDim.x) twx[t] = I.twx[t];
-  for (int t = threadIdx.x; t < I.nz; t += blockDim.x) twz[t] = I.twz[t];
+template <class T>
+__device__ __forceinline__ void load_twiddles(const Inst& I, typename Cx<T>::c* twx, typename Cx<T>::c* twz) {
+  const typename Cx<T>::c* sx = twx_of<T>(I);
+  const typename Cx<T>::c* sz = twz_of<T>(I);
+  for (int t = threadIdx.x; t < I.nx; t += blockDim.x) twx[t] = sx[t];
+  for (int t = threadIdx.x; t < I.nz; t += blockDim.x) twz[t] = sz[t];
 }
 
-__host__ __device__ inline size_t plane_buf_elems(const Inst& I) {
-  const size_t a = (size_t)I.Mz * I.nx, b = (size_t)(I.nx / 2) * I.nz;
-  return a > b ? a : b;
+// Shared-memory plan of a plane transform: two buffers of PB complex values.  The z stage
+// handles `chunk` row pairs at a time: all of them when both stages fit the budget, else
+// as many as fit (two ping-pong buffers) inside the partner of the x-stage buffer.
+struct PlanePlan {
+  int PB, chunk;
+};
+__host__ __device__ inline PlanePlan plane_plan(const Inst& I, int elem) {
+  const int a = I.Mz * I.nx, b = (I.nx / 2) * I.nz;
+  PlanePlan pp;
+  if ((size_t)2 * (a > b ? a : b) * elem <= 100 * 1024) {
+    pp.PB = a > b ? a : b;
+    pp.chunk = I.nx / 2;
+  } else {
+    pp.PB = a;
+    pp.chunk = a / (2 * I.nz);
+    if (pp.chunk < 1) pp.chunk = 1;
+  }
+  return pp;
 }
-size_t smem_xzsynth(const Inst& I) { return sizeof(double2) * (2 * plane_buf_elems(I) + I.nx + I.nz); }
-size_t smem_prod(const Inst& I) { return sizeof(double2) * (2 * plane_buf_elems(I) + I.nx + I.nz) + 8 * 32; }
+size_t smem_plane(const Inst& I, int elem) {
+  const PlanePlan pp = plane_plan(I, elem);
+  return (size_t)elem * (2 * (size_t)pp.PB + I.nx + I.nz) + 8 * 32;
+}
+size_t smem_xzsynth(const Inst& I) { return smem_plane(I, sizeof(double2)); }
+size_t smem_prod(const Inst& I) { return smem_plane(I, sizeof(double2)); }
 
 __device__ __forceinline__ bool inst_active(const Inst& I) { return I.active == nullptr || *I.active != 0; }
 
@@ -143,70 +208,80 @@ __device__ __forceinline__ bool inst_active(const Inst& I) { return I.active == 
 __constant__ int c_src[kFieldsSynth] = {0, 1, 2, 0, 3, 0, 1, 1, 2, 4, 2};
 __constant__ int c_fac[kFieldsSynth] = {0, 0, 0, 1, 0, 2, 1, 2, 1, 0, 2};
 
-__global__ void __launch_bounds__(128) k_xzsynth(LaunchInfo li, int slot, int nfields) {
-  extern __shared__ double2 sm[];
+template <class T>
+__global__ void __launch_bounds__(128) k_xzsynth_t(LaunchInfo li, int slot, int nfields) {
+  using C = typename Cx<T>::c;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
   int local;
   const int b = find_inst(li, blockIdx.x, &local);
   const Inst& I = li.insts[b];
   if (!inst_active(I)) return;
   const int f = local % nfields, j = local / nfields;
   const int nx = I.nx, nz = I.nz, Mx = I.Mx, Mz = I.Mz, Kx = I.Kx, Kz = I.Kz;
-  const size_t PB = plane_buf_elems(I);
-  double2* B0 = sm;
-  double2* B1 = sm + PB;
-  double2* twx = sm + 2 * PB;
-  double2* twz = twx + nx;
-  load_twiddles(I, twx, twz);
-  for (int t = threadIdx.x; t < Mz * nx; t += blockDim.x) B0[t] = make_double2(0.0, 0.0);
+  const PlanePlan pp = plane_plan(I, sizeof(C));
+  C* B0 = sm;
+  C* B1 = sm + pp.PB;
+  C* twx = sm + 2 * pp.PB;
+  C* twz = twx + nx;
+  load_twiddles<T>(I, twx, twz);
+  for (int t = threadIdx.x; t < Mz * nx; t += blockDim.x) B0[t] = Cx<T>::mk(0, 0);
   __syncthreads();
-  const double2* src = I.yv + (((size_t)slot * kFieldsY + c_src[f]) * I.ny + j) * (size_t)I.nmodes;
+  const C* src = yv_of<T>(I) + (((size_t)slot * kFieldsY + c_src[f]) * I.ny + j) * (size_t)I.nmodes;
   const int fac = c_fac[f];
   for (int t = threadIdx.x; t < I.nmodes; t += blockDim.x) {
     const int i = t / Mz, p = t - i * Mz;
-    double2 s = src[t];
-    if (fac == 1) { const double k = I.kx[i]; s = make_double2(-k * s.y, k * s.x); }
-    else if (fac == 2) { const double k = I.kz[p]; s = make_double2(-k * s.y, k * s.x); }
+    C s = src[t];
+    if (fac == 1) { const T k = (T)I.kx[i]; s = Cx<T>::mk(-k * s.y, k * s.x); }
+    else if (fac == 2) { const T k = (T)I.kz[p]; s = Cx<T>::mk(-k * s.y, k * s.x); }
     B0[p * nx + xbin(i, Kx, Mx, nx)] = s;
   }
   __syncthreads();
-  double2* G = fft_run(B0, B1, nx, Mz, I.rx, I.nrx, twx, true);
-  double2* Hb = (G == B0) ? B1 : B0;
+  C* G = fft_run<C>(B0, B1, nx, Mz, I.rx, I.nrx, twx, true);
+  C* Zb = (G == B0) ? B1 : B0;
   const int nr = nx / 2;
-  for (int t = threadIdx.x; t < nr * nz; t += blockDim.x) {
-    const int r = t / nz, z = t - r * nz;
-    const int x1 = 2 * r, x2 = x1 + 1;
-    double2 h = make_double2(0.0, 0.0);
-    if (z == 0) {
-      h = make_double2(G[x1].x, G[x2].x);
-    } else if (z <= Kz) {
-      const double2 g1 = G[z * nx + x1], g2 = G[z * nx + x2];
-      h = make_double2(g1.x - g2.y, g1.y + g2.x);
-    } else if (z >= nz - Kz) {
-      const int p = nz - z;
-      const double2 g1 = G[p * nx + x1], g2 = G[p * nx + x2];
-      h = make_double2(g1.x + g2.y, g2.x - g1.y);
+  T* out = phys_of<T>(I) + (((size_t)slot * kFieldsSynth + f) * I.ny + j) * (size_t)nx * nz;
+  for (int r0 = 0; r0 < nr; r0 += pp.chunk) {
+    const int nrc = min(pp.chunk, nr - r0);
+    C* Z0 = Zb;
+    C* Z1 = (pp.chunk == nr) ? G : Zb + pp.chunk * nz;
+    for (int t = threadIdx.x; t < nrc * nz; t += blockDim.x) {
+      const int r = t / nz, z = t - r * nz;
+      const int x1 = 2 * (r0 + r), x2 = x1 + 1;
+      C h = Cx<T>::mk(0, 0);
+      if (z == 0) {
+        h = Cx<T>::mk(G[x1].x, G[x2].x);
+      } else if (z <= Kz) {
+        const C g1 = G[z * nx + x1], g2 = G[z * nx + x2];
+        h = Cx<T>::mk(g1.x - g2.y, g1.y + g2.x);
+      } else if (z >= nz - Kz) {
+        const int p = nz - z;
+        const C g1 = G[p * nx + x1], g2 = G[p * nx + x2];
+        h = Cx<T>::mk(g1.x + g2.y, g2.x - g1.y);
+      }
+      Z0[t] = h;
     }
-    Hb[t] = h;
-  }
-  __syncthreads();
-  double2* Rz = fft_run(Hb, G, nz, nr, I.rz, I.nrz, twz, true);
-  double* out = I.phys + (((size_t)slot * kFieldsSynth + f) * I.ny + j) * (size_t)nx * nz;
-  for (int t = threadIdx.x; t < nr * nz; t += blockDim.x) {
-    const int r = t / nz, z = t - r * nz;
-    const double2 h = Rz[t];
-    out[(2 * r) * nz + z] = h.x;
-    out[(2 * r + 1) * nz + z] = h.y;
+    __syncthreads();
+    C* Rz = fft_run<C>(Z0, Z1, nz, nrc, I.rz, I.nrz, twz, true);
+    for (int t = threadIdx.x; t < nrc * nz; t += blockDim.x) {
+      const int r = t / nz, z = t - r * nz;
+      const C h = Rz[t];
+      out[(2 * (r0 + r)) * nz + z] = h.x;
+      out[(2 * (r0 + r) + 1) * nz + z] = h.y;
+    }
+    __syncthreads();
   }
 }
 
 // ------------------------------------------------------------------ products + analysis
-// Field pointer of slot s, field f, plane j.
-__device__ __forceinline__ const double* fplane(const Inst& I, int s, int f, int j) {
-  return I.phys + (((size_t)s * kFieldsSynth + f) * I.ny + j) * (size_t)I.nx * I.nz;
+template <class T>
+__device__ __forceinline__ const T* fplane(const Inst& I, int s, int f, int j) {
+  return phys_of<T>(I) + (((size_t)s * kFieldsSynth + f) * I.ny + j) * (size_t)I.nx * I.nz;
 }
 
 // gradient component d_d (d = 0 x, 1 y, 2 z) of velocity component c at point e of plane j
-__device__ __forceinline__ double grad_at(const double* const* F, int c, int d, int e) {
+template <class T>
+__device__ __forceinline__ T grad_at(const T* const* F, int c, int d, int e) {
   // fields: 3 u_x, 4 u_y, 5 u_z, 6 v_x, 7 v_z, 8 w_x, 9 w_y, 10 w_z; v_y = -u_x - w_z
   if (c == 0) return F[3 + d][e];
   if (c == 2) return F[8 + d][e];
@@ -215,137 +290,122 @@ __device__ __forceinline__ double grad_at(const double* const* F, int c, int d, 
   return -(F[3][e] + F[10][e]);
 }
 
-// Forward 2D transform of the product plane held in Hb as pairs of rows, 2/3 truncation.
-__device__ void analyse_plane(const Inst& I, double2* Hb, double2* Ob, const double2* twx, const double2* twz,
-                              double2* dst) {
-  const int nx = I.nx, nz = I.nz, Mx = I.Mx, Mz = I.Mz, Kx = I.Kx;
-  const int nr = nx / 2;
-  double2* R = fft_run(Hb, Ob, nz, nr, I.rz, I.nrz, twz, false);
-  double2* X = (R == Hb) ? Ob : Hb;
-  for (int t = threadIdx.x; t < nr * Mz; t += blockDim.x) {
-    const int r = t / Mz, p = t - r * Mz;
-    const double2 hp = R[r * nz + p];
-    const double2 hm = R[r * nz + (p == 0 ? 0 : nz - p)];
-    const double2 g1 = make_double2(0.5 * (hp.x + hm.x), 0.5 * (hp.y - hm.y));
-    const double2 g2 = make_double2(0.5 * (hp.y + hm.y), -0.5 * (hp.x - hm.x));
-    X[p * nx + 2 * r] = g1;
-    X[p * nx + 2 * r + 1] = g2;
-  }
-  __syncthreads();
-  double2* Y = fft_run(X, R, nx, Mz, I.rx, I.nrx, twx, false);
-  const double s = I.inv_nxnz;
-  for (int t = threadIdx.x; t < I.nmodes; t += blockDim.x) {
-    const int i = t / Mz, p = t - i * Mz;
-    const double2 v = Y[p * nx + xbin(i, Kx, Mx, nx)];
-    dst[t] = make_double2(v.x * s, v.y * s);
-  }
-}
-
-// CTA = (instance, plane j, component c): M_c = -y d_x u_c - v [c=x] - (u.grad) u_c.
-__global__ void __launch_bounds__(128) k_prod_M(LaunchInfo li) {
-  extern __shared__ double2 sm[];
-  int local;
-  const int b = find_inst(li, blockIdx.x, &local);
-  const Inst& I = li.insts[b];
-  if (!inst_active(I)) return;
-  const int c = local % 3, j = local / 3;
-  const int nx = I.nx, nz = I.nz;
-  const size_t PB = plane_buf_elems(I);
-  double2* B0 = sm;
-  double2* B1 = sm + PB;
-  double2* twx = sm + 2 * PB;
-  double2* twz = twx + nx;
-  load_twiddles(I, twx, twz);
-  const double* F[kFieldsSynth];
+// Pointwise products of the plane, row pairs packed as complex values.
+template <class T, bool ADJ>
+__device__ __forceinline__ void product_pair(const Inst& I, const T* const* U, const T* const* Q, int c, T y, int e0,
+                                             int e1, T* m, double* sq) {
 #pragma unroll
-  for (int f = 0; f < kFieldsSynth; ++f) F[f] = fplane(I, 0, f, j);
-  const double y = I.ygrid[j];
-  const int nr = nx / 2;
-  for (int t = threadIdx.x; t < nr * nz; t += blockDim.x) {
-    const int r = t / nz, z = t - r * nz;
-    double m[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int e = (2 * r + h) * nz + z;
-      const double u = F[0][e], v = F[1][e], w = F[2][e];
-      const double gx = grad_at(F, c, 0, e), gy = grad_at(F, c, 1, e), gz = grad_at(F, c, 2, e);
-      double val = -fma(y + u, gx, fma(v, gy, w * gz));
+  for (int h = 0; h < 2; ++h) {
+    const int e = h == 0 ? e0 : e1;
+    const T u = U[0][e], v = U[1][e], w = U[2][e];
+    if (!ADJ) {
+      const T gx = grad_at<T>(U, c, 0, e), gy = grad_at<T>(U, c, 1, e), gz = grad_at<T>(U, c, 2, e);
+      T val = -fma(y + u, gx, fma(v, gy, w * gz));
       if (c == 0) val -= v;
       m[h] = val;
-    }
-    B0[t] = make_double2(m[0], m[1]);
-  }
-  __syncthreads();
-  analyse_plane(I, B0, B1, twx, twz, I.xz + ((size_t)c * I.ny + j) * I.nmodes);
-}
-
-// CTA = (instance, plane j, component c):
-// N_c = (U.grad) q_c - q_j d_c U_j with U = (y + u, v, w), plus sum over the plane of q_c^2.
-__global__ void __launch_bounds__(128) k_prod_N(LaunchInfo li) {
-  extern __shared__ double2 sm[];
-  int local;
-  const int b = find_inst(li, blockIdx.x, &local);
-  const Inst& I = li.insts[b];
-  if (!inst_active(I)) return;
-  const int c = local % 3, j = local / 3;
-  const int nx = I.nx, nz = I.nz;
-  const size_t PB = plane_buf_elems(I);
-  double2* B0 = sm;
-  double2* B1 = sm + PB;
-  double2* twx = sm + 2 * PB;
-  double2* twz = twx + nx;
-  double* red = reinterpret_cast<double*>(twz + nz);
-  load_twiddles(I, twx, twz);
-  const double* U[kFieldsSynth];
-  const double* Q[kFieldsSynth];
-#pragma unroll
-  for (int f = 0; f < kFieldsSynth; ++f) {
-    U[f] = fplane(I, 0, f, j);
-    Q[f] = fplane(I, 1, f, j);
-  }
-  const double y = I.ygrid[j];
-  const int nr = nx / 2;
-  double sq = 0.0;
-  for (int t = threadIdx.x; t < nr * nz; t += blockDim.x) {
-    const int r = t / nz, z = t - r * nz;
-    double m[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int e = (2 * r + h) * nz + z;
-      const double u = U[0][e], v = U[1][e], w = U[2][e];
-      const double q0 = Q[0][e], q1 = Q[1][e], q2 = Q[2][e];
-      const double qc = Q[c][e];
-      sq = fma(qc, qc, sq);
-      const double adv = fma(y + u, grad_at(Q, c, 0, e), fma(v, grad_at(Q, c, 1, e), w * grad_at(Q, c, 2, e)));
-      const double tr = fma(q0, grad_at(U, 0, c, e), fma(q1, grad_at(U, 1, c, e), q2 * grad_at(U, 2, c, e)));
-      double val = adv - tr;
+    } else {
+      const T q0 = Q[0][e], q1 = Q[1][e], q2 = Q[2][e];
+      const T qc = Q[c][e];
+      *sq = fma((double)qc, (double)qc, *sq);
+      const T adv = fma(y + u, grad_at<T>(Q, c, 0, e), fma(v, grad_at<T>(Q, c, 1, e), w * grad_at<T>(Q, c, 2, e)));
+      const T tr = fma(q0, grad_at<T>(U, 0, c, e), fma(q1, grad_at<T>(U, 1, c, e), q2 * grad_at<T>(U, 2, c, e)));
+      T val = adv - tr;
       if (c == 1) val -= q0;
       m[h] = val;
     }
-    B0[t] = make_double2(m[0], m[1]);
   }
-  // deterministic block reduction of sum q_c^2
-  for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+}
+
+// CTA = (instance, plane j, component c): product component c on the plane (M(u) or
+// N(q) with U = (y + u, v, w)), forward FFT in z then x, 2/3 truncation.  ADJ also sums
+// q_c^2 over the plane (in FP64) for J.
+template <class T, bool ADJ>
+__global__ void __launch_bounds__(128) k_prod_t(LaunchInfo li) {
+  using C = typename Cx<T>::c;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  int local;
+  const int b = find_inst(li, blockIdx.x, &local);
+  const Inst& I = li.insts[b];
+  if (!inst_active(I)) return;
+  const int c = local % 3, j = local / 3;
+  const int nx = I.nx, nz = I.nz, Mx = I.Mx, Mz = I.Mz, Kx = I.Kx;
+  const PlanePlan pp = plane_plan(I, sizeof(C));
+  C* B0 = sm;
+  C* B1 = sm + pp.PB;
+  C* twx = sm + 2 * pp.PB;
+  C* twz = twx + nx;
+  double* red = reinterpret_cast<double*>(twz + nz);
+  load_twiddles<T>(I, twx, twz);
+  const T* U[kFieldsSynth];
+  const T* Q[kFieldsSynth];
+#pragma unroll
+  for (int f = 0; f < kFieldsSynth; ++f) {
+    U[f] = fplane<T>(I, 0, f, j);
+    Q[f] = ADJ ? fplane<T>(I, 1, f, j) : nullptr;
+  }
+  const T y = (T)I.ygrid[j];
+  const int nr = nx / 2;
+  const bool whole = pp.chunk == nr;
+  // the x-stage input X[p][x] lives in B0 when chunked (z chunks use B1), else decided below
+  C* X = B0;
+  double sq = 0.0;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    I.normpart[(size_t)c * I.ny + j] = s;
+  for (int r0 = 0; r0 < nr; r0 += pp.chunk) {
+    const int nrc = min(pp.chunk, nr - r0);
+    C* Z0 = whole ? B0 : B1;
+    C* Z1 = whole ? B1 : B1 + pp.chunk * nz;
+    for (int t = threadIdx.x; t < nrc * nz; t += blockDim.x) {
+      const int r = t / nz, z = t - r * nz;
+      const int e0 = (2 * (r0 + r)) * nz + z, e1 = e0 + nz;
+      T m[2];
+      product_pair<T, ADJ>(I, U, Q, c, y, e0, e1, m, &sq);
+      Z0[t] = Cx<T>::mk(m[0], m[1]);
+    }
+    __syncthreads();
+    C* R = fft_run<C>(Z0, Z1, nz, nrc, I.rz, I.nrz, twz, false);
+    if (whole) X = (R == B0) ? B1 : B0;
+    for (int t = threadIdx.x; t < nrc * Mz; t += blockDim.x) {
+      const int r = t / Mz, p = t - r * Mz;
+      const C hp = R[r * nz + p];
+      const C hm = R[r * nz + (p == 0 ? 0 : nz - p)];
+      const T half = (T)0.5;
+      X[p * nx + 2 * (r0 + r)] = Cx<T>::mk(half * (hp.x + hm.x), half * (hp.y - hm.y));
+      X[p * nx + 2 * (r0 + r) + 1] = Cx<T>::mk(half * (hp.y + hm.y), -half * (hp.x - hm.x));
+    }
+    __syncthreads();
   }
-  analyse_plane(I, B0, B1, twx, twz, I.xz + ((size_t)c * I.ny + j) * I.nmodes);
+  if (ADJ) {
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+      I.normpart[(size_t)c * I.ny + j] = s;
+    }
+  }
+  C* Y = fft_run<C>(X, X == B0 ? B1 : B0, nx, Mz, I.rx, I.nrx, twx, false);
+  const T sc = (T)I.inv_nxnz;
+  C* dst = xz_of<T>(I) + ((size_t)c * I.ny + j) * I.nmodes;
+  for (int t = threadIdx.x; t < I.nmodes; t += blockDim.x) {
+    const int i = t / Mz, p = t - i * Mz;
+    const C v = Y[p * nx + xbin(i, Kx, Mx, nx)];
+    dst[t] = Cx<T>::mk(v.x * sc, v.y * sc);
+  }
 }
 
 // CTA = (instance, plane j, component c): sum over the plane of q_c^2 (slot 1, field c).
-__global__ void __launch_bounds__(128) k_norm_planes(LaunchInfo li) {
+template <class T>
+__global__ void __launch_bounds__(128) k_norm_planes_t(LaunchInfo li) {
   __shared__ double red[32];
   int local;
   const int b = find_inst(li, blockIdx.x, &local);
   const Inst& I = li.insts[b];
   const int c = local % 3, j = local / 3;
-  const double* q = fplane(I, 1, c, j);
+  const T* q = fplane<T>(I, 1, c, j);
   double sq = 0.0;
-  for (int t = threadIdx.x; t < I.nx * I.nz; t += blockDim.x) sq = fma(q[t], q[t], sq);
+  for (int t = threadIdx.x; t < I.nx * I.nz; t += blockDim.x) sq = fma((double)q[t], (double)q[t], sq);
   for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
   __syncthreads();
@@ -354,6 +414,36 @@ __global__ void __launch_bounds__(128) k_norm_planes(LaunchInfo li) {
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
     I.normpart[(size_t)c * I.ny + j] = s;
   }
+}
+
+// host launchers (the kernel templates are instantiated in this translation unit only)
+void launch_xzsynth(bool f32, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int slot, int nf) {
+  if (f32) k_xzsynth_t<float><<<ctas, 128, smem, s>>>(li, slot, nf);
+  else k_xzsynth_t<double><<<ctas, 128, smem, s>>>(li, slot, nf);
+}
+void launch_prod(bool f32, bool adj, int ctas, size_t smem, cudaStream_t s, LaunchInfo li) {
+  if (f32) {
+    if (adj) k_prod_t<float, true><<<ctas, 128, smem, s>>>(li);
+    else k_prod_t<float, false><<<ctas, 128, smem, s>>>(li);
+  } else {
+    if (adj) k_prod_t<double, true><<<ctas, 128, smem, s>>>(li);
+    else k_prod_t<double, false><<<ctas, 128, smem, s>>>(li);
+  }
+}
+void launch_norm_planes(bool f32, int ctas, cudaStream_t s, LaunchInfo li) {
+  if (f32) k_norm_planes_t<float><<<ctas, 128, 0, s>>>(li);
+  else k_norm_planes_t<double><<<ctas, 128, 0, s>>>(li);
+}
+cudaError_t set_plane_smem(bool f32, size_t synth, size_t prod) {
+  cudaError_t e;
+  if (f32) {
+    if ((e = cudaFuncSetAttribute(k_xzsynth_t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)synth))) return e;
+    if ((e = cudaFuncSetAttribute(k_prod_t<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prod))) return e;
+    return cudaFuncSetAttribute(k_prod_t<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prod);
+  }
+  if ((e = cudaFuncSetAttribute(k_xzsynth_t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)synth))) return e;
+  if ((e = cudaFuncSetAttribute(k_prod_t<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prod))) return e;
+  return cudaFuncSetAttribute(k_prod_t<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prod);
 }
 
 // J = sqrt(0.5 * sum_j w_j * mean_{x,z} |q|^2) from the plane sums (fixed order).
@@ -372,11 +462,12 @@ __global__ void k_norm_final(LaunchInfo li, double* out) {
 
 // ------------------------------------------------------------------ per-mode kernel
 size_t smem_mode(const Inst& I, int mpc) {
-  // cheb + rco + per mode: solver table, Fr/U0/Out ([3][2][L2] each), chain scratch [4][6][Mh]
+  // [cheb (FP64 form only)] + rco + per mode: [solver table (sweep solve only)],
+  // Fr/U0/Out ([3][2][L2] each), chain scratch [4][6][Mh]
   const int N = I.N, Mh = N / 2 + 1, H = Mh, L2 = 2 * Mh;
   const TabLayout TL(N);
-  size_t d = 6 * (size_t)H * H + 10 * (size_t)Mh;
-  d += (size_t)mpc * (TL.per_mode() + 18 * (size_t)L2 + 24 * (size_t)Mh);
+  size_t d = (I.mixed ? 0 : 6 * (size_t)H * H) + 10 * (size_t)Mh;
+  d += (size_t)mpc * ((I.dense[0] ? 0 : TL.per_mode()) + 18 * (size_t)L2 + 24 * (size_t)Mh);
   return d * sizeof(double);
 }
 
@@ -408,19 +499,21 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
     return;
   }
 
+  const bool need_cheb = !I.mixed, need_tabs = !I.dense[0];
   double* cheb = smd;
-  double* rco = cheb + CL.total();
+  double* rco = cheb + (need_cheb ? CL.total() : 0);
   double* tabs = rco + RL.total();
   const int PM = TL.per_mode();
-  double* Fr = tabs + (size_t)mpc * PM;          // [mpc][3][2][L2]
+  double* Fr = tabs + (need_tabs ? (size_t)mpc * PM : 0);  // [mpc][3][2][L2]
   double* U0 = Fr + (size_t)mpc * 6 * L2;        // [mpc][3][2][L2]
   double* Out = U0 + (size_t)mpc * 6 * L2;       // [mpc][3][2][L2] (also y-values input)
   double* Ch = Out + (size_t)mpc * 6 * L2;       // [mpc][4][6][Mh]
 
-  for (int t = threadIdx.x; t < CL.total(); t += blockDim.x) cheb[t] = I.cheb[t];
+  if (need_cheb)
+    for (int t = threadIdx.x; t < CL.total(); t += blockDim.x) cheb[t] = I.cheb[t];
   for (int t = threadIdx.x; t < RL.total(); t += blockDim.x) rco[t] = I.rco[t];
   const double* tabg = solve ? I.tab[sig] : nullptr;
-  if (solve && !I.dense[sig])
+  if (solve && need_tabs)
     for (int t = threadIdx.x; t < nmod * PM; t += blockDim.x) tabs[t] = tabg[(size_t)m0 * PM + t];
 
   // state coefficients of the input (u for PHI/SYNTH, r1 for PSI, rhs for SOLVE), class-split
@@ -433,7 +526,7 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
     dst[L2] = v.y;
   }
   // y-values of the products at this CTA's modes
-  if (op == MODE_PHI || op == MODE_PSI_UPDATE || op == MODE_PSI_GRAD) {
+  if (!I.mixed && (op == MODE_PHI || op == MODE_PSI_UPDATE || op == MODE_PSI_GRAD)) {
     for (int t = threadIdx.x; t < nmod * 3 * ny; t += blockDim.x) {
       const int mm = t % nmod, cj = t / nmod, j = cj % ny, c = cj / ny;
       const double2 v = I.xz[((size_t)c * ny + j) * nm + m0 + mm];
@@ -449,7 +542,18 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
   const double inv_nu = 1.0 / I.nu;
   const int half = N / 2;
   if (solve) {
-    if (op != MODE_SOLVE) {
+    if (I.mixed && op != MODE_SOLVE) {
+      // mixed form: Chebyshev coefficients of the products come from the tensor-core kernel
+      for (int t = threadIdx.x; t < nmod * 3 * ny; t += blockDim.x) {
+        const int mm = t % nmod, cn = t / nmod, n = cn % ny, c = cn / ny;
+        const float2 v = I.xzc[((size_t)c * ny + n) * nm + m0 + mm];
+        const int pos = (n & 1) * Mh + (n >> 1);
+        const double* u0 = U0 + ((size_t)mm * 3 + c) * 2 * L2;
+        double* fr = Fr + ((size_t)mm * 3 + c) * 2 * L2;
+        fr[pos] = fma(u0[pos], inv_step, (double)v.x) * inv_nu;
+        fr[L2 + pos] = fma(u0[L2 + pos], inv_step, (double)v.y) * inv_nu;
+      }
+    } else if (op != MODE_SOLVE) {
       // fold y-values: P_j = V_j + V_{N-j} (at j), Q_j = V_j - V_{N-j} (at N-j), j < N/2
       for (int t = threadIdx.x; t < nmod * 6 * half; t += blockDim.x) {
         const int j = t % half, a = t / half;
@@ -624,6 +728,7 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
   if (op == MODE_PSI_GRAD) { gout = I.fhat; }
   if (op == MODE_SOLVE) { gout = I.fhat; }
   if (op == MODE_SYNTH_ONLY) { slot = sig; }
+  if (I.mixed) slot = -1;  // the tensor-core kernel synthesises from the FP64 state
   for (int t = threadIdx.x; t < nmod * 3 * ny; t += blockDim.x) {
     const int n = t % ny, mc = t / ny, c = mc % 3, mm = mc / 3;
     const int pos = (n & 1) * Mh + (n >> 1);

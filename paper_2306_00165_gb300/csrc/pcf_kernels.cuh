@@ -19,16 +19,32 @@ struct LaunchInfo {
   int ninst;
 };
 
-__global__ void k_xzsynth(LaunchInfo li, int slot, int nfields);
-__global__ void k_prod_M(LaunchInfo li);
-__global__ void k_prod_N(LaunchInfo li);
-__global__ void k_norm_planes(LaunchInfo li);
+__device__ __forceinline__ int find_inst(const LaunchInfo& li, int cta, int* local) {
+  int lo = 0, hi = li.ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (li.prefix[mid] <= cta) lo = mid; else hi = mid - 1;
+  }
+  *local = cta - li.prefix[lo];
+  return lo;
+}
+
+void launch_xzsynth(bool f32, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int slot, int nf);
+void launch_prod(bool f32, bool adj, int ctas, size_t smem, cudaStream_t s, LaunchInfo li);
+void launch_norm_planes(bool f32, int ctas, cudaStream_t s, LaunchInfo li);
+cudaError_t set_plane_smem(bool f32, size_t synth, size_t prod);
 __global__ void k_mode(LaunchInfo li, int op, int sig, int mpc, int step_index);
 __global__ void k_norm_final(LaunchInfo li, double* out);
 __global__ void k_fp64_probe(double* out, int iters);
 
+size_t smem_plane(const Inst& I, int elem_bytes);
 size_t smem_xzsynth(const Inst& I);
 size_t smem_prod(const Inst& I);
 size_t smem_mode(const Inst& I, int mpc);
+size_t smem_cheb_tc(int ny);
+void launch_cheb_synth_tc(int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int slot);
+void launch_cheb_analysis_tc(int ctas, size_t smem, cudaStream_t s, LaunchInfo li);
+cudaError_t set_cheb_tc_smem(size_t smem);
+int cheb_tc_tiles(int nmodes);
 
 }  // namespace pcf
