@@ -202,6 +202,44 @@ pcf_status pcf_run(pcf_ctx* ctx, double* u_hat, double dtau, int max_steps, doub
 pcf_status pcf_influence_matrix_solve_noalloc(const pcf_params* params, const double* rhs_hat, double* out_hat,
                                               double step, void* stream);
 
+/* ---- Learned proposal (the accelerated form with a neural operator) ----
+ * A Fourier-space neural operator on the spectral coefficients of the state proposes the
+ * state far ahead in pseudo-time; the descent judges every proposal by the residual norm
+ * and keeps its own state otherwise.  Features per retained Fourier mode mp (all Mx*Mz)
+ * and Chebyshev index n: (Re v, Im v, Re eta, Im eta), eta = i kz u - i kx w, or
+ * (u, w, 0, 0) for the mean mode; layout float [MP][S][NY][4].
+ * `scale` is a device array [MP][NY][4] of per-coefficient feature scales (e.g. inverse RMS
+ * over the training states); network outputs are increments in the same scaled units.
+ * Network, per retained Fourier mode mp with F = NY*4 coefficients X[mp]:
+ * H0 = X[mp] E[mp]^T + bE; Z_l = H_{l-1} (R_l[mp] + L_l)^T + b_l; H_l = H_{l-1} + GELU(Z_l);
+ * Y[mp] = H_L D[mp]^T + bD[mp]; loss mean((Y - T)^2).  All products run on the tensor
+ * cores in BF16 with FP32 accumulation; Adam on FP32 master weights.
+ * Parameter layout (float): E [MP][W][F], bE [W], D [MP][F][W], bD [MP][F], then per
+ * layer R [MP][W][W], L [W][W], b [W].  All array arguments are device pointers
+ * unless named *_host. */
+typedef struct pcf_fno pcf_fno;
+pcf_status pcf_fno_create(int MP, int NY, int width, int layers, unsigned long long seed, void* stream, pcf_fno** out);
+void pcf_fno_destroy(pcf_fno* net);
+long long pcf_fno_num_params(const pcf_fno* net);
+pcf_status pcf_fno_set_params(pcf_fno* net, const float* params_host);
+pcf_status pcf_fno_get_params(pcf_fno* net, float* params_host);
+/* Y = network(X) for S samples. */
+pcf_status pcf_fno_forward(pcf_fno* net, const float* X, int S, float* Y);
+/* Loss and its gradient (grad: device, pcf_fno_num_params floats, may be NULL); loss on the host. */
+pcf_status pcf_fno_loss_grad(pcf_fno* net, const float* X, const float* T, int S, double* loss_host, float* grad);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr; loss before the step. */
+pcf_status pcf_fno_train_step(pcf_fno* net, const float* X, const float* T, int S, float lr, double* loss_host);
+/* Features of every instance of a uniform context: X [nm][batch][ny][4]. */
+pcf_status pcf_fno_features(pcf_ctx* ctx, const double* u_hat, float* X, const float* scale);
+/* One proposal: u' = state of (features(u) + network(features(u))) / scale, completed to an
+ * admissible field (walls, divergence).  With relax_steps > 0 both u and u' first take that
+ * many plain descent steps of size dtau.  Instance b then takes the proposal's branch iff
+ * its residual norm J is lower (ties keep the plain branch).  accepted_host,
+ * J_before_host (plain branch), J_after_host (proposal branch): batch entries each (may
+ * be NULL).  Synchronises. */
+pcf_status pcf_fno_propose(pcf_ctx* ctx, pcf_fno* net, double* u_hat, const float* scale, int relax_steps,
+                           double dtau, int* accepted_host, double* J_before_host, double* J_after_host);
+
 /* Measures the FP64 FMA throughput of the current device with a dependent-chain-free
  * DFMA loop (used for the ALU roofline).  gflops: host output.  Synchronises. */
 pcf_status pcf_probe_fp64_peak(void* stream, double* gflops);

@@ -13,7 +13,7 @@ import os
 
 from . import build as _build
 
-__all__ = ["Solver", "load_library", "state_shape", "psi_len", "probe_fp64_peak", "PCFError"]
+__all__ = ["Solver", "FNO", "load_library", "state_shape", "psi_len", "probe_fp64_peak", "PCFError"]
 
 LX_PAPER = 2.0 * math.pi / 1.14
 LZ_PAPER = 2.0 * math.pi / 2.5
@@ -66,6 +66,16 @@ def load_library(path=None):
         "pcf_dmd_extrapolate": (I, [P, P, ctypes.c_longlong, I, D, P, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "pcf_run": (I, [P, P, D, I, D, I, I, D, P, P, ctypes.POINTER(I)]),
         "pcf_probe_fp64_peak": (I, [P, ctypes.POINTER(D)]),
+        "pcf_fno_create": (I, [I, I, I, I, ctypes.c_ulonglong, P, ctypes.POINTER(P)]),
+        "pcf_fno_destroy": (None, [P]),
+        "pcf_fno_num_params": (ctypes.c_longlong, [P]),
+        "pcf_fno_set_params": (I, [P, P]),
+        "pcf_fno_get_params": (I, [P, P]),
+        "pcf_fno_forward": (I, [P, P, I, P]),
+        "pcf_fno_loss_grad": (I, [P, P, P, I, ctypes.POINTER(D), P]),
+        "pcf_fno_train_step": (I, [P, P, P, I, ctypes.c_float, ctypes.POINTER(D)]),
+        "pcf_fno_features": (I, [P, P, P, P]),
+        "pcf_fno_propose": (I, [P, P, P, P, I, D, P, P, P]),
         "pcf_set_kernel_timing": (I, [P, I]),
         "pcf_kernel_times": (I, [P, P, P, I]),
         "pcf_launches_per_step": (I, [P]),
@@ -273,3 +283,110 @@ class Solver:
 
     def launches_per_step(self):
         return int(self.lib.pcf_launches_per_step(self._h))
+
+
+class FNO:
+    """Learned proposal network (see include/pcfadj.h); features/targets are float32 CUDA
+    tensors [MP, S, NY, 4] with MP = Mx*Mz retained Fourier modes and NY = ny."""
+
+    def __init__(self, MP, NY, width=32, layers=4, seed=0):
+        import torch
+        self.lib = load_library()
+        self.MP, self.NY, self.W, self.L = MP, NY, width, layers
+        h = ctypes.c_void_p()
+        _check(self.lib.pcf_fno_create(MP, NY, width, layers, seed, _stream(), ctypes.byref(h)))
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.pcf_fno_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_params(self):
+        return int(self.lib.pcf_fno_num_params(self._h))
+
+    def get_params(self):
+        import numpy as np
+        out = np.empty(self.num_params(), np.float32)
+        _check(self.lib.pcf_fno_get_params(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def set_params(self, flat):
+        import numpy as np
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.num_params()
+        _check(self.lib.pcf_fno_set_params(self._h, flat.ctypes.data_as(ctypes.c_void_p)))
+
+    def pack(self, p):
+        """Oracle-style parameter dict -> flat float32 array in the library's layout."""
+        import numpy as np
+        parts = [p["E"], p["bE"], p["D"], p["bD"]]
+        for l in range(self.L):
+            parts += [p[f"R{l}"], p[f"L{l}"], p[f"b{l}"]]
+        return np.concatenate([np.asarray(a, np.float64).ravel() for a in parts]).astype(np.float32)
+
+    def unpack(self, flat):
+        W, MP, F = self.W, self.MP, self.NY * 4
+        shapes = [("E", (MP, W, F)), ("bE", (W,)), ("D", (MP, F, W)), ("bD", (MP, F))]
+        for l in range(self.L):
+            shapes += [(f"R{l}", (MP, W, W)), (f"L{l}", (W, W)), (f"b{l}", (W,))]
+        out, o = {}, 0
+        for k, shp in shapes:
+            n = 1
+            for d in shp:
+                n *= d
+            out[k] = flat[o:o + n].reshape(shp)
+            o += n
+        return out
+
+    def forward(self, X, Y=None):
+        import torch
+        S = X.shape[1]
+        Y = torch.empty_like(X) if Y is None else Y
+        _check(self.lib.pcf_fno_forward(self._h, _ptr(X), S, _ptr(Y)))
+        return Y
+
+    def loss_grad(self, X, T):
+        import torch
+        g = torch.empty(self.num_params(), dtype=torch.float32, device=self.device)
+        loss = ctypes.c_double()
+        _check(self.lib.pcf_fno_loss_grad(self._h, _ptr(X), _ptr(T), X.shape[1], ctypes.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def train_step(self, X, T, lr):
+        loss = ctypes.c_double()
+        _check(self.lib.pcf_fno_train_step(self._h, _ptr(X), _ptr(T), X.shape[1], float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    @staticmethod
+    def unit_scale(solver):
+        import torch
+        MP = solver.shape[2] * solver.shape[3]
+        return torch.ones((MP, solver.ny, 4), dtype=torch.float32, device=solver.device)
+
+    @staticmethod
+    def features(solver, u, scale=None, X=None):
+        """Scaled features [MP, batch, NY, 4]; scale: float32 [MP, NY, 4] (default ones)."""
+        import torch
+        MP = solver.shape[2] * solver.shape[3]
+        scale = FNO.unit_scale(solver) if scale is None else scale
+        X = torch.empty((MP, solver.batch, solver.ny, 4), dtype=torch.float32, device=solver.device) if X is None else X
+        _check(solver.lib.pcf_fno_features(solver._h, _ptr(u), _ptr(X), _ptr(scale)))
+        return X
+
+    def propose(self, solver, u, scale, relax_steps=0, dtau=0.01):
+        """One judged proposal on every instance of ``solver``; returns (accepted, J_plain, J_proposal)."""
+        B = solver.batch
+        acc = (ctypes.c_int * B)()
+        j0 = (ctypes.c_double * B)()
+        j1 = (ctypes.c_double * B)()
+        _check(self.lib.pcf_fno_propose(solver._h, self._h, _ptr(u), _ptr(scale), int(relax_steps), float(dtau),
+                                        acc, j0, j1))
+        return list(acc), list(j0), list(j1)
