@@ -179,6 +179,128 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _timed_steps(s, u, dtau, nsteps, flush, stream):
+    """Device time of nsteps descent steps, L2 flushed before each (CUDA events)."""
+    import torch
+    tot = 0.0
+    for k in range(nsteps):
+        flush.fill_(float(k))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.descent_step(u, dtau, 1, hist=False)
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot
+
+
+def run_forms(pcf, gi, flush, stream, dev, args):
+    """The batched, mixed-precision and learned forms of the method, each next to the plain
+    FP64 method on the same work."""
+    import numpy as np
+    import torch
+    out = {}
+    # batched: 64 guesses on uneven grids in one context (one graph per step)
+    grids = [(32, 33, 32, 24), (48, 49, 48, 24), (64, 65, 64, 16)]
+    sb = pcf.Solver.batched(grids)
+    us, k = [], 0
+    for (nx, ny, nz, cnt) in grids:
+        for _ in range(cnt):
+            us.append(gi.streak_roll(nx, ny, nz, seed=k).ravel())
+            k += 1
+    ub = torch.from_numpy(np.concatenate(us)).to(dev)
+    sb.descent_step(ub, DTAU, 3)
+    ms = _timed_steps(sb, ub, DTAU, 10, flush, stream)
+    out["batched"] = {"config": "64 guesses: 24x32x33x32 + 24x48x49x48 + 16x64x65x64, Re 400, FP64",
+                      "gradient_evals_per_s": 64 * 10 / (ms * 1e-3), "ms_per_step": ms / 10,
+                      "mode_tile_autotuned": sb.mode_tile(), "points": int(24 * 33792 + 24 * 112896 + 16 * 266240)}
+    sb.close()
+    # mixed precision vs FP64 at 128x97x128, Re 1000
+    g4 = (128, 97, 128)
+    u4 = gi.random_perturbation(*g4, 0.1, 0)[None]
+    res = {}
+    for name, prec in (("fp64", 0), ("mixed", 1)):
+        s4 = pcf.Solver(*g4, batch=1, Re=1000.0, precision=prec)
+        u = torch.from_numpy(u4).to(dev)
+        s4.descent_step(u, DTAU, 2)
+        ms = _timed_steps(s4, u, DTAU, 5, flush, stream)
+        r, J = s4.residual(torch.from_numpy(u4).to(dev))
+        res[name] = (ms / 5, r.cpu().numpy()[0], float(J[0]))
+        s4.close()
+    err = {c: float(np.max(np.abs(res["mixed"][1][i] - res["fp64"][1][i])) / np.max(np.abs(res["fp64"][1][i])))
+           for i, c in enumerate("uvw")}
+    out["mixed"] = {"config": "1 guess, 128x97x128, Re 1000; FP32 x-z FFTs and products, split-BF16 tensor-core "
+                              "Chebyshev transforms, FP64 solves/norms",
+                    "ms_per_step": res["mixed"][0], "fp64_ms_per_step": res["fp64"][0],
+                    "speedup_vs_fp64": res["fp64"][0] / res["mixed"][0],
+                    "gradient_evals_per_s": 1e3 / res["mixed"][0],
+                    "r1_rel_error_vs_fp64_path_per_component": err,
+                    "J_rel_error_vs_fp64_path": abs(res["mixed"][2] - res["fp64"][2]) / res["fp64"][2]}
+    if args.no_learned:
+        return out
+    # learned proposal: train on the method's own trajectories, then judge on fresh guesses
+    t0 = time.perf_counter()
+    g5 = GRID
+    seeds = list(range(1000, 1064))
+    st = pcf.Solver(*g5, batch=len(seeds))
+    u = torch.from_numpy(gi.batch(gi.streak_roll, seeds, *g5)).to(dev)
+    every, lag, nsnap = 100, args.learn_lag // 100, args.learn_lag // 100 + 80
+    feats = []
+    for _ in range(nsnap):
+        feats.append(pcf.FNO.features(st, u).clone())
+        st.descent_step(u, DTAU, every, hist=False)
+    st.close()
+    X = torch.cat(feats[:nsnap - lag], 1)
+    Y = torch.cat([feats[k + lag] - feats[k] for k in range(nsnap - lag)], 1)
+    del feats
+    rms = X.pow(2).mean(1).sqrt()
+    sc = torch.where(rms > 1e-30, 1.0 / rms.clamp_min(1e-30), torch.zeros_like(rms)).contiguous()
+    X, Y = X * sc[:, None], Y * sc[:, None]
+    t_data = time.perf_counter() - t0
+    net = pcf.FNO(X.shape[0], g5[1], seed=1)
+    n = X.shape[1]
+    gen = torch.Generator(device=dev).manual_seed(0)
+    t1 = time.perf_counter()
+    losses = []
+    for it in range(args.learn_iters):
+        idx = torch.randint(0, n, (32,), device=dev, generator=gen)
+        losses.append(net.train_step(X[:, idx].contiguous(), Y[:, idx].contiguous(),
+                                     1e-3 if it < args.learn_iters // 2 else 3e-4))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    del X, Y
+    fresh = gi.batch(gi.streak_roll, range(2000, 2064), *g5)
+    sp = pcf.Solver(*g5, batch=64)
+    sl = pcf.Solver(*g5, batch=64)
+    up = torch.from_numpy(fresh).to(dev)
+    ul = torch.from_numpy(fresh).to(dev)
+    taken = 0
+    t2 = time.perf_counter()
+    rounds = args.learn_steps // 500
+    for _ in range(rounds):
+        sp.descent_step(up, DTAU, 500, hist=False)
+        sl.descent_step(ul, DTAU, 500, hist=False)
+        acc, _, _ = net.propose(sl, ul, sc, relax_steps=20, dtau=DTAU)
+        sp.descent_step(up, DTAU, 20, hist=False)
+        taken += sum(acc)
+    torch.cuda.synchronize()
+    t_inf = time.perf_counter() - t2
+    Jp = sp.residual(up)[1].cpu().numpy()
+    Jl = sl.residual(ul)[1].cpu().numpy()
+    out["learned"] = {"config": f"FNO ({net.num_params()} params, width 32, 4 layers, GELU) trained on {n} "
+                                f"(state, state + {args.learn_lag * DTAU:g} tau) pairs from 64 streak/roll descent "
+                                "trajectories at 32x33x32 Re 400; judged on 64 fresh guesses (seeds 2000-2063)",
+                      "pairs": n, "train_iters": args.learn_iters, "loss_first": losses[0],
+                      "loss_last": float(np.mean(losses[-20:])), "data_s": t_data, "train_s": t_train,
+                      "proposals_taken": taken, "proposals": 64 * rounds,
+                      "descent_steps_each": rounds * 520, "inference_s": t_inf,
+                      "J_plain_over_J_learned_geomean": float(np.exp(np.mean(np.log(Jp / Jl)))),
+                      "J_plain_median": float(np.median(Jp)), "J_learned_median": float(np.median(Jl))}
+    net.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -295,6 +417,8 @@ def run_ours(args):
                 "time_to_converge": ttc,
                 "roofline": roof, "clocks": ck, "wall_s": wall,
                 "J_after": [float(x) for x in J_last]}
+        if ws == 1 and not args.no_forms:
+            line["forms"] = run_forms(pcf, gi, flush, stream, dev, args)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(15.0)
         print(json.dumps(line), flush=True)
@@ -315,6 +439,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttc", action="store_true", help="skip the time-to-converge runs")
     ap.add_argument("--ttc-steps", type=int, default=20000)
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched/mixed/learned forms")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal form")
+    ap.add_argument("--learn-lag", type=int, default=5000, help="steps between a training pair's states")
+    ap.add_argument("--learn-iters", type=int, default=3000)
+    ap.add_argument("--learn-steps", type=int, default=4000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
