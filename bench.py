@@ -44,9 +44,11 @@ def _fft_flops(L):
     return 5.0 * L * math.log2(L)
 
 
-def kernel_flops(grid, batch):
+def kernel_flops(grid, batch, split=True):
     """Algorithmic FP64 flops per launch of each kernel class (FFT counted as 5 L log2 L,
-    dense Chebyshev matrices with parity folding as 2 flops per multiply-add)."""
+    dense Chebyshev matrices with parity folding as 2 flops per multiply-add, the Stokes
+    solve as the banded tau sweeps it replaces).  split: the per-mode work of a step runs as
+    analysis (yanalysis), solve (mode_phi / mode_psi) and synthesis (ysynth_step) kernels."""
     nx, ny, nz = grid
     Kx, Kz = nx // 3 - 1, nz // 3 - 1
     Mx, Mz = 2 * Kx + 1, Kz + 1
@@ -61,9 +63,15 @@ def kernel_flops(grid, batch):
     analysis = 3 * cheb_fold
     synth_y = 5 * cheb_fold
     solve = 2 * 2 * (8.0 * 3 * H + 6 * H) + 3 * 2 * (N + 1) * 4.0
-    mode_step = batch * nm * (analysis + solve + synth_y)
-    return {"xzsynth_u": synth, "xzsynth_q": synth, "prod_M": prod_M, "prod_N": prod_N,
-            "mode_phi": mode_step, "mode_psi": mode_step, "ysynth": batch * nm * synth_y}
+    out = {"xzsynth_u": synth, "xzsynth_q": synth, "prod_M": prod_M, "prod_N": prod_N,
+           "ysynth": batch * nm * synth_y, "jnorm": batch * ny * 4.0}
+    if split:
+        out.update(mode_phi=batch * nm * solve, mode_psi=batch * nm * solve, yanalysis=batch * nm * analysis,
+                   ysynth_step=batch * nm * synth_y)
+    else:
+        mode_step = batch * nm * (analysis + solve + synth_y)
+        out.update(mode_phi=mode_step, mode_psi=mode_step, yanalysis=0.0, ysynth_step=0.0)
+    return out
 
 
 class Clocks:
@@ -314,7 +322,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     seeds = list(range(rank * BATCH, rank * BATCH + BATCH))
     u0 = gi.batch(gi.streak_roll, seeds, *GRID)
-    s = pcf.Solver(*GRID, batch=BATCH, Re=RE, dt=DT, dtau_hat=DTAU_HAT)
+    s = pcf.Solver(*GRID, batch=BATCH, Re=RE, dt=DT, dtau_hat=DTAU_HAT, modes_per_block=args.mode_tile)
     u = torch.from_numpy(u0).to(dev)
     J0 = s.residual(u)[1].cpu().numpy()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -390,7 +398,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     kt = s.kernel_times()
     s.set_kernel_timing(False)
-    flops = kernel_flops(GRID, BATCH)
+    flops = kernel_flops(GRID, BATCH, split=kt["yanalysis"][1] > 0)
     total_ms = sum(v[0] for v in kt.values())
     dom = max(kt, key=lambda k: kt[k][0])
     dom_ms = kt[dom][0] / max(1, kt[dom][1])
@@ -400,7 +408,7 @@ def run_ours(args):
     roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_tf, 4), "unit": "TFLOP/s",
             "frac": round(achieved / peak_tf, 4), "traffic": None, "kernel": dom,
             "peak_source": "measured FP64 DFMA throughput (k_fp64_probe) on this GPU",
-            "kernel_share": round(kt[dom][0] / total_ms, 4),
+            "kernel_share": round(kt[dom][0] / total_ms, 4), "mode_tile": s.mode_tile(),
             "kernel_ms_per_launch": round(dom_ms, 5),
             "per_kernel_ms_per_step": {k: round(v[0] / nk, 5) for k, v in kt.items()}}
 
@@ -437,6 +445,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode-tile", type=int, default=0,
+                    help="tile of the per-mode kernels (instances per group of the split kernels); 0 = autotune")
     ap.add_argument("--no-ttc", action="store_true", help="skip the time-to-converge runs")
     ap.add_argument("--ttc-steps", type=int, default=20000)
     ap.add_argument("--no-forms", action="store_true", help="skip the batched/mixed/learned forms")

@@ -67,8 +67,13 @@ typedef struct pcf_params {
   double Lx, Lz, Re;
   double dt, dtau_hat;
   int precision;        /* pcf_precision; PCF_FP64 for the plain method */
-  int modes_per_block;  /* tile of the per-mode kernels; 0 = library default */
-  int solve_kind;       /* 0: dense per-mode operators when ny <= 65, else sweeps; 1: banded sweeps */
+  int modes_per_block;  /* tile of the per-mode kernels (Fourier modes per CTA of the single
+                           per-mode kernel; instances per group of the split kernels);
+                           0 = autotuned */
+  int solve_kind;       /* 0: dense per-mode operators when ny <= 129, else banded sweeps (FP64
+                           form, ny <= 97: the per-mode work as separate analysis, solve and
+                           synthesis kernels over instance groups); 1: banded sweeps; 2: dense
+                           operators inside the single per-mode kernel (same results as 0) */
   int reserved;
 } pcf_params;
 
@@ -109,7 +114,8 @@ pcf_status pcf_batch_create(const pcf_params* list, int n, void* stream, pcf_ctx
  * (instance = batch gives the total); -1 for an invalid instance. */
 long long pcf_state_offset(const pcf_ctx* ctx, int instance);
 
-/* Fourier modes per CTA chosen for the per-mode kernel (by the autotuner or the caller). */
+/* Fourier modes per CTA chosen for the per-mode kernels of the descent step (by the
+ * autotuner or the caller). */
 int pcf_mode_tile(const pcf_ctx* ctx);
 
 /* Release a context (waits for its stream).  NULL is ignored. */
@@ -248,7 +254,12 @@ pcf_status pcf_probe_fp64_peak(void* stream, double* gflops);
  * subsequent eager (non-graph) calls; pcf_kernel_times returns the accumulated
  * milliseconds and launch counts per kernel class (host arrays of length n).
  * Kernel classes: 0 ysynth, 1 xzsynth_u, 2 prod_M, 3 mode_phi, 4 xzsynth_q,
- * 5 prod_N, 6 mode_psi. */
+ * 5 prod_N, 6 mode_psi, 7 yanalysis, 8 ysynth_step, 9 jnorm.  In the FP64 form with
+ * dense per-mode operators (ny <= 97) the per-mode work of a step runs as three kernels:
+ * 7 (Chebyshev analysis + right-hand side, twice per step), 3/6 (Stokes solve and
+ * update of the NSE / dummy step), 8 (Chebyshev synthesis of r1 and of the new u), and
+ * 9 computes J, its history and the convergence mask once per step; otherwise 3/6 hold
+ * the whole per-mode kernel and 7, 8, 9 stay empty. */
 pcf_status pcf_set_kernel_timing(pcf_ctx* ctx, int enable);
 pcf_status pcf_kernel_times(pcf_ctx* ctx, double* ms, long long* launches, int n);
 

@@ -126,7 +126,8 @@ class Solver:
     ``Solver.batched([(nx, ny, nz, count), ...])`` builds a heterogeneous batch instead; its
     states are one flat complex128 tensor (``flat_len`` values, instance views via ``view``)."""
 
-    KERNEL_CLASSES = ["ysynth", "xzsynth_u", "prod_M", "mode_phi", "xzsynth_q", "prod_N", "mode_psi"]
+    KERNEL_CLASSES = ["ysynth", "xzsynth_u", "prod_M", "mode_phi", "xzsynth_q", "prod_N", "mode_psi",
+                      "yanalysis", "ysynth_step", "jnorm"]
 
     def __init__(self, nx, ny, nz, batch=1, Lx=LX_PAPER, Lz=LZ_PAPER, Re=400.0, dt=0.25, dtau_hat=0.25,
                  precision=0, modes_per_block=0, solve_kind=0):
@@ -143,14 +144,16 @@ class Solver:
         self.flat = False
 
     @classmethod
-    def batched(cls, grids, Lx=LX_PAPER, Lz=LZ_PAPER, Re=400.0, dt=0.25, dtau_hat=0.25, modes_per_block=0):
+    def batched(cls, grids, Lx=LX_PAPER, Lz=LZ_PAPER, Re=400.0, dt=0.25, dtau_hat=0.25, modes_per_block=0,
+                solve_kind=0):
         """grids: list of (nx, ny, nz, count)."""
         import torch
         self = cls.__new__(cls)
         self.lib = load_library()
         arr = (_Params * len(grids))()
         for k, (nx, ny, nz, cnt) in enumerate(grids):
-            arr[k] = _Params(nx, ny, nz, cnt, Lx, Lz, Re, dt, dtau_hat, 0, modes_per_block if k == 0 else 0, 0, 0)
+            arr[k] = _Params(nx, ny, nz, cnt, Lx, Lz, Re, dt, dtau_hat, 0, modes_per_block if k == 0 else 0,
+                             solve_kind, 0)
         h = ctypes.c_void_p()
         _check(self.lib.pcf_batch_create(arr, len(grids), _stream(), ctypes.byref(h)))
         self._h = h

@@ -29,6 +29,18 @@ struct pcf_ctx {
   int* pre_tca = nullptr;   // tensor-core analysis (mixed form)
   int cta_synth11 = 0, cta_synth3 = 0, cta_prod = 0, cta_mode = 0, cta_tcs = 0, cta_tca = 0;
   size_t sm_synth = 0, sm_prod = 0, sm_mode = 0, sm_tc = 0;
+  // split mode kernels (FP64 form with dense operators): instance groups and geometry
+  bool split = false;
+  int sgrp = 0;                 // largest instances per group
+  int ngroups = 0;
+  int2* d_groups = nullptr;     // [B] (first, count)
+  int* pre_ya = nullptr;        // CTA prefixes over groups [B + 1]
+  int* pre_ys = nullptr;
+  int* pre_yy = nullptr;
+  int cta_ya = 0, cta_ys = 0, cta_yy = 0;
+  int grid_ys = 0, buf_ys = 0, rows_ys = 0;  // persistent solve: CTAs, stage buffer, scratch rows
+  size_t sm_ya = 0, sm_ys = 0, sm_yy = 0;
+  double tuned_split_ms = 0.0;
   double2* r_int = nullptr;    // internal r1 buffer for descent
   double2* u_dev = nullptr;    // device state for the *_host entry point
   double* hist_dev = nullptr;

@@ -244,7 +244,7 @@ std::vector<double> make_dense_tables(int N, const std::vector<double>& kx, cons
             e[j] = 1.0;
             tau_solve(Mc, s, s + Mh, s + 2 * Mh, s + 3 * Mh, s[4 * Mh], rco.data() + RL.off(g, 0),
                       rco.data() + RL.off(g, 1), rco.data() + RL.off(g, 2), e.data(), 0.0, y.data());
-            for (int r = 0; r < Mc; ++r) d[DL.block(g, 4) + r * Mh + j] = y[r];
+            for (int r = 0; r < Mc; ++r) d[DL.at(g, 4, r, j)] = y[r];
           }
           continue;
         }
@@ -263,8 +263,8 @@ std::vector<double> make_dense_tables(int N, const std::vector<double>& kx, cons
             }
             std::fill(sc.begin(), sc.end(), 0.0);
             mode_chain(N, g, 0, kx[i], kz[p], sigma + k2, tab, rco.data(), Fr.data(), L2, sc.data());
-            for (int r = 0; r < McV; ++r) d[DL.block(g, src == 0 ? 0 : 1) + r * Mh + j] = sc[2 * Mh + r];
-            for (int r = 0; r < McP; ++r) d[DL.block(g, src == 0 ? 2 : 3) + r * Mh + j] = sc[3 * Mh + r];
+            for (int r = 0; r < McV; ++r) d[DL.at(g, src == 0 ? 0 : 1, r, j)] = sc[2 * Mh + r];
+            for (int r = 0; r < McP; ++r) d[DL.at(g, src == 0 ? 2 : 3, r, j)] = sc[3 * Mh + r];
           }
         }
         // eta: inverse Helmholtz of class pP
@@ -275,7 +275,7 @@ std::vector<double> make_dense_tables(int N, const std::vector<double>& kx, cons
           e[j] = 1.0;
           tau_solve(McP, s, s + Mh, s + 2 * Mh, s + 3 * Mh, s[4 * Mh], rco.data() + RL.off(pP, 0),
                     rco.data() + RL.off(pP, 1), rco.data() + RL.off(pP, 2), e.data(), 0.0, y.data());
-          for (int r = 0; r < McP; ++r) d[DL.block(g, 4) + r * Mh + j] = y[r];
+          for (int r = 0; r < McP; ++r) d[DL.at(g, 4, r, j)] = y[r];
         }
       }
     }
@@ -422,9 +422,28 @@ pcf_status launch_tc_synth(pcf_ctx* c, int slot) {
 pcf_status launch_tc_analysis(pcf_ctx* c) {
   return timed(c, 0, [&] { launch_cheb_analysis_tc(c->cta_tca, c->sm_tc, c->cs, li_of(c, c->pre_tca)); });
 }
+// split mode kernels of the FP64 descent step
+GroupLaunch gl_of(pcf_ctx* c, const int* pre) { return GroupLaunch{c->dinst, pre, c->d_groups, c->ngroups}; }
+pcf_status launch_split_analysis(pcf_ctx* c, int op) {
+  return timed(c, 7, [&] { launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), op); });
+}
+pcf_status launch_split_solve(pcf_ctx* c, int op) {
+  return timed(c, op == MODE_PHI ? 3 : 6, [&] {
+    launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_of(c, c->pre_ys), op);
+  });
+}
+pcf_status launch_split_jnorm(pcf_ctx* c, int step_index) {
+  return timed(c, 9, [&] { launch_jnorm(c->B, c->cs, c->dinst, step_index); });
+}
+pcf_status launch_split_synth(pcf_ctx* c, int slot, int in_step) {
+  return timed(c, in_step ? 8 : 0,
+               [&] { launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), slot, in_step); });
+}
+
 // y-synthesis of the state (slot 0) or of r1 (slot 1) in either form
 pcf_status launch_ysynth(pcf_ctx* c, int slot) {
   if (c->mixed) return launch_tc_synth(c, slot);
+  if (c->split) return launch_split_synth(c, slot, 0);
   return launch_mode(c, MODE_SYNTH_ONLY, slot, 0);
 }
 
@@ -476,6 +495,20 @@ pcf_status step_body(pcf_ctx* c, int s) {
     PCF_TRY(launch_mode(c, MODE_PSI_UPDATE, 1, s));
     return PCF_OK;
   }
+  if (c->split) {
+    PCF_TRY(launch_synth(c, 0, kFieldsSynth));
+    PCF_TRY(launch_prodM(c));
+    PCF_TRY(launch_split_analysis(c, MODE_PHI));
+    PCF_TRY(launch_split_solve(c, MODE_PHI));
+    PCF_TRY(launch_split_synth(c, 1, 1));
+    PCF_TRY(launch_synth(c, 1, kFieldsSynth));
+    PCF_TRY(launch_prodN(c));
+    PCF_TRY(launch_split_jnorm(c, s));
+    PCF_TRY(launch_split_analysis(c, MODE_PSI_UPDATE));
+    PCF_TRY(launch_split_solve(c, MODE_PSI_UPDATE));
+    PCF_TRY(launch_split_synth(c, 0, 1));
+    return PCF_OK;
+  }
   PCF_TRY(launch_synth(c, 0, kFieldsSynth));
   PCF_TRY(launch_prodM(c));
   PCF_TRY(launch_mode(c, MODE_PHI, 0, s));
@@ -521,7 +554,8 @@ long long pcf_psi_len(int nx, int ny, int nz) {
 
 static bool params_ok(const pcf_params* prm) {
   return grid_ok(prm->nx, prm->ny, prm->nz) && prm->batch >= 1 && prm->Re > 0 && prm->dt > 0 &&
-         prm->dtau_hat > 0 && prm->Lx > 0 && prm->Lz > 0;
+         prm->dtau_hat > 0 && prm->Lx > 0 && prm->Lz > 0 && prm->solve_kind >= 0 && prm->solve_kind <= 2 &&
+         prm->modes_per_block >= 0;
 }
 
 // Device tables of one grid (shared by every instance on that grid).
@@ -618,6 +652,106 @@ static pcf_status set_mode_tiles(pcf_ctx* c, int want) {
   return PCF_OK;
 }
 
+// Instance groups of the split mode kernels: runs of consecutive instances on the same grid,
+// at most G per group, and the derived launch geometry.
+static pcf_status set_split_groups(pcf_ctx* c, int G) {
+  int Nmax = 0;
+  for (const Inst& I : c->hinst) Nmax = std::max(Nmax, I.N);
+  G = std::max(1, std::min(G, split_max_group(Nmax)));
+  while (G > 1 && smem_ysolve(Nmax, G) > 227 * 1024) --G;
+  std::vector<int2> groups;
+  for (int b = 0; b < c->B; ++b) {
+    const Inst& I = c->hinst[b];
+    bool fresh = groups.empty() || groups.back().y == G;
+    if (!fresh) {
+      const Inst& P = c->hinst[b - 1];
+      fresh = I.dense[0] != P.dense[0] || I.dense[1] != P.dense[1] || I.cheb != P.cheb || I.nmodes != P.nmodes;
+    }
+    if (fresh) groups.push_back(make_int2(b, 1)); else groups.back().y += 1;
+  }
+  const int ng = (int)groups.size();
+  std::vector<int> pa(ng + 1, 0), ps(ng + 1, 0), py(ng + 1, 0);
+  size_t sa = 0, sy = 0;
+  int gmax = 1;
+  for (int q = 0; q < ng; ++q) {
+    const Inst& I = c->hinst[groups[q].x];
+    pa[q + 1] = pa[q] + split_ctas_per_group(0, I.nmodes);
+    ps[q + 1] = ps[q] + split_ctas_per_group(1, I.nmodes);
+    py[q + 1] = py[q] + split_ctas_per_group(2, I.nmodes);
+    sa = std::max(sa, smem_yanalysis(I.N, groups[q].y));
+    sy = std::max(sy, smem_ysynth(I.N, groups[q].y));
+    gmax = std::max(gmax, groups[q].y);
+  }
+  // the persistent solve lays out every item in buffers sized for the largest grid and group
+  const size_t ss = smem_ysolve(Nmax, gmax);
+  if (std::max(sa, std::max(ss, sy)) > 227 * 1024) return PCF_ENOTSUP;
+  if (!c->d_groups) {
+    if (ctx_alloc(c, &c->d_groups, (size_t)c->B) || ctx_alloc(c, &c->pre_ya, (size_t)c->B + 1) ||
+        ctx_alloc(c, &c->pre_ys, (size_t)c->B + 1) || ctx_alloc(c, &c->pre_yy, (size_t)c->B + 1))
+      return PCF_ENOMEM;
+  }
+  PCF_CUDA(cudaMemcpy(c->d_groups, groups.data(), sizeof(int2) * ng, cudaMemcpyHostToDevice));
+  PCF_CUDA(cudaMemcpy(c->pre_ya, pa.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
+  PCF_CUDA(cudaMemcpy(c->pre_ys, ps.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
+  PCF_CUDA(cudaMemcpy(c->pre_yy, py.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
+  c->sgrp = G;
+  c->ngroups = ng;
+  c->cta_ya = pa[ng];
+  c->cta_ys = ps[ng];
+  c->cta_yy = py[ng];
+  c->sm_ya = sa;
+  c->sm_ys = ss;
+  c->sm_yy = sy;
+  c->buf_ys = (int)ysolve_buffer(Nmax, gmax);
+  c->rows_ys = Nmax / 2 + 1;
+  PCF_CUDA(set_split_smem(sa, ss, sy));
+  int dev = 0, nsm = 0;
+  PCF_CUDA(cudaGetDevice(&dev));
+  PCF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int per_sm = std::max(1, ysolve_ctas_per_sm(ss));
+  c->grid_ys = std::min(c->cta_ys, nsm * per_sm);
+  return PCF_OK;
+}
+
+// Autotuner of the split mode kernels: time analysis + solve + synthesis of the NSE Stokes
+// step on the batch for each candidate group size and keep the fastest.
+static pcf_status autotune_split(pcf_ctx* c) {
+  const int cand[] = {1, 2, 4, 6, 8};
+  cudaEvent_t a, b;
+  PCF_CUDA(cudaEventCreate(&a));
+  PCF_CUDA(cudaEventCreate(&b));
+  int best = 2;
+  float best_ms = 1e30f;
+  int last = 0;
+  for (int G0 : cand) {
+    const int G = std::min(G0, c->B);
+    if (G == last) continue;
+    last = G;
+    if (set_split_groups(c, G) != PCF_OK) continue;
+    if (c->sgrp != G) continue;
+    auto seq = [&] {
+      launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), MODE_PHI);
+      launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_of(c, c->pre_ys), MODE_PHI);
+      launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), 1, 1);
+    };
+    seq();
+    PCF_CUDA(cudaEventRecord(a, c->cs));
+    for (int r = 0; r < 3; ++r) seq();
+    PCF_CUDA(cudaEventRecord(b, c->cs));
+    PCF_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    PCF_CUDA(cudaEventElapsedTime(&ms, a, b));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = G;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  c->tuned_split_ms = best_ms / 3.0;
+  return set_split_groups(c, best);
+}
+
 // Autotuner: time the Stokes-step mode kernel on the batch (laminar input) for each
 // candidate tile and keep the fastest.
 static pcf_status autotune_tiles(pcf_ctx* c) {
@@ -650,9 +784,15 @@ static pcf_status autotune_tiles(pcf_ctx* c) {
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  cudaFree(z);
   c->tuned_ms = best_ms / 3.0;
-  return set_mode_tiles(c, best);
+  pcf_status st = set_mode_tiles(c, best);
+  if (st == PCF_OK && c->split) {
+    st = push_descriptors(c);
+    if (st == PCF_OK) st = autotune_split(c);
+  }
+  if (cudaStreamSynchronize(c->cs) != cudaSuccess && st == PCF_OK) st = PCF_ECUDA;
+  cudaFree(z);
+  return st;
 }
 
 static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, pcf_ctx** out) {
@@ -712,7 +852,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
   }
 
   // per-instance workspace, one allocation per buffer kind
-  size_t n_yv = 0, n_ph = 0, n_xz = 0, n_np = 0;
+  size_t n_yv = 0, n_ph = 0, n_xz = 0, n_np = 0, n_fr = 0;
   c->state_off.assign(B + 1, 0);
   {
     int b = 0;
@@ -724,12 +864,13 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
         n_ph += 2ULL * kFieldsSynth * p.ny * p.nx * p.nz;
         n_xz += 3ULL * p.ny * nm;
         n_np += 3ULL * p.ny;
+        n_fr += 6ULL * (p.ny + 1) * nm;
         c->state_off[b + 1] = c->state_off[b] + 3LL * nm * p.ny;
       }
   }
   c->total_state = c->state_off[B];
   double2 *yv = nullptr, *xz = nullptr;
-  double *ph = nullptr, *np = nullptr;
+  double *ph = nullptr, *np = nullptr, *fr = nullptr;
   float2 *yvf = nullptr, *xzf = nullptr, *xzc = nullptr;
   float* phf = nullptr;
   if (ctx_alloc(c, &np, n_np) || ctx_alloc(c, &c->r_int, (size_t)c->total_state) || ctx_alloc(c, &c->active, (size_t)B))
@@ -738,11 +879,13 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
     if (ctx_alloc(c, &yvf, n_yv) || ctx_alloc(c, &phf, n_ph) || ctx_alloc(c, &xzf, n_xz) || ctx_alloc(c, &xzc, n_xz))
       return fail(PCF_ENOMEM);
   } else {
-    if (ctx_alloc(c, &yv, n_yv) || ctx_alloc(c, &ph, n_ph) || ctx_alloc(c, &xz, n_xz)) return fail(PCF_ENOMEM);
+    if (ctx_alloc(c, &yv, n_yv) || ctx_alloc(c, &ph, n_ph) || ctx_alloc(c, &xz, n_xz) || ctx_alloc(c, &fr, n_fr))
+      return fail(PCF_ENOMEM);
   }
   c->hinst.resize(B);
   std::vector<int> per11(B), per3(B), per1(B, 1), per_tcs(B), per_tca(B);
-  size_t o_yv = 0, o_ph = 0, o_xz = 0, o_np = 0;
+  size_t o_yv = 0, o_ph = 0, o_xz = 0, o_np = 0, o_fr = 0;
+  c->split = !c->mixed;
   int b = 0;
   for (int k = 0; k < nlist; ++k)
     for (int r = 0; r < list[k].batch; ++r, ++b) {
@@ -756,6 +899,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       radix_plan(p.nx, I.rx, &I.nrx);
       radix_plan(p.nz, I.rz, &I.nrz);
       I.nu = 1.0 / p.Re; I.dt = p.dt; I.dtau_hat = p.dtau_hat; I.dtau = 0.0;
+      I.inv_nu = 1.0 / I.nu; I.inv_dt = 1.0 / I.dt; I.inv_dtau_hat = 1.0 / I.dtau_hat;
       I.inv_nxnz = 1.0 / ((double)p.nx * p.nz);
       I.cheb = g.cheb; I.rco = g.rco; I.ygrid = g.y; I.ccw = g.ccw; I.kx = g.kx; I.kz = g.kz;
       I.twx = g.twx; I.twz = g.twz;
@@ -767,12 +911,14 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
         I.yvf = yvf + o_yv; I.physf = phf + o_ph; I.xzf = xzf + o_xz; I.xzc = xzc + o_xz;
         I.twxf = g.twxf; I.twzf = g.twzf; I.tcA = g.tcA; I.mixed = 1;
       } else {
-        I.yv = yv + o_yv; I.phys = ph + o_ph; I.xz = xz + o_xz;
+        I.yv = yv + o_yv; I.phys = ph + o_ph; I.xz = xz + o_xz; I.frg = fr + o_fr;
       }
+      if (!I.dense[0] || !I.dense[1] || p.solve_kind == 2 || smem_ysolve(I.N, 1) > 227 * 1024) c->split = false;
       o_yv += 2ULL * kFieldsY * p.ny * I.nmodes;
       o_ph += 2ULL * kFieldsSynth * p.ny * p.nx * p.nz;
       o_xz += 3ULL * p.ny * I.nmodes;
       o_np += 3ULL * p.ny;
+      o_fr += 6ULL * (p.ny + 1) * I.nmodes;
       I.hist_stride = B;
       per11[b] = kFieldsSynth * p.ny;
       per3[b] = 3 * p.ny;
@@ -798,6 +944,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
     return fail(PCF_ECUDA);
   const int want = list[0].modes_per_block;
   st = want > 0 ? set_mode_tiles(c, want) : autotune_tiles(c);
+  if (st == PCF_OK && want > 0 && c->split) st = set_split_groups(c, want);
   if (st != PCF_OK) return fail(st);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(PCF_ECUDA);
   *out = c;
@@ -818,7 +965,7 @@ long long pcf_state_offset(const pcf_ctx* c, int instance) {
   return c->state_off[instance];
 }
 
-int pcf_mode_tile(const pcf_ctx* c) { return c ? c->mpc : 0; }
+int pcf_mode_tile(const pcf_ctx* c) { return c ? (c->split ? c->sgrp : c->mpc) : 0; }
 
 void pcf_destroy(pcf_ctx* c) {
   if (!c) return;
@@ -1044,7 +1191,7 @@ pcf_status pcf_kernel_times(pcf_ctx* c, double* ms, long long* launches, int n) 
   return PCF_OK;
 }
 
-int pcf_launches_per_step(pcf_ctx* c) { return c ? (c->mixed ? 10 : 6) : 0; }
+int pcf_launches_per_step(pcf_ctx* c) { return c ? (c->split ? 11 : c->mixed ? 10 : 6) : 0; }
 
 pcf_status pcf_probe_fp64_peak(void* stream, double* gflops) {
   if (!gflops) return PCF_EINVAL;

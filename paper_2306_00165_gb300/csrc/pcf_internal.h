@@ -12,7 +12,7 @@ namespace pcf {
 constexpr int kMaxRadix = 8;     // max number of FFT stages
 constexpr int kFieldsSynth = 11; // u v w u_x u_y u_z v_x v_z w_x w_y w_z (v_y = -u_x - w_z)
 constexpr int kFieldsY = 5;      // y-values V_u V_v V_w and y-derivative values W_u W_w
-constexpr int kNumKernelClasses = 7;
+constexpr int kNumKernelClasses = 10;
 
 // ------------------------------------------------------------------ table layout
 // Chebyshev index n runs 0..N (N = ny - 1, even).  A parity class par holds the
@@ -32,7 +32,8 @@ struct TabLayout {
 };
 
 // Dense form of the same per-mode solve (used for N <= kDenseMaxN): for each parity group g
-// five Mh x Mh row-major blocks mapping the group's inputs to its outputs,
+// five Mh x Mh column-major blocks (element (r, j) at block + j Mh + r, so that threads
+// computing consecutive rows read consecutive addresses) mapping the group's inputs to its outputs,
 //   v  = Av f_v + Ag g,   xi = Xv f_v + Xg g,   eta = Eh h,
 // with f_v the v right-hand side (class g), g = Re/Im part of i(kx f_u + kz f_w) and
 // h = Re/Im part of i(kz f_u - kx f_w) (class 1-g).  For the mean mode, Eh of group g is
@@ -42,6 +43,7 @@ struct DenseLayout {
   int Mh;
   PCF_HD DenseLayout(int N) : Mh(N / 2 + 1) {}
   PCF_HD int block(int g, int k) const { return (g * 5 + k) * Mh * Mh; }  // k: 0 Av 1 Ag 2 Xv 3 Xg 4 Eh
+  PCF_HD int at(int g, int k, int r, int j) const { return block(g, k) + j * Mh + r; }
   PCF_HD int per_mode() const { return 10 * Mh * Mh; }
 };
 
@@ -81,6 +83,7 @@ struct Inst {
   int nrx, nrz;
   int rx[kMaxRadix], rz[kMaxRadix];
   double nu, dt, dtau_hat, dtau, inv_nxnz, tol;
+  double inv_nu, inv_dt, inv_dtau_hat;  // 1/nu, 1/dt, 1/dtau_hat (IEEE quotients, set on the host)
   // tables (device)
   const double* cheb;
   const double* rco;
@@ -103,6 +106,7 @@ struct Inst {
   double* phys;       // [2][11][ny][nx][nz]: slot 0 for u, slot 1 for q
   double2* xz;        // [3][ny][Mx][Mz]
   double* normpart;   // [3][ny]
+  double* frg;        // [nmodes][3][2][N + 2]: class-split Stokes right-hand sides (FP64 split mode kernels)
   // mixed-precision form: FP32 plane data and Chebyshev coefficients of the products
   float* physf;       // [2][11][ny][nx][nz]
   float2* yvf;        // [2][5][ny][Mx][Mz]

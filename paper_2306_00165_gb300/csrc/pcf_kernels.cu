@@ -200,7 +200,6 @@ size_t smem_plane(const Inst& I, int elem) {
 size_t smem_xzsynth(const Inst& I) { return smem_plane(I, sizeof(double2)); }
 size_t smem_prod(const Inst& I) { return smem_plane(I, sizeof(double2)); }
 
-__device__ __forceinline__ bool inst_active(const Inst& I) { return I.active == nullptr || *I.active != 0; }
 
 // ------------------------------------------------------------------ plane synthesis
 // CTA = (instance, y-plane j, field f).  Field f of slot: 0 u, 1 v, 2 w, 3 u_x, 4 u_y,
@@ -446,16 +445,6 @@ cudaError_t set_plane_smem(bool f32, size_t synth, size_t prod) {
   return cudaFuncSetAttribute(k_prod_t<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prod);
 }
 
-// J = sqrt(0.5 * sum_j w_j * mean_{x,z} |q|^2) from the plane sums (fixed order).
-__device__ double norm_from_parts(const Inst& I) {
-  double s = 0.0;
-  for (int j = 0; j < I.ny; ++j) {
-    const double pj = I.normpart[j] + I.normpart[I.ny + j] + I.normpart[2 * I.ny + j];
-    s = fma(I.ccw[j], pj, s);
-  }
-  return sqrt(0.5 * I.inv_nxnz * s);
-}
-
 __global__ void k_norm_final(LaunchInfo li, double* out) {
   for (int b = threadIdx.x; b < li.ninst; b += blockDim.x) out[b] = norm_from_parts(li.insts[b]);
 }
@@ -538,8 +527,8 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
   __syncthreads();
 
   const double step = sig == 0 ? I.dt : I.dtau_hat;
-  const double inv_step = 1.0 / step;
-  const double inv_nu = 1.0 / I.nu;
+  const double inv_step = sig == 0 ? I.inv_dt : I.inv_dtau_hat;  // = 1.0 / step
+  const double inv_nu = I.inv_nu;
   const int half = N / 2;
   if (solve) {
     if (I.mixed && op != MODE_SOLVE) {
@@ -624,35 +613,35 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
           // mean mode: u (which 0) and w (which 1) of class g
           const int Mc = (N - g) / 2 + 1;
           if (which == 2 || r >= Mc) continue;
-          const double* row = D + DL.block(g, 4) + r * Mh;
+          const double* col = D + DL.at(g, 4, r, 0);
           const double* f = fr + ((which == 0 ? 0 : 2) * 2 + rho) * L2 + g * Mh;
           double a = 0.0;
-          for (int j = 0; j < Mc; ++j) a = fma(__ldg(row + j), f[j], a);
+          for (int j = 0; j < Mc; ++j) a = fma(__ldg(col + j * Mh), f[j], a);
           sc[(which == 0 ? 0 : Mh) + r] = a;
           continue;
         }
         const double* fv = fr + (1 * 2 + rho) * L2 + pv * Mh;
         if (which == 0) {
           if (r >= McV) continue;
-          const double* ra = D + DL.block(g, 0) + r * Mh;
-          const double* rg = D + DL.block(g, 1) + r * Mh;
+          const double* ra = D + DL.at(g, 0, r, 0);
+          const double* rg = D + DL.at(g, 1, r, 0);
           double a = 0.0;
-          for (int j = 0; j < McV; ++j) a = fma(__ldg(ra + j), fv[j], a);
-          for (int j = 0; j < McP; ++j) a = fma(__ldg(rg + j), sc[j], a);
+          for (int j = 0; j < McV; ++j) a = fma(__ldg(ra + j * Mh), fv[j], a);
+          for (int j = 0; j < McP; ++j) a = fma(__ldg(rg + j * Mh), sc[j], a);
           sc[2 * Mh + r] = a;
         } else if (which == 1) {
           if (r >= McP) continue;
-          const double* ra = D + DL.block(g, 2) + r * Mh;
-          const double* rg = D + DL.block(g, 3) + r * Mh;
+          const double* ra = D + DL.at(g, 2, r, 0);
+          const double* rg = D + DL.at(g, 3, r, 0);
           double a = 0.0;
-          for (int j = 0; j < McV; ++j) a = fma(__ldg(ra + j), fv[j], a);
-          for (int j = 0; j < McP; ++j) a = fma(__ldg(rg + j), sc[j], a);
+          for (int j = 0; j < McV; ++j) a = fma(__ldg(ra + j * Mh), fv[j], a);
+          for (int j = 0; j < McP; ++j) a = fma(__ldg(rg + j * Mh), sc[j], a);
           sc[3 * Mh + r] = a;
         } else {
           if (r >= McP) continue;
-          const double* re = D + DL.block(g, 4) + r * Mh;
+          const double* re = D + DL.at(g, 4, r, 0);
           double a = 0.0;
-          for (int j = 0; j < McP; ++j) a = fma(__ldg(re + j), sc[Mh + j], a);
+          for (int j = 0; j < McP; ++j) a = fma(__ldg(re + j * Mh), sc[Mh + j], a);
           sc[4 * Mh + r] = a;
         }
       }
@@ -723,7 +712,7 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
   double2* gout = nullptr;
   double scale = 0.0;
   int slot = -1;
-  if (op == MODE_PHI) { gout = I.rhat; scale = 1.0 / I.dt; slot = 1; }
+  if (op == MODE_PHI) { gout = I.rhat; scale = I.inv_dt; slot = 1; }
   if (op == MODE_PSI_UPDATE) { slot = 0; }
   if (op == MODE_PSI_GRAD) { gout = I.fhat; }
   if (op == MODE_SOLVE) { gout = I.fhat; }

@@ -19,6 +19,14 @@ struct LaunchInfo {
   int ninst;
 };
 
+// Launch over groups of consecutive instances that share one grid.
+struct GroupLaunch {
+  const Inst* insts;
+  const int* prefix;   // CTA prefix over groups (length ngroups + 1)
+  const int2* groups;  // (first instance, instance count) per group
+  int ngroups;
+};
+
 __device__ __forceinline__ int find_inst(const LaunchInfo& li, int cta, int* local) {
   int lo = 0, hi = li.ninst - 1;
   while (lo < hi) {
@@ -27,6 +35,18 @@ __device__ __forceinline__ int find_inst(const LaunchInfo& li, int cta, int* loc
   }
   *local = cta - li.prefix[lo];
   return lo;
+}
+
+__device__ __forceinline__ bool inst_active(const Inst& I) { return I.active == nullptr || *I.active != 0; }
+
+// J = sqrt(0.5 * sum_j w_j * mean_{x,z} |q|^2) from the plane sums (fixed order).
+__device__ __forceinline__ double norm_from_parts(const Inst& I) {
+  double s = 0.0;
+  for (int j = 0; j < I.ny; ++j) {
+    const double pj = I.normpart[j] + I.normpart[I.ny + j] + I.normpart[2 * I.ny + j];
+    s = fma(I.ccw[j], pj, s);
+  }
+  return sqrt(0.5 * I.inv_nxnz * s);
 }
 
 void launch_xzsynth(bool f32, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int slot, int nf);
@@ -46,5 +66,25 @@ void launch_cheb_synth_tc(int ctas, size_t smem, cudaStream_t s, LaunchInfo li, 
 void launch_cheb_analysis_tc(int ctas, size_t smem, cudaStream_t s, LaunchInfo li);
 cudaError_t set_cheb_tc_smem(size_t smem);
 int cheb_tc_tiles(int nmodes);
+
+// Split mode kernels of the FP64 descent step (Chebyshev analysis, dense Stokes solve,
+// Chebyshev synthesis) over groups of instances on the same grid (at most
+// split_max_group() instances; G below is the largest group of a launch).
+// kind: 0 analysis, 1 solve, 2 synthesis.
+// The solve kernel is persistent (ctas <= nitems CTAs loop over the (group, mode, parity)
+// items, double-buffering each item's operands in shared memory).
+int split_ctas_per_group(int kind, int nmodes);
+int split_max_group(int N);
+size_t smem_yanalysis(int N, int G);
+size_t ysolve_buffer(int N, int G);
+size_t smem_ysolve(int N, int G);
+size_t smem_ysynth(int N, int G);
+void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op);
+void launch_ysolve(int ctas, int nitems, int bufsz, int scr_rows, size_t smem, cudaStream_t s, GroupLaunch gl,
+                   int op);
+void launch_jnorm(int ninst, cudaStream_t s, const Inst* insts, int step_index);
+int ysolve_ctas_per_sm(size_t smem);
+void launch_ysynth_split(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int slot, int check_active);
+cudaError_t set_split_smem(size_t analysis, size_t solve, size_t synth);
 
 }  // namespace pcf

@@ -1,0 +1,537 @@
+// The per-mode work of the FP64 descent step (paper §4, steps 1-5) as three streaming kernels
+// over groups of instances.
+//
+// k_mode performs the Chebyshev analysis, the Stokes solve and the Chebyshev synthesis of a
+// few Fourier modes of one instance in one CTA.  Every instance of a batch on the same grid
+// applies the same matrices to its own columns, so the descent step instead runs each phase
+// as a small batched matrix product whose right-hand sides are the columns of a group of up
+// to G instances (real and imaginary parts: 2 G columns), one CTA per sub-problem:
+//   k_yanalysis  CTA (group, mode, component c): parity-folded Chebyshev analysis of the
+//                product y-values and the right-hand side F = (state/step + product)/nu,
+//                written class-split to frg
+//   k_ysolve     CTA (group, mode, parity group g): the dense Stokes operators of group g
+//                (v of class g; xi = -dv/dy and eta of class 1-g), the assembly of v (class g)
+//                and u, w (class 1-g), and the finite-difference quotient: r1 = (u+ - u)/dt
+//                (PHI) or f = -(q+ - q)/dtau_hat followed by u += dtau f (PSI_UPDATE)
+//   k_ysynth     CTA (group, mode, output field q): Chebyshev synthesis of values
+//                (u, v, w) or y-derivative values (u_y, w_y) of u or r1 into yv
+// Matrices are staged in shared memory (the Chebyshev tables, and the five operator blocks of
+// the CTA's mode and parity group).  On GB300 a warp's FP64 instruction holds the FP64 pipe
+// for the same time whatever its active lanes, so every warp is kept full and branch-uniform:
+// a lane owns one column and two matrix rows (two independent accumulations sharing each
+// right-hand-side load), the columns of a group are padded to SP = 2, 4, 8 or 16 and a warp
+// covers 32/SP row pairs, and row lists with different loop structure (even / odd
+// Chebyshev rows; v and xi / eta) start on warp boundaries.  Shared-memory column arrays
+// have the odd row stride SP + 1 (no bank conflicts when a warp walks down a column).  Each
+// output is the same sequence of operations as in k_mode, so both paths give bit-identical
+// results.
+#include <algorithm>
+
+#include "pcf_kernels.cuh"
+
+namespace pcf {
+
+constexpr int kSplitThreads = 128;
+constexpr int kSolveThreads = 256;
+constexpr int kMaxGroup = 8;  // instances per group (16 columns)
+
+// frg of one instance: [mode][3][2][L2] doubles, L2 = 2 (N/2 + 1); class-split (even n at
+// n/2, odd n at N/2 + 1 + n/2).
+
+__device__ __forceinline__ int find_group(const GroupLaunch& gl, int cta, int* local) {
+  int lo = 0, hi = gl.ngroups - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (gl.prefix[mid] <= cta) lo = mid; else hi = mid - 1;
+  }
+  *local = cta - gl.prefix[lo];
+  return lo;
+}
+
+// Columns of a group of nI instances, padded to a power of two (SP divides 32).
+__device__ __forceinline__ int col_pad(int nI) {
+  int sp = 2;
+  while (sp < 2 * nI) sp <<= 1;
+  return sp;
+}
+__device__ __forceinline__ int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Per-instance flags of a group in shared memory: live[i] = instance takes part in this
+// launch (active; in the dummy-dynamics step the mask already holds this step's J < tol).
+__device__ __forceinline__ void group_flags(const GroupLaunch& gl, int first, int nI, int* live) {
+  if (threadIdx.x < nI) live[threadIdx.x] = inst_active(gl.insts[first + threadIdx.x]) ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int op) {
+  extern __shared__ double sm[];
+  __shared__ int live[kMaxGroup];
+  int local;
+  const int2 grp = gl.groups[find_group(gl, blockIdx.x, &local)];
+  const int first = grp.x, nI = grp.y;
+  const Inst& I0 = gl.insts[first];
+  const int N = I0.N, H = N / 2 + 1, Mh = H, L2 = 2 * H, ny = I0.ny, nm = I0.nmodes, half = N / 2;
+  const int m = local / 3, c = local - 3 * m;
+  const int SP = col_pad(nI), XS = SP + 1, RW = 32 / SP;
+  const ChebLayout CL(N);
+  double* Ae = sm;                 // [H][H]
+  double* Ao = Ae + H * H;         // [H][H] (rows < H-1 used)
+  double* VP = Ao + H * H;         // [H][XS]    P_j = V_j + V_{N-j} (j < N/2), V_{N/2}
+  double* VQ = VP + H * XS;        // [half][XS] Q_j = V_j - V_{N-j}
+  group_flags(gl, first, nI, live);
+  for (int t = threadIdx.x; t < 2 * H * H; t += blockDim.x) Ae[t] = I0.cheb[CL.Ae() + t];
+  for (int t = threadIdx.x; t < H * SP / 2; t += blockDim.x) {
+    const int i = t % (SP / 2), j = t / (SP / 2);
+    double2 a = make_double2(0.0, 0.0), b = a;
+    if (i < nI) {
+      const double2* xz = gl.insts[first + i].xz + (size_t)c * ny * nm + m;
+      a = xz[(size_t)j * nm];
+      if (j < half) b = xz[(size_t)(N - j) * nm];
+    }
+    double* p = VP + j * XS + 2 * i;
+    if (j < half) {
+      p[0] = a.x + b.x;
+      p[1] = a.y + b.y;
+      double* q = VQ + j * XS + 2 * i;
+      q[0] = a.x - b.x;
+      q[1] = a.y - b.y;
+    } else {
+      p[0] = a.x;
+      p[1] = a.y;
+    }
+  }
+  __syncthreads();
+  const double inv_step = op == MODE_PHI ? I0.inv_dt : I0.inv_dtau_hat, inv_nu = I0.inv_nu;
+  // row pairs (k, k + hE) of the even coefficients n = 2k (k < H, from P), then pairs
+  // (k, k + hO) of the odd coefficients n = 2k+1 (k < N/2, from Q)
+  const int hE = (H + 1) / 2, hO = (half + 1) / 2;
+  const int ER = round_up(hE, RW), OR = round_up(hO, RW);
+  for (int t = threadIdx.x; t < (ER + OR) * SP; t += blockDim.x) {
+    const int sc = t % SP, rs = t / SP;
+    const bool even = rs < ER;
+    const int nrow = even ? H : half, hh = even ? hE : hO;
+    const int k0 = even ? rs : rs - ER, k1 = k0 + hh;
+    const bool v0 = k0 < hh, v1 = v0 && k1 < nrow;
+    const int i = sc >> 1, part = sc & 1;
+    const bool out = i < nI && live[i];
+    const double* st = nullptr;
+    double u0a = 0.0, u0b = 0.0;
+    if (out) {
+      const Inst& I = gl.insts[first + i];
+      st = reinterpret_cast<const double*>((op == MODE_PHI ? I.uhat : I.rhat) + ((size_t)c * nm + m) * ny) + part;
+      if (v0) u0a = st[2 * (even ? 2 * k0 : 2 * k0 + 1)];
+      if (v1) u0b = st[2 * (even ? 2 * k1 : 2 * k1 + 1)];
+    }
+    const double* row0 = (even ? Ae : Ao) + (v0 ? k0 : 0) * H;
+    const double* row1 = (even ? Ae : Ao) + (v1 ? k1 : 0) * H;
+    const double* v = (even ? VP : VQ) + sc;
+    const int len = even ? H : half;  // P_j for j < H, Q_j for j < N/2
+    double a0 = 0.0, a1 = 0.0;
+    for (int j = 0; j < len; ++j) {
+      const double x = v[j * XS];
+      a0 = fma(row0[j], x, a0);
+      a1 = fma(row1[j], x, a1);
+    }
+    if (!out) continue;
+    double* fr = gl.insts[first + i].frg + ((size_t)m * 3 + c) * 2 * L2 + part * L2;
+    if (v0) fr[even ? k0 : Mh + k0] = fma(u0a, inv_step, a0) * inv_nu;
+    if (v1) fr[even ? k1 : Mh + k1] = fma(u0b, inv_step, a1) * inv_nu;
+  }
+}
+
+// ---------------------------------------------------------------- norm of r1
+// J = ||r1|| of every active instance from the plane sums of the adjoint product kernel
+// (same order of operations as norm_from_parts), its history entry, and the convergence
+// mask (J < tol: the instance stops before this step's update).  One CTA per instance;
+// ny <= 257 (the split kernels serve grids with dense operators, ny <= 129).
+__global__ void __launch_bounds__(128) k_jnorm(const Inst* insts, int step_index) {
+  __shared__ double part[3 * 257];
+  __shared__ double w[257];
+  const Inst& I = insts[blockIdx.x];
+  if (!inst_active(I)) return;
+  const int ny = I.ny;
+  for (int t = threadIdx.x; t < 3 * ny; t += blockDim.x) part[t] = I.normpart[t];
+  for (int t = threadIdx.x; t < ny; t += blockDim.x) w[t] = I.ccw[t];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double s = 0.0;
+  for (int j = 0; j < ny; ++j) s = fma(w[j], part[j] + part[ny + j] + part[2 * ny + j], s);
+  const double J = sqrt(0.5 * I.inv_nxnz * s);
+  if (I.hist) I.hist[(size_t)step_index * I.hist_stride] = J;
+  if (I.tol > 0.0 && J < I.tol && I.active) *I.active = 0;
+}
+
+// ---------------------------------------------------------------- Stokes solve
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(double* dst, const double* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+struct SolveItem {
+  int first, nI, m, g;
+};
+__device__ __forceinline__ SolveItem solve_item(const GroupLaunch& gl, int item) {
+  int local;
+  const int2 grp = gl.groups[find_group(gl, item, &local)];
+  return SolveItem{grp.x, grp.y, local >> 1, local & 1};
+}
+
+// Stage the five operator blocks of (mode m, parity group g) and the class-split right-hand
+// sides of the group's instances at mode m (6 (N+2) doubles each) into buf.
+__device__ __forceinline__ void solve_stage(const GroupLaunch& gl, const SolveItem& it, int sig, double* buf) {
+  const Inst& I0 = gl.insts[it.first];
+  const int N = I0.N, Mh = N / 2 + 1, per = 6 * (N + 2);
+  const DenseLayout DL(N);
+  const int n5 = 5 * Mh * Mh, n5p = (n5 + 1) & ~1;
+  const double* src = I0.dense[sig] + (size_t)it.m * DL.per_mode() + DL.block(it.g, 0);
+  for (int t = threadIdx.x; t < n5; t += blockDim.x) cp_async8(buf + t, src + t);
+  double* fr = buf + n5p;
+  const int hp = per / 2;
+  for (int t = threadIdx.x; t < it.nI * hp; t += blockDim.x) {
+    const int i = t / hp, k = t - i * hp;
+    cp_async16(fr + i * per + 2 * k, gl.insts[it.first + i].frg + (size_t)it.m * per + 2 * k);
+  }
+}
+
+// Persistent: CTA b takes the items b, b + gridDim.x, ...; the operands of the next item are
+// copied asynchronously while the current one is computed.  bufsz: doubles per stage buffer;
+// scratch after the two buffers: six [Mh][SP + 1] arrays for the largest grid of the launch.
+__global__ void __launch_bounds__(kSolveThreads) k_ysolve(GroupLaunch gl, int op, int nitems, int bufsz, int scr_rows) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ int live[kMaxGroup];
+  __shared__ double ik2_sh;
+  const int sig = op == MODE_PHI ? 0 : 1;
+  int item = blockIdx.x;
+  if (item >= nitems) return;
+  SolveItem cur = solve_item(gl, item);
+  solve_stage(gl, cur, sig, sm);
+  cp_commit();
+  for (int k = 0; item < nitems; ++k, item += gridDim.x) {
+    double* buf = sm + (size_t)(k & 1) * bufsz;
+    const int nxt = item + gridDim.x;
+    SolveItem nx = cur;
+    if (nxt < nitems) {
+      nx = solve_item(gl, nxt);
+      solve_stage(gl, nx, sig, sm + (size_t)((k + 1) & 1) * bufsz);
+    }
+    cp_commit();
+    cp_wait_prev();
+    const int first = cur.first, nI = cur.nI, m = cur.m, g = cur.g;
+    const Inst& I0 = gl.insts[first];
+    if (threadIdx.x < nI) live[threadIdx.x] = inst_active(gl.insts[first + threadIdx.x]) ? 1 : 0;
+    if (threadIdx.x == 32) {
+      // 1/k^2 of the mode, once per item (an FP64 division costs the pipe per lane-instruction)
+      const int Mz0 = I0.Mz, ix0 = m / Mz0;
+      const double kx0 = I0.kx[ix0], kz0 = I0.kz[m - ix0 * Mz0];
+      ik2_sh = (kx0 == 0.0 && kz0 == 0.0) ? 0.0 : 1.0 / (kx0 * kx0 + kz0 * kz0);
+    }
+    const int N = I0.N, Mh = N / 2 + 1, L2 = 2 * Mh, ny = I0.ny, nm = I0.nmodes, Mz = I0.Mz;
+    const int SP = col_pad(nI), XS = SP + 1, RW = 32 / SP;
+    const int pv = g, pP = 1 - g, McV = (N - pv) / 2 + 1, McP = (N - pP) / 2 + 1;
+    const int ix = m / Mz, p = m - ix * Mz;
+    const double kx = I0.kx[ix], kz = I0.kz[p];
+    const bool mean = kx == 0.0 && kz == 0.0;
+    const int MM = Mh * Mh, per = 6 * L2;
+    const double* D = buf;                          // [5][Mh][Mh] operator blocks of group g
+    const double* FR = buf + ((5 * MM + 1) & ~1);   // [nI][3][2][L2] right-hand sides
+    double* FV = sm + 2 * (size_t)bufsz;            // [Mh][XS] f_v (class g); mean mode: f_u (class g)
+    double* GG = FV + scr_rows * XS;                // [Mh][XS] g (class 1-g);   mean mode: f_w (class g)
+    double* HH = GG + scr_rows * XS;                // [Mh][XS] h (class 1-g)
+    double* OV = HH + scr_rows * XS;                // [Mh][XS] v (class g);     mean mode: u
+    double* OX = OV + scr_rows * XS;                // [Mh][XS] xi (class 1-g);  mean mode: w
+    double* OE = OX + scr_rows * XS;                // [Mh][XS] eta (class 1-g)
+    __syncthreads();
+    // right-hand sides: column s = 2 i + rho (instance i, real/imaginary part rho)
+    for (int t = threadIdx.x; t < Mh * SP; t += blockDim.x) {
+      const int s = t % SP, j = t / SP, i = s >> 1, rho = s & 1;
+      double fv = 0.0, gg = 0.0, hh = 0.0;
+      if (i < nI) {
+        const double* fr = FR + i * per;
+        if (mean) {
+          const int Mc = (N - g) / 2 + 1;
+          if (j < Mc) {
+            fv = fr[(0 * 2 + rho) * L2 + g * Mh + j];
+            gg = fr[(2 * 2 + rho) * L2 + g * Mh + j];
+          }
+        } else {
+          if (j < McV) fv = fr[(1 * 2 + rho) * L2 + pv * Mh + j];
+          if (j < McP) {
+            const double fu = fr[(0 * 2 + (1 - rho)) * L2 + pP * Mh + j];
+            const double fw = fr[(2 * 2 + (1 - rho)) * L2 + pP * Mh + j];
+            const double sgn = rho == 0 ? -1.0 : 1.0;  // Re(i a) = -Im a, Im(i a) = Re a
+            gg = sgn * fma(kx, fu, kz * fw);
+            hh = sgn * fma(kz, fu, -kx * fw);
+          }
+        }
+      }
+      FV[j * XS + s] = fv;
+      GG[j * XS + s] = gg;
+      HH[j * XS + s] = hh;
+    }
+    // outputs of this thread (assembly below): v rows, then u rows, then w rows per instance;
+    // their state values are loaded now and used after the products
+    const int nV = mean ? (N - g) / 2 + 1 : McV;
+    const int nU = mean ? nV : McP;
+    const int nout = nV + 2 * nU;
+    constexpr int kOut = 4;  // outputs per thread (nI * nout <= kOut * kSolveThreads)
+    double2 sa[kOut], sb[kOut];
+#pragma unroll
+    for (int q = 0; q < kOut; ++q) {
+      const int t = threadIdx.x + q * kSolveThreads;
+      sa[q] = sb[q] = make_double2(0.0, 0.0);
+      if (t >= nI * nout) continue;
+      const int i = t / nout, kk = t - i * nout;
+      if (!live[i]) continue;
+      const int comp = kk < nV ? 1 : (kk < nV + nU ? 0 : 2);
+      const int row = kk < nV ? kk : kk - nV - (kk < nV + nU ? 0 : nU);
+      const int n = (kk < nV ? (mean ? g : pv) : (mean ? g : pP)) + 2 * row;
+      const Inst& I = gl.insts[first + i];
+      const size_t gidx = ((size_t)comp * nm + m) * ny + n;
+      sa[q] = op == MODE_PHI ? I.uhat[gidx] : I.rhat[gidx];
+      if (op != MODE_PHI) sb[q] = I.uhat[gidx];
+    }
+    __syncthreads();
+    // v = Av f_v + Ag g, xi = Xv f_v + Xg g (row list A: v rows, then xi rows), eta = Eh h
+    // (row list B); mean mode: u = Eh f_u, w = Eh f_w (list A), no list B.  A thread takes
+    // the rows r and r + h of a list (h = half the list, rounded up).
+    {
+      const int Mc0 = (N - g) / 2 + 1;
+      const int nA = mean ? 2 * Mc0 : McV + McP, nB = mean ? 0 : McP;
+      const int hA = (nA + 1) / 2, hB = (nB + 1) / 2;
+      const int PA = round_up(hA, RW), PB = round_up(hB, RW);
+      for (int t = threadIdx.x; t < (PA + PB) * SP; t += blockDim.x) {
+        const int sc = t % SP, rs = t / SP;
+        double a0 = 0.0, a1 = 0.0;
+        double *out0, *out1;
+        bool v0, v1;
+        if (rs < PA) {
+          v0 = rs < hA;
+          v1 = v0 && rs + hA < nA;
+          const int r0 = v0 ? rs : 0, r1 = v1 ? rs + hA : 0;
+          if (mean) {
+            // r0 < Mc0 (u rows), r1 = r0 + Mc0 (w rows)
+            const double* col0 = D + 4 * MM + r0;
+            const double* col1 = D + 4 * MM + (v1 ? r1 - Mc0 : 0);
+            for (int j = 0; j < Mc0; ++j) {
+              a0 = fma(col0[j * Mh], FV[j * XS + sc], a0);
+              a1 = fma(col1[j * Mh], GG[j * XS + sc], a1);
+            }
+            out0 = OV + r0 * XS + sc;
+            out1 = OX + (v1 ? r1 - Mc0 : 0) * XS + sc;
+          } else {
+            const bool isv0 = r0 < McV, isv1 = r1 < McV;
+            const int rr0 = isv0 ? r0 : r0 - McV, rr1 = isv1 ? r1 : r1 - McV;
+            const double* cA0 = D + (isv0 ? 0 : 2) * MM + rr0;  // Av or Xv
+            const double* cA1 = D + (isv1 ? 0 : 2) * MM + rr1;
+            for (int j = 0; j < McV; ++j) {
+              const double x = FV[j * XS + sc];
+              a0 = fma(cA0[j * Mh], x, a0);
+              a1 = fma(cA1[j * Mh], x, a1);
+            }
+            const double* cG0 = cA0 + MM;                       // Ag or Xg
+            const double* cG1 = cA1 + MM;
+            for (int j = 0; j < McP; ++j) {
+              const double x = GG[j * XS + sc];
+              a0 = fma(cG0[j * Mh], x, a0);
+              a1 = fma(cG1[j * Mh], x, a1);
+            }
+            out0 = (isv0 ? OV : OX) + rr0 * XS + sc;
+            out1 = (isv1 ? OV : OX) + rr1 * XS + sc;
+          }
+        } else {
+          const int q = rs - PA;
+          v0 = q < hB;
+          v1 = v0 && q + hB < nB;
+          const int r0 = v0 ? q : 0, r1 = v1 ? q + hB : 0;
+          const double* c0 = D + 4 * MM + r0;
+          const double* c1 = D + 4 * MM + r1;
+          for (int j = 0; j < McP; ++j) {
+            const double x = HH[j * XS + sc];
+            a0 = fma(c0[j * Mh], x, a0);
+            a1 = fma(c1[j * Mh], x, a1);
+          }
+          out0 = OE + r0 * XS + sc;
+          out1 = OE + r1 * XS + sc;
+        }
+        if (v0) *out0 = a0;
+        if (v1) *out1 = a1;
+      }
+    }
+    __syncthreads();
+    // assembly and output: v (class g) and u, w (class 1-g); mean mode: u, v = 0, w (class g)
+    const double inv_step = op == MODE_PHI ? I0.inv_dt : I0.inv_dtau_hat;
+    const double ik2 = ik2_sh;
+#pragma unroll
+    for (int q = 0; q < kOut; ++q) {
+      const int t = threadIdx.x + q * kSolveThreads;
+      if (t >= nI * nout) continue;
+      const int i = t / nout, kk = t - i * nout;
+      if (!live[i]) continue;
+      int comp, row, n;
+      double vr, vi;
+      if (kk < nV) {
+        comp = 1;
+        row = kk;
+        n = (mean ? g : pv) + 2 * row;
+        vr = mean ? 0.0 : OV[row * XS + 2 * i];
+        vi = mean ? 0.0 : OV[row * XS + 2 * i + 1];
+      } else {
+        const bool isu = kk < nV + nU;
+        comp = isu ? 0 : 2;
+        row = kk - nV - (isu ? 0 : nU);
+        n = (mean ? g : pP) + 2 * row;
+        if (mean) {
+          const double* src = isu ? OV : OX;
+          vr = src[row * XS + 2 * i];
+          vi = src[row * XS + 2 * i + 1];
+        } else {
+          const double xr = OX[row * XS + 2 * i], xi = OX[row * XS + 2 * i + 1];
+          const double er = OE[row * XS + 2 * i], ei = OE[row * XS + 2 * i + 1];
+          if (isu) {
+            vr = fma(kx, xi, kz * ei) * ik2;
+            vi = -fma(kx, xr, kz * er) * ik2;
+          } else {
+            vr = fma(kz, xi, -kx * ei) * ik2;
+            vi = fma(-kz, xr, kx * er) * ik2;
+          }
+        }
+      }
+      const Inst& I = gl.insts[first + i];
+      const size_t gidx = ((size_t)comp * nm + m) * ny + n;
+      if (op == MODE_PHI) {
+        I.rhat[gidx] = make_double2((vr - sa[q].x) * inv_step, (vi - sa[q].y) * inv_step);
+      } else {
+        const double fr = -(vr - sa[q].x) * inv_step;
+        const double fi = -(vi - sa[q].y) * inv_step;
+        I.uhat[gidx] = make_double2(fma(I.dtau, fr, sb[q].x), fma(I.dtau, fi, sb[q].y));
+      }
+    }
+    __syncthreads();  // buffer and scratch are reused by the next item
+    cur = nx;
+  }
+}
+
+// slot 0: synthesis of uhat, slot 1: of rhat.  q = 0..4: V_u V_v V_w W_u W_w.
+__global__ void __launch_bounds__(kSplitThreads) k_ysynth(GroupLaunch gl, int slot, int check_active) {
+  extern __shared__ double sm[];
+  __shared__ int live[kMaxGroup];
+  int local;
+  const int2 grp = gl.groups[find_group(gl, blockIdx.x, &local)];
+  const int first = grp.x, nI = grp.y;
+  const Inst& I0 = gl.insts[first];
+  const int N = I0.N, H = N / 2 + 1, ny = I0.ny, nm = I0.nmodes, half = N / 2;
+  const int m = local / kFieldsY, qf = local - kFieldsY * m;
+  const int c = qf < 3 ? qf : (qf == 3 ? 0 : 2);
+  const bool deriv = qf >= 3;
+  const int SP = col_pad(nI), XS = SP + 1, RW = 32 / SP;
+  const ChebLayout CL(N);
+  double* ME = sm;                  // [H][H] Ce or De
+  double* MO = ME + H * H;          // [H][H] Co or Do (columns < H-1 used)
+  double* AE = MO + H * H;          // [H][XS] even coefficients a_{2k}
+  double* AO = AE + H * XS;         // [H-1][XS] odd coefficients a_{2k+1}
+  if (threadIdx.x < nI) live[threadIdx.x] = (!check_active || inst_active(gl.insts[first + threadIdx.x])) ? 1 : 0;
+  const double* tabE = I0.cheb + (deriv ? CL.De() : CL.Ce());
+  const double* tabO = I0.cheb + (deriv ? CL.Do() : CL.Co());
+  for (int t = threadIdx.x; t < H * H; t += blockDim.x) {
+    ME[t] = tabE[t];
+    MO[t] = tabO[t];
+  }
+  for (int t = threadIdx.x; t < ny * (SP / 2); t += blockDim.x) {
+    const int n = t % ny, i = t / ny;
+    double2 v = make_double2(0.0, 0.0);
+    if (i < nI) v = (slot == 0 ? gl.insts[first + i].uhat : gl.insts[first + i].rhat)[((size_t)c * nm + m) * ny + n];
+    double* d = ((n & 1) ? AO : AE) + (n >> 1) * XS + 2 * i;
+    d[0] = v.x;
+    d[1] = v.y;
+  }
+  __syncthreads();
+  // rows j and j + hJ of the output (hJ = H/2 rounded up), values at y_j and y_{N-j}
+  const int hJ = (H + 1) / 2, JR = round_up(hJ, RW);
+  for (int t = threadIdx.x; t < JR * SP; t += blockDim.x) {
+    const int sc = t % SP, j0 = t / SP, j1 = j0 + hJ;
+    const bool v0 = j0 < hJ, v1 = v0 && j1 < H;
+    const double* re0 = ME + (v0 ? j0 : 0) * H;
+    const double* ro0 = MO + (v0 ? j0 : 0) * H;
+    const double* re1 = ME + (v1 ? j1 : 0) * H;
+    const double* ro1 = MO + (v1 ? j1 : 0) * H;
+    double e0 = 0.0, o0 = 0.0, e1 = 0.0, o1 = 0.0;
+    for (int k = 0; k < H; ++k) {
+      const double x = AE[k * XS + sc];
+      e0 = fma(re0[k], x, e0);
+      e1 = fma(re1[k], x, e1);
+    }
+    for (int k = 0; k < H - 1; ++k) {
+      const double x = AO[k * XS + sc];
+      o0 = fma(ro0[k], x, o0);
+      o1 = fma(ro1[k], x, o1);
+    }
+    const int i = sc >> 1, part = sc & 1;
+    if (!v0 || i >= nI || !live[i]) continue;
+    double* dst = reinterpret_cast<double*>(gl.insts[first + i].yv + ((size_t)slot * kFieldsY + qf) * ny * nm + m) + part;
+    // T_{2k} even, T_{2k+1} odd in y; T'_{2k} odd, T'_{2k+1} even
+    dst[(size_t)j0 * nm * 2] = e0 + o0;
+    if (j0 < half) dst[(size_t)(N - j0) * nm * 2] = deriv ? o0 - e0 : e0 - o0;
+    if (v1) {
+      dst[(size_t)j1 * nm * 2] = e1 + o1;
+      if (j1 < half) dst[(size_t)(N - j1) * nm * 2] = deriv ? o1 - e1 : e1 - o1;
+    }
+  }
+}
+
+int split_ctas_per_group(int kind, int nmodes) { return nmodes * (kind == 0 ? 3 : kind == 1 ? 2 : kFieldsY); }
+// Largest group on a grid: kMaxGroup, and the solve's four outputs per thread
+// (G (N/2 + 1) 3 <= 4 kSolveThreads).
+int split_max_group(int N) { return std::min(kMaxGroup, 4 * kSolveThreads / (3 * (N / 2 + 1))); }
+static size_t col_pad_host(int G) {
+  size_t sp = 2;
+  while (sp < 2 * (size_t)G) sp <<= 1;
+  return sp;
+}
+size_t smem_yanalysis(int N, int G) {
+  const size_t H = N / 2 + 1, XS = col_pad_host(G) + 1;
+  return sizeof(double) * (2 * H * H + (2 * H) * XS);
+}
+// Stage buffer of the persistent solve (doubles): operator blocks + right-hand sides of G instances.
+size_t ysolve_buffer(int N, int G) {
+  const size_t Mh = N / 2 + 1, n5p = (5 * Mh * Mh + 1) & ~(size_t)1;
+  return n5p + (size_t)G * 6 * (N + 2);
+}
+size_t smem_ysolve(int N, int G) {
+  const size_t Mh = N / 2 + 1, XS = col_pad_host(G) + 1;
+  return sizeof(double) * (2 * ysolve_buffer(N, G) + 6 * Mh * XS);
+}
+size_t smem_ysynth(int N, int G) {
+  const size_t H = N / 2 + 1, XS = col_pad_host(G) + 1;
+  return sizeof(double) * (2 * H * H + (2 * H) * XS);
+}
+void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op) {
+  k_yanalysis<<<ctas, kSplitThreads, smem, s>>>(gl, op);
+}
+void launch_ysolve(int ctas, int nitems, int bufsz, int scr_rows, size_t smem, cudaStream_t s, GroupLaunch gl,
+                   int op) {
+  k_ysolve<<<ctas, kSolveThreads, smem, s>>>(gl, op, nitems, bufsz, scr_rows);
+}
+void launch_jnorm(int ninst, cudaStream_t s, const Inst* insts, int step_index) {
+  k_jnorm<<<ninst, 128, 0, s>>>(insts, step_index);
+}
+int ysolve_ctas_per_sm(size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ysolve, kSolveThreads, smem) != cudaSuccess) return 0;
+  return n;
+}
+void launch_ysynth_split(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int slot, int check_active) {
+  k_ysynth<<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active);
+}
+cudaError_t set_split_smem(size_t analysis, size_t solve, size_t synth) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_yanalysis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)analysis))) return e;
+  if ((e = cudaFuncSetAttribute(k_ysolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve))) return e;
+  return cudaFuncSetAttribute(k_ysynth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)synth);
+}
+
+}  // namespace pcf

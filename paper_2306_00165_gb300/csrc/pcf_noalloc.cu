@@ -228,6 +228,8 @@ extern "C" pcf_status pcf_influence_matrix_solve_noalloc(const pcf_params* prm, 
   I.nu = 1.0 / prm->Re;
   I.dt = step;
   I.dtau_hat = step;
+  I.inv_nu = 1.0 / I.nu;
+  I.inv_dt = I.inv_dtau_hat = 1.0 / step;
   I.inv_nxnz = 1.0 / ((double)prm->nx * prm->nz);
   I.rco = base + L.rco;
   I.cheb = base + L.cheb;
