@@ -315,6 +315,20 @@ __device__ __forceinline__ void product_pair(const Inst& I, const T* const* U, c
   }
 }
 
+// Products of the rows r0 .. r0 + nrc - 1 of a plane for component CC (a compile-time
+// constant, so that the field indices fold and the plane pointers stay in registers).
+template <class T, bool ADJ, int CC>
+__device__ __forceinline__ void product_rows(const Inst& I, const T* const* U, const T* const* Q, T y, int r0,
+                                             int nrc, int nz, typename Cx<T>::c* Z0, double* sq) {
+  for (int t = threadIdx.x; t < nrc * nz; t += blockDim.x) {
+    const int r = t / nz, z = t - r * nz;
+    const int e0 = (2 * (r0 + r)) * nz + z, e1 = e0 + nz;
+    T m[2];
+    product_pair<T, ADJ>(I, U, Q, CC, y, e0, e1, m, sq);
+    Z0[t] = Cx<T>::mk(m[0], m[1]);
+  }
+}
+
 // CTA = (instance, plane j, component c): product component c on the plane (M(u) or
 // N(q) with U = (y + u, v, w)), forward FFT in z then x, 2/3 truncation.  ADJ also sums
 // q_c^2 over the plane (in FP64) for J.
@@ -354,13 +368,9 @@ __global__ void __launch_bounds__(128) k_prod_t(LaunchInfo li) {
     const int nrc = min(pp.chunk, nr - r0);
     C* Z0 = whole ? B0 : B1;
     C* Z1 = whole ? B1 : B1 + pp.chunk * nz;
-    for (int t = threadIdx.x; t < nrc * nz; t += blockDim.x) {
-      const int r = t / nz, z = t - r * nz;
-      const int e0 = (2 * (r0 + r)) * nz + z, e1 = e0 + nz;
-      T m[2];
-      product_pair<T, ADJ>(I, U, Q, c, y, e0, e1, m, &sq);
-      Z0[t] = Cx<T>::mk(m[0], m[1]);
-    }
+    if (c == 0) product_rows<T, ADJ, 0>(I, U, Q, y, r0, nrc, nz, Z0, &sq);
+    else if (c == 1) product_rows<T, ADJ, 1>(I, U, Q, y, r0, nrc, nz, Z0, &sq);
+    else product_rows<T, ADJ, 2>(I, U, Q, y, r0, nrc, nz, Z0, &sq);
     __syncthreads();
     C* R = fft_run<C>(Z0, Z1, nz, nrc, I.rz, I.nrz, twz, false);
     if (whole) X = (R == B0) ? B1 : B0;
