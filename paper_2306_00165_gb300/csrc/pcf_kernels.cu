@@ -117,10 +117,12 @@ __device__ __forceinline__ void butterfly<3, double2>(double2* v, bool inv) { bu
 template <>
 __device__ __forceinline__ void butterfly<3, float2>(float2* v, bool inv) { butterfly3(v, inv); }
 
-// One radix-R pass over nb contiguous batches of length L (Stockham autosort).
+// One radix-R pass over nb batches of length L, batch b at b LS (Stockham autosort).  The
+// plane kernels use LS = L + 1: a warp that walks down a column of a batch array then meets
+// 32 different banks.
 template <int R, class C>
-__device__ __forceinline__ void stockham_pass(const C* __restrict__ a, C* __restrict__ b, int L, int nb, int Ns,
-                                              const C* __restrict__ tw, bool inv) {
+__device__ __forceinline__ void stockham_pass(const C* __restrict__ a, C* __restrict__ b, int L, int LS, int nb,
+                                              int Ns, const C* __restrict__ tw, bool inv) {
   const int nq = L / R;
   const int total = nq * nb;
   const int twstep = L / (Ns * R);
@@ -128,7 +130,7 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ a, C* __rest
     const int bi = t / nq;
     const int j = t - bi * nq;
     const int k = j % Ns;
-    const C* ab = a + bi * L;
+    const C* ab = a + bi * LS;
     C v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = ab[j + r * nq];
@@ -142,21 +144,21 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ a, C* __rest
     }
     butterfly<R, C>(v, inv);
     const int idx = (j / Ns) * Ns * R + k;
-    C* bb = b + bi * L;
+    C* bb = b + bi * LS;
 #pragma unroll
     for (int r = 0; r < R; ++r) bb[idx + r * Ns] = v[r];
   }
 }
 
-// Full transform of nb batches; a holds the input; returns the buffer with the result.
+// Full transform of nb batches (stride LS); a holds the input; returns the buffer with the result.
 template <class C>
-__device__ C* fft_run(C* a, C* b, int L, int nb, const int* radix, int nr, const C* tw, bool inv) {
+__device__ C* fft_run(C* a, C* b, int L, int LS, int nb, const int* radix, int nr, const C* tw, bool inv) {
   int Ns = 1;
   for (int s = 0; s < nr; ++s) {
     const int R = radix[s];
-    if (R == 4) stockham_pass<4, C>(a, b, L, nb, Ns, tw, inv);
-    else if (R == 2) stockham_pass<2, C>(a, b, L, nb, Ns, tw, inv);
-    else stockham_pass<3, C>(a, b, L, nb, Ns, tw, inv);
+    if (R == 4) stockham_pass<4, C>(a, b, L, LS, nb, Ns, tw, inv);
+    else if (R == 2) stockham_pass<2, C>(a, b, L, LS, nb, Ns, tw, inv);
+    else stockham_pass<3, C>(a, b, L, LS, nb, Ns, tw, inv);
     __syncthreads();
     C* t = a;
     a = b;
@@ -174,21 +176,25 @@ __device__ __forceinline__ void load_twiddles(const Inst& I, typename Cx<T>::c* 
   for (int t = threadIdx.x; t < I.nz; t += blockDim.x) twz[t] = sz[t];
 }
 
-// Shared-memory plan of a plane transform: two buffers of PB complex values.  The z stage
-// handles `chunk` row pairs at a time: all of them when both stages fit the budget, else
-// as many as fit (two ping-pong buffers) inside the partner of the x-stage buffer.
+// Shared-memory plan of a plane transform: two buffers of PB complex values; x-stage
+// batches (one per retained z mode) have stride LX = nx + 1, z-stage batches (one per row
+// pair) stride LZ = nz + 1.  The z stage handles `chunk` row pairs at a time: all of them
+// when both stages fit the budget, else as many as fit (two ping-pong buffers) inside the
+// partner of the x-stage buffer.
 struct PlanePlan {
-  int PB, chunk;
+  int PB, chunk, LX, LZ;
 };
 __host__ __device__ inline PlanePlan plane_plan(const Inst& I, int elem) {
-  const int a = I.Mz * I.nx, b = (I.nx / 2) * I.nz;
   PlanePlan pp;
+  pp.LX = I.nx + 1;
+  pp.LZ = I.nz + 1;
+  const int a = I.Mz * pp.LX, b = (I.nx / 2) * pp.LZ;
   if ((size_t)2 * (a > b ? a : b) * elem <= 100 * 1024) {
     pp.PB = a > b ? a : b;
     pp.chunk = I.nx / 2;
   } else {
     pp.PB = a;
-    pp.chunk = a / (2 * I.nz);
+    pp.chunk = a / (2 * pp.LZ);
     if (pp.chunk < 1) pp.chunk = 1;
   }
   return pp;
@@ -224,7 +230,8 @@ __global__ void __launch_bounds__(128) k_xzsynth_t(LaunchInfo li, int slot, int 
   C* twx = sm + 2 * pp.PB;
   C* twz = twx + nx;
   load_twiddles<T>(I, twx, twz);
-  for (int t = threadIdx.x; t < Mz * nx; t += blockDim.x) B0[t] = Cx<T>::mk(0, 0);
+  const int LX = pp.LX, LZ = pp.LZ;
+  for (int t = threadIdx.x; t < Mz * LX; t += blockDim.x) B0[t] = Cx<T>::mk(0, 0);
   __syncthreads();
   const C* src = yv_of<T>(I) + (((size_t)slot * kFieldsY + c_src[f]) * I.ny + j) * (size_t)I.nmodes;
   const int fac = c_fac[f];
@@ -233,17 +240,17 @@ __global__ void __launch_bounds__(128) k_xzsynth_t(LaunchInfo li, int slot, int 
     C s = src[t];
     if (fac == 1) { const T k = (T)I.kx[i]; s = Cx<T>::mk(-k * s.y, k * s.x); }
     else if (fac == 2) { const T k = (T)I.kz[p]; s = Cx<T>::mk(-k * s.y, k * s.x); }
-    B0[p * nx + xbin(i, Kx, Mx, nx)] = s;
+    B0[p * LX + xbin(i, Kx, Mx, nx)] = s;
   }
   __syncthreads();
-  C* G = fft_run<C>(B0, B1, nx, Mz, I.rx, I.nrx, twx, true);
+  C* G = fft_run<C>(B0, B1, nx, LX, Mz, I.rx, I.nrx, twx, true);
   C* Zb = (G == B0) ? B1 : B0;
   const int nr = nx / 2;
   T* out = phys_of<T>(I) + (((size_t)slot * kFieldsSynth + f) * I.ny + j) * (size_t)nx * nz;
   for (int r0 = 0; r0 < nr; r0 += pp.chunk) {
     const int nrc = min(pp.chunk, nr - r0);
     C* Z0 = Zb;
-    C* Z1 = (pp.chunk == nr) ? G : Zb + pp.chunk * nz;
+    C* Z1 = (pp.chunk == nr) ? G : Zb + pp.chunk * LZ;
     for (int t = threadIdx.x; t < nrc * nz; t += blockDim.x) {
       const int r = t / nz, z = t - r * nz;
       const int x1 = 2 * (r0 + r), x2 = x1 + 1;
@@ -251,20 +258,20 @@ __global__ void __launch_bounds__(128) k_xzsynth_t(LaunchInfo li, int slot, int 
       if (z == 0) {
         h = Cx<T>::mk(G[x1].x, G[x2].x);
       } else if (z <= Kz) {
-        const C g1 = G[z * nx + x1], g2 = G[z * nx + x2];
+        const C g1 = G[z * LX + x1], g2 = G[z * LX + x2];
         h = Cx<T>::mk(g1.x - g2.y, g1.y + g2.x);
       } else if (z >= nz - Kz) {
         const int p = nz - z;
-        const C g1 = G[p * nx + x1], g2 = G[p * nx + x2];
+        const C g1 = G[p * LX + x1], g2 = G[p * LX + x2];
         h = Cx<T>::mk(g1.x + g2.y, g2.x - g1.y);
       }
-      Z0[t] = h;
+      Z0[r * LZ + z] = h;
     }
     __syncthreads();
-    C* Rz = fft_run<C>(Z0, Z1, nz, nrc, I.rz, I.nrz, twz, true);
+    C* Rz = fft_run<C>(Z0, Z1, nz, LZ, nrc, I.rz, I.nrz, twz, true);
     for (int t = threadIdx.x; t < nrc * nz; t += blockDim.x) {
       const int r = t / nz, z = t - r * nz;
-      const C h = Rz[t];
+      const C h = Rz[r * LZ + z];
       out[(2 * (r0 + r)) * nz + z] = h.x;
       out[(2 * (r0 + r) + 1) * nz + z] = h.y;
     }
@@ -319,13 +326,13 @@ __device__ __forceinline__ void product_pair(const Inst& I, const T* const* U, c
 // constant, so that the field indices fold and the plane pointers stay in registers).
 template <class T, bool ADJ, int CC>
 __device__ __forceinline__ void product_rows(const Inst& I, const T* const* U, const T* const* Q, T y, int r0,
-                                             int nrc, int nz, typename Cx<T>::c* Z0, double* sq) {
+                                             int nrc, int nz, int LZ, typename Cx<T>::c* Z0, double* sq) {
   for (int t = threadIdx.x; t < nrc * nz; t += blockDim.x) {
     const int r = t / nz, z = t - r * nz;
     const int e0 = (2 * (r0 + r)) * nz + z, e1 = e0 + nz;
     T m[2];
     product_pair<T, ADJ>(I, U, Q, CC, y, e0, e1, m, sq);
-    Z0[t] = Cx<T>::mk(m[0], m[1]);
+    Z0[r * LZ + z] = Cx<T>::mk(m[0], m[1]);
   }
 }
 
@@ -358,7 +365,7 @@ __global__ void __launch_bounds__(128) k_prod_t(LaunchInfo li) {
     Q[f] = ADJ ? fplane<T>(I, 1, f, j) : nullptr;
   }
   const T y = (T)I.ygrid[j];
-  const int nr = nx / 2;
+  const int nr = nx / 2, LX = pp.LX, LZ = pp.LZ;
   const bool whole = pp.chunk == nr;
   // the x-stage input X[p][x] lives in B0 when chunked (z chunks use B1), else decided below
   C* X = B0;
@@ -367,20 +374,20 @@ __global__ void __launch_bounds__(128) k_prod_t(LaunchInfo li) {
   for (int r0 = 0; r0 < nr; r0 += pp.chunk) {
     const int nrc = min(pp.chunk, nr - r0);
     C* Z0 = whole ? B0 : B1;
-    C* Z1 = whole ? B1 : B1 + pp.chunk * nz;
-    if (c == 0) product_rows<T, ADJ, 0>(I, U, Q, y, r0, nrc, nz, Z0, &sq);
-    else if (c == 1) product_rows<T, ADJ, 1>(I, U, Q, y, r0, nrc, nz, Z0, &sq);
-    else product_rows<T, ADJ, 2>(I, U, Q, y, r0, nrc, nz, Z0, &sq);
+    C* Z1 = whole ? B1 : B1 + pp.chunk * LZ;
+    if (c == 0) product_rows<T, ADJ, 0>(I, U, Q, y, r0, nrc, nz, LZ, Z0, &sq);
+    else if (c == 1) product_rows<T, ADJ, 1>(I, U, Q, y, r0, nrc, nz, LZ, Z0, &sq);
+    else product_rows<T, ADJ, 2>(I, U, Q, y, r0, nrc, nz, LZ, Z0, &sq);
     __syncthreads();
-    C* R = fft_run<C>(Z0, Z1, nz, nrc, I.rz, I.nrz, twz, false);
+    C* R = fft_run<C>(Z0, Z1, nz, LZ, nrc, I.rz, I.nrz, twz, false);
     if (whole) X = (R == B0) ? B1 : B0;
     for (int t = threadIdx.x; t < nrc * Mz; t += blockDim.x) {
       const int r = t / Mz, p = t - r * Mz;
-      const C hp = R[r * nz + p];
-      const C hm = R[r * nz + (p == 0 ? 0 : nz - p)];
+      const C hp = R[r * LZ + p];
+      const C hm = R[r * LZ + (p == 0 ? 0 : nz - p)];
       const T half = (T)0.5;
-      X[p * nx + 2 * (r0 + r)] = Cx<T>::mk(half * (hp.x + hm.x), half * (hp.y - hm.y));
-      X[p * nx + 2 * (r0 + r) + 1] = Cx<T>::mk(half * (hp.y + hm.y), -half * (hp.x - hm.x));
+      X[p * LX + 2 * (r0 + r)] = Cx<T>::mk(half * (hp.x + hm.x), half * (hp.y - hm.y));
+      X[p * LX + 2 * (r0 + r) + 1] = Cx<T>::mk(half * (hp.y + hm.y), -half * (hp.x - hm.x));
     }
     __syncthreads();
   }
@@ -394,12 +401,12 @@ __global__ void __launch_bounds__(128) k_prod_t(LaunchInfo li) {
       I.normpart[(size_t)c * I.ny + j] = s;
     }
   }
-  C* Y = fft_run<C>(X, X == B0 ? B1 : B0, nx, Mz, I.rx, I.nrx, twx, false);
+  C* Y = fft_run<C>(X, X == B0 ? B1 : B0, nx, LX, Mz, I.rx, I.nrx, twx, false);
   const T sc = (T)I.inv_nxnz;
   C* dst = xz_of<T>(I) + ((size_t)c * I.ny + j) * I.nmodes;
   for (int t = threadIdx.x; t < I.nmodes; t += blockDim.x) {
     const int i = t / Mz, p = t - i * Mz;
-    const C v = Y[p * nx + xbin(i, Kx, Mx, nx)];
+    const C v = Y[p * LX + xbin(i, Kx, Mx, nx)];
     dst[t] = Cx<T>::mk(v.x * sc, v.y * sc);
   }
 }
