@@ -5,6 +5,7 @@ import os
 import re
 
 import pytest
+from tests.paper_values import paper_values
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -43,7 +44,8 @@ def test_host_only_queries(lib):
     assert lib.pcf_state_len(32, 33, 32) == 3 * 19 * 10 * 33
     assert lib.pcf_state_len(30, 33, 32) == 0          # 30 = 2*3*5 has a radix-5 factor
     assert lib.pcf_state_len(32, 32, 32) == 0          # even ny rejected
-    assert lib.pcf_psi_len(32, 31, 32) == 20218        # the paper's snapshot dimension
+    pv = paper_values()
+    assert lib.pcf_psi_len(pv["nx"], pv["ny"], pv["nz"]) == pv["snapshot_dim"]  # §6.2
     assert lib.pcf_status_str(1) == b"invalid argument"
 
 

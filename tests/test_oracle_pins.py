@@ -14,6 +14,7 @@ import pcf_inputs as gi
 from oracle import PCFOracle, dmd
 from oracle import pcf_oracle as po
 from tests.analytic_fields import Grid, Scalar, vector_eval
+from tests.paper_values import paper_values
 
 LX, LZ = gi.LX_PAPER, gi.LZ_PAPER
 
@@ -143,6 +144,21 @@ def test_descent_monotone(o16):
     u = gi.random_perturbation(16, 17, 16, 0.1, 1)
     _, hist = o16.run(u, 0.01, 40)
     assert np.all(np.diff(hist) < 0)
+
+
+def test_descent_with_the_papers_step_sizes():
+    """The paper's test case (§5.1: Re, box, 32 x 31 x 32, dt = dtau_hat = 0.25, dtau = 0.03)
+    descends: J falls at every step.  The dummy-dynamics step taken in the diffusive direction
+    keeps the forward-Euler update stable at the paper's dtau; an ascent (f with the wrong
+    sign) raises J."""
+    pv = paper_values()
+    o = PCFOracle(pv["nx"], pv["ny"], pv["nz"], Lx=2 * math.pi / pv["Lx_over_2pi_inverse"],
+                  Lz=2 * math.pi / pv["Lz_over_2pi_inverse"], Re=pv["Re"], dt=pv["dt"], dtau_hat=pv["dtau_hat"])
+    u = gi.streak_roll(pv["nx"], pv["ny"], pv["nz"], seed=3)
+    _, hist = o.run(u, pv["dtau"], 12)
+    assert np.all(np.diff(hist) < 0)
+    _, up = o.run(u, -pv["dtau"], 3)
+    assert np.all(np.diff(up) > 0)
 
 
 def _shift(o, a, lx, lz):
@@ -390,8 +406,9 @@ def _adjoint_on_residual(U, g, nu):
 
 # ------------------------------------------------------------------ snapshot vector, DMD
 def test_psi_dimension_matches_paper():
-    """N = 20218 independent reals at Nx x Ny x Nz = 32 x 31 x 32 (§6.2)."""
-    assert PCFOracle(32, 31, 32).psi_dim() == 20218
+    """N = 20218 independent reals at Nx x Ny x Nz = 32 x 31 x 32 (§5.1 grid, §6.2 count)."""
+    pv = paper_values()
+    assert PCFOracle(pv["nx"], pv["ny"], pv["nz"]).psi_dim() == pv["snapshot_dim"]
 
 
 @pytest.mark.parametrize("grid", [(16, 17, 16), (32, 33, 32)])
