@@ -32,6 +32,12 @@ DTAU = 0.01
 WORKLOAD = "PCF Re=400 box 2pi/1.14 x 2 x 2pi/2.5, 32x33x32, 8 streak/roll guesses, plain FP64 descent step"
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel classes
+# from the ncu capture in profiles/fp64_step_32x33x32_b8_launches_and_top_kernels.md; reset
+# an entry to None when that kernel changes.
+TRAFFIC_BYTES = {"xzsynth_u": 4.05e6, "xzsynth_q": 4.05e6}
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -406,7 +412,7 @@ def run_ours(args):
     achieved = flops[dom] / (dom_ms * 1e-3) / 1e12
     peak_tf = fp64 / 1e3
     roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_tf, 4), "unit": "TFLOP/s",
-            "frac": round(achieved / peak_tf, 4), "traffic": None, "kernel": dom,
+            "frac": round(achieved / peak_tf, 4), "traffic": TRAFFIC_BYTES.get(dom), "kernel": dom,
             "peak_source": "measured FP64 DFMA throughput (k_fp64_probe) on this GPU",
             "kernel_share": round(kt[dom][0] / total_ms, 4), "mode_tile": s.mode_tile(),
             "kernel_ms_per_launch": round(dom_ms, 5),
