@@ -37,7 +37,7 @@ def _solver(lib, grid, batch, **kw):
     return lib.Solver(*grid, batch=batch, **kw)
 
 
-GRIDS = [(16, 17, 16), (32, 33, 32), (48, 49, 48), (32, 17, 48)]
+GRIDS = [(16, 17, 16), (32, 33, 32), (48, 49, 48), (32, 17, 48), (32, 31, 32)]  # last: the paper's §5.1 grid
 
 
 @pytest.mark.parametrize("grid", GRIDS)
