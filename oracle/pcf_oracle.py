@@ -68,31 +68,44 @@ def clenshaw_curtis_weights(N):
     return w
 
 
-def nonlinear_M(u, gu, y):
-    """M(u) = -y d_x u - v e_x - (u.grad) u, pointwise.
+def base_profile(kind, y):
+    """Streamwise laminar base flow u_b = (U(y), 0, 0) and U'(y) (§3.1: the method is derived
+    for a general u_b; §7 names plane Poiseuille flow as the next case).
+    couette: U = y (walls moving at +-1); poiseuille: U = 1 - y^2 (driven by a fixed
+    pressure gradient that the base flow absorbs)."""
+    if kind == "couette":
+        return y, np.ones_like(y)
+    if kind == "poiseuille":
+        return 1.0 - y * y, -2.0 * y
+    raise ValueError(kind)
 
-    u: (3, ...) velocity values; gu: (3, 3, ...) with gu[i, j] = d_j u_i; y broadcastable.
+
+def nonlinear_M(u, gu, U, dU=1.0):
+    """M(u) = -(u_b.grad) u - (u.grad) u_b - (u.grad) u = -U d_x u - U' v e_x - (u.grad) u,
+    pointwise, for u_b = (U(y), 0, 0).
+
+    u: (3, ...) velocity values; gu: (3, 3, ...) with gu[i, j] = d_j u_i; U, dU broadcastable.
     """
     out = np.empty_like(u)
     for i in range(3):
         conv = u[0] * gu[i, 0] + u[1] * gu[i, 1] + u[2] * gu[i, 2]
-        out[i] = -y * gu[i, 0] - conv
-    out[0] = out[0] - u[1]
+        out[i] = -U * gu[i, 0] - conv
+    out[0] = out[0] - dU * u[1]
     return out
 
 
-def adjoint_N(q, gq, u, gu, y):
-    """N(q) = (U.grad) q - (grad U)^T q with U = (y, 0, 0) + u, pointwise.
+def adjoint_N(q, gq, u, gu, U, dU=1.0):
+    """N(q) = (W.grad) q - (grad W)^T q with W = u_b + u = (U(y), 0, 0) + u, pointwise.
 
-    Component i: U_j d_j q_i - q_j d_i U_j, where d_i U_j = d_i u_j + delta_{j x} delta_{i y}.
+    Component i: W_j d_j q_i - q_j d_i W_j, where d_i W_j = d_i u_j + delta_{j x} delta_{i y} U'.
     """
-    U0 = u[0] + y
+    U0 = u[0] + U
     out = np.empty_like(q)
     for i in range(3):
         adv = U0 * gq[i, 0] + u[1] * gq[i, 1] + u[2] * gq[i, 2]
         tr = q[0] * gu[0, i] + q[1] * gu[1, i] + q[2] * gu[2, i]
         out[i] = adv - tr
-    out[1] = out[1] - q[0]
+    out[1] = out[1] - dU * q[0]
     return out
 
 
@@ -100,7 +113,7 @@ class PCFOracle:
     """Oracle for one grid; all state arrays are complex128 [3][Mx][Mz][Ny]."""
 
     def __init__(self, nx, ny, nz, Lx=TWO_PI / 1.14, Lz=TWO_PI / 2.5, Re=400.0,
-                 dt=0.25, dtau_hat=0.25):
+                 dt=0.25, dtau_hat=0.25, base_flow="couette"):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.Lx, self.Lz, self.Re = float(Lx), float(Lz), float(Re)
         self.nu = 1.0 / self.Re
@@ -124,6 +137,9 @@ class PCFOracle:
         self.Dmat = np.stack([cheb_deriv(e) for e in np.eye(self.N + 1)], axis=1)
         self._lu = {}
         self.y_phys = self.y[:, None, None]   # broadcast over (Ny, Nx, Nz)
+        self.base_flow = base_flow
+        Ub, dUb = base_profile(base_flow, self.y)
+        self.U_phys, self.dU_phys = Ub[:, None, None], dUb[:, None, None]
 
     # ---------------------------------------------------------------- transforms
     def to_phys(self, a):
@@ -228,10 +244,10 @@ class PCFOracle:
 
     # ---------------------------------------------------------------- method
     def M_hat(self, uval, ugrad):
-        return self.to_spec(nonlinear_M(uval, ugrad, self.y_phys))
+        return self.to_spec(nonlinear_M(uval, ugrad, self.U_phys, self.dU_phys))
 
     def N_hat(self, qval, qgrad, uval, ugrad):
-        return self.to_spec(adjoint_N(qval, qgrad, uval, ugrad, self.y_phys))
+        return self.to_spec(adjoint_N(qval, qgrad, uval, ugrad, self.U_phys, self.dU_phys))
 
     def norm_phys(self, val):
         """Volume-normalised L2 norm of physical values (3, Ny, Nx, Nz)."""

@@ -128,6 +128,35 @@ def test_laminar_is_equilibrium(o16):
     assert np.all(o16.adjoint_direction(z, r1) == 0)
 
 
+def test_poiseuille_laminar_is_equilibrium():
+    """u = 0 is an equilibrium for the plane Poiseuille base flow too: r1 = f = 0 exactly."""
+    o = PCFOracle(16, 17, 16, base_flow="poiseuille")
+    z = np.zeros((3, o.Mx, o.Mz, o.N + 1), np.complex128)
+    r1, J = o.residual(z)
+    assert J == 0.0 and np.all(r1 == 0)
+    assert np.all(o.adjoint_direction(z, r1) == 0)
+
+
+def _mirror_y(o, a):
+    """[u,v,w](x,y,z) -> [u,-v,w](x,-y,z): T_n(-y) = (-1)^n T_n(y)."""
+    sgn = (-1.0) ** np.arange(o.N + 1)
+    out = a * sgn
+    out[1] = -out[1]
+    return out
+
+
+@pytest.mark.parametrize("base,symmetric", [("poiseuille", True), ("couette", False)])
+def test_mirror_symmetry_of_the_base_flow(base, symmetric):
+    """U = 1 - y^2 is even in y, so the Poiseuille descent commutes with the y mirror; the
+    odd Couette profile U = y breaks it (the test tells the two base flows apart)."""
+    o = PCFOracle(16, 17, 16, base_flow=base)
+    u = gi.random_perturbation(16, 17, 16, 0.1, 4)
+    a1 = _mirror_y(o, o.descent_step(u, 0.01)[0])
+    a2 = o.descent_step(_mirror_y(o, u), 0.01)[0]
+    err = np.max(np.abs(a1 - a2)) / np.max(np.abs(a1))
+    assert (err <= 1e-13) if symmetric else (err > 1e-6)
+
+
 def test_r1_and_f_admissible(o16):
     """§4 steps 2 and 4: r1 and f are divergence-free and vanish at the walls."""
     u = gi.random_perturbation(16, 17, 16, 0.1, 0)
@@ -201,6 +230,16 @@ def test_equivariance(o16, op):
 
 
 # ------------------------------------------------------------------ continuous pins
+BASES = ["couette", "poiseuille"]
+
+
+def _profile(base):
+    """M and N of the oracle for the base flow `base`, as functions of (..., Y)."""
+    M = lambda u, gu, Y: po.nonlinear_M(u, gu, *po.base_profile(base, Y))
+    N = lambda q, gq, u, gu, Y: po.adjoint_N(q, gq, u, gu, *po.base_profile(base, Y))
+    return M, N
+
+
 def _residual(v, gv, lapv, gq, Y, nu, M=po.nonlinear_M):
     """R(U) = [F(v, q), div v], F = M(v) - grad q + nu Lap v (§3.1, Eq. (momentum))."""
     r1 = M(v, gv, Y) - gq + nu * lapv
@@ -255,9 +294,12 @@ def _adjoint_identity_gap(Nfun=po.adjoint_N, M=po.nonlinear_M):
     return abs(lhs - rhs) / scale
 
 
-def test_adjoint_identity():
-    """<L(U;G), R> = <G, L+(U;R)> for U, R, G in P0 (Appendix A), exact quadrature."""
-    assert _adjoint_identity_gap() <= 1e-12
+@pytest.mark.parametrize("base", BASES)
+def test_adjoint_identity(base):
+    """<L(U;G), R> = <G, L+(U;R)> for U, R, G in P0 (Appendix A), exact quadrature; for
+    plane Couette (u_b = (y,0,0)) and plane Poiseuille (u_b = (1-y^2,0,0)) base flows."""
+    M, N = _profile(base)
+    assert _adjoint_identity_gap(Nfun=N, M=M) <= 1e-12
 
 
 def _bad_N_sign(q, gq, u, gu, y):
@@ -283,27 +325,32 @@ def test_adjoint_identity_catches_planted_mistakes(bad):
     assert _adjoint_identity_gap(Nfun=bad) > 1e-4
 
 
-def test_M_is_perturbative_nse():
-    """M(u) = -((u_b+u).grad)(u_b+u) + (u_b.grad)u_b with u_b = (y,0,0) (§3.1)."""
+@pytest.mark.parametrize("base,U,dU", [("couette", lambda Y: Y, lambda Y: 1.0 + 0.0 * Y),
+                                        ("poiseuille", lambda Y: 1.0 - Y * Y, lambda Y: -2.0 * Y)])
+def test_M_is_perturbative_nse(base, U, dU):
+    """M(u) = -((u_b+u).grad)(u_b+u) + (u_b.grad)u_b with u_b = (U(y),0,0) (§3.1);
+    (u_b.grad)u_b = U d_x U = 0.  The profile is written out here, not taken from the oracle."""
     rng = np.random.default_rng(3)
     g = Grid(LX, LZ, nf=8, ng=10)
     comps = _fields(rng, 1, 4, [1, 1, 1])
     u, gu, _ = vector_eval(comps, g)
     Ut = u.copy()
-    Ut[0] += g.Y
+    Ut[0] += U(g.Y)
     gUt = gu.copy()
-    gUt[0, 1] += 1.0
+    gUt[0, 1] += dU(g.Y)
     full = -np.einsum("j...,ij...->i...", Ut, gUt)
-    got = po.nonlinear_M(u, gu, g.Y)
+    got = _profile(base)[0](u, gu, g.Y)
     assert np.max(np.abs(got - full)) <= 1e-13
 
 
-def test_gradient_vs_finite_differences():
+@pytest.mark.parametrize("base", BASES)
+def test_gradient_vs_finite_differences(base):
     """dJ^2/dU along G equals 2 <G, L+(U; R(U))> (the gradient of §2), to 1e-6 relative.
 
     G satisfies g1 = dg1/dy = 0 and g2 = 0 at the walls, so every boundary term of
     Appendix A vanishes for any U in P0 without requiring R(U) in P0.
     """
+    M, N = _profile(base)
     rng = np.random.default_rng(5)
     g = Grid(LX, LZ, nf=12, ng=24)
     nu = 1.0 / 400.0
@@ -316,14 +363,14 @@ def test_gradient_vs_finite_differences():
             # promote both to the same wall factor by folding the wall into the coefficients
             comps.append(_sum_fields(a, b, eps))
         v, gv, lv, gq, _ = _eval_U_mixed(comps, g)
-        r1, r2 = _residual(v, gv, lv, gq, g.Y, nu)
+        r1, r2 = _residual(v, gv, lv, gq, g.Y, nu, M)
         return g.integrate((r1 ** 2).sum(axis=0) + r2 ** 2)
 
     eps = 1e-3
     d1 = (cost(eps) - cost(-eps)) / (2 * eps)
     d2 = (cost(eps / 2) - cost(-eps / 2)) / eps
     fd = (4 * d2 - d1) / 3.0        # removes the exact eps^2 term of the quartic
-    a_dot = _adjoint_on_residual(U, g, nu)
+    a_dot = _adjoint_on_residual(U, g, nu, M, N)
     gvv, _, _ = vector_eval(G[:3], g)
     g2 = G[3].eval(g)["f"]
     grad_dot = 2.0 * g.integrate((gvv * a_dot[0]).sum(axis=0) + g2 * a_dot[1])
@@ -354,7 +401,7 @@ def _eval_U_mixed(comps, g):
     return v, gv, lv, np.stack([q["fx"], q["fy"], q["fz"]]), q["f"]
 
 
-def _adjoint_on_residual(U, g, nu):
+def _adjoint_on_residual(U, g, nu, M=po.nonlinear_M, Nfun=po.adjoint_N):
     """L+(U; R(U)), with R(U) and its derivatives obtained exactly.
 
     R(U) is a trigonometric polynomial in (x, z) (degree <= 2K) and a polynomial in y
@@ -369,7 +416,7 @@ def _adjoint_on_residual(U, g, nu):
     gg.y = yy
     gg.Y = yy[:, None, None]
     v, gv, lv, gq, _ = _eval_U(U, gg)
-    r1, r2 = _residual(v, gv, lv, gq, gg.Y, nu)
+    r1, r2 = _residual(v, gv, lv, gq, gg.Y, nu, M)
 
     def spectral(fgrid):
         """Return callables evaluating f, grad f, Lap f on g from samples on gg."""
@@ -401,7 +448,7 @@ def _adjoint_on_residual(U, g, nu):
     gr = np.stack([np.stack([e["fx"], e["fy"], e["fz"]]) for e in rr])
     lapr = np.stack([e["lap"] for e in rr])
     vq, gvq, _, _, _ = _eval_U(U, g)
-    return _adjoint(vq, gvq, r, gr, lapr, rh["f"], np.stack([rh["fx"], rh["fy"], rh["fz"]]), g.Y, nu)
+    return _adjoint(vq, gvq, r, gr, lapr, rh["f"], np.stack([rh["fx"], rh["fy"], rh["fz"]]), g.Y, nu, Nfun)
 
 
 # ------------------------------------------------------------------ snapshot vector, DMD
