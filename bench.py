@@ -230,6 +230,15 @@ def run_forms(pcf, gi, flush, stream, dev, args):
                       "gradient_evals_per_s": 64 * 10 / (ms * 1e-3), "ms_per_step": ms / 10,
                       "mode_tile_autotuned": sb.mode_tile(), "points": int(24 * 33792 + 24 * 112896 + 16 * 266240)}
     sb.close()
+    # plane Poiseuille base flow u_b = (1 - y^2, 0, 0): the same step on the bench workload's shape
+    sq = pcf.Solver(*GRID, batch=BATCH, Re=RE, dt=DT, dtau_hat=DTAU_HAT, base_flow=pcf.POISEUILLE)
+    uq = torch.from_numpy(gi.batch(gi.streak_roll, range(BATCH), *GRID)).to(dev)
+    sq.descent_step(uq, DTAU, 3)
+    ms = _timed_steps(sq, uq, DTAU, 50, flush, stream)
+    out["poiseuille"] = {"config": "8 streak/roll guesses on plane Poiseuille flow u_b = (1 - y^2, 0, 0), "
+                                   "32x33x32, Re 400, FP64",
+                         "gradient_evals_per_s": BATCH * 50 / (ms * 1e-3), "ms_per_step": ms / 50}
+    sq.close()
     # mixed precision vs FP64 at 128x97x128, Re 1000
     g4 = (128, 97, 128)
     u4 = gi.random_perturbation(*g4, 0.1, 0)[None]

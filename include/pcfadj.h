@@ -74,8 +74,17 @@ typedef struct pcf_params {
                            form, ny <= 97: the per-mode work as separate analysis, solve and
                            synthesis kernels over instance groups); 1: banded sweeps; 2: dense
                            operators inside the single per-mode kernel (same results as 0) */
-  int reserved;
+  int base_flow;        /* pcf_base_flow: the laminar base flow u_b = (U(y), 0, 0) */
 } pcf_params;
+
+/* Base flows (§3.1 derives the method for a general laminar base flow u_b; §7 names plane
+ * Poiseuille flow as a direct next case).  The perturbation u vanishes at both walls in
+ * either case; the Poiseuille base flow absorbs the fixed driving pressure gradient, so the
+ * perturbation's mean pressure gradient stays zero. */
+typedef enum {
+  PCF_COUETTE = 0,     /* plane Couette flow:    U = y       (walls moving at +-1) */
+  PCF_POISEUILLE = 1   /* plane Poiseuille flow: U = 1 - y^2 (pressure-driven) */
+} pcf_base_flow;
 
 typedef struct pcf_ctx pcf_ctx;
 

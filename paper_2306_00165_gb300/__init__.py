@@ -30,7 +30,9 @@ class _Params(ctypes.Structure):
                 ("Lx", ctypes.c_double), ("Lz", ctypes.c_double), ("Re", ctypes.c_double),
                 ("dt", ctypes.c_double), ("dtau_hat", ctypes.c_double),
                 ("precision", ctypes.c_int), ("modes_per_block", ctypes.c_int),
-                ("solve_kind", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("solve_kind", ctypes.c_int), ("base_flow", ctypes.c_int)]
+
+COUETTE, POISEUILLE = 0, 1   # laminar base flows u_b = (y,0,0) and (1-y^2,0,0)
 
 
 def load_library(path=None):
@@ -130,13 +132,13 @@ class Solver:
                       "yanalysis", "ysynth_step", "jnorm"]
 
     def __init__(self, nx, ny, nz, batch=1, Lx=LX_PAPER, Lz=LZ_PAPER, Re=400.0, dt=0.25, dtau_hat=0.25,
-                 precision=0, modes_per_block=0, solve_kind=0):
+                 precision=0, modes_per_block=0, solve_kind=0, base_flow=COUETTE):
         import torch
         self.lib = load_library()
         self.shape = state_shape(nx, ny, nz, batch)
         self.nx, self.ny, self.nz, self.batch = nx, ny, nz, batch
         self.dt, self.dtau_hat = dt, dtau_hat
-        p = _Params(nx, ny, nz, batch, Lx, Lz, Re, dt, dtau_hat, precision, modes_per_block, solve_kind, 0)
+        p = _Params(nx, ny, nz, batch, Lx, Lz, Re, dt, dtau_hat, precision, modes_per_block, solve_kind, base_flow)
         h = ctypes.c_void_p()
         _check(self.lib.pcf_create(ctypes.byref(p), _stream(), ctypes.byref(h)))
         self._h = h
@@ -146,14 +148,15 @@ class Solver:
     @classmethod
     def batched(cls, grids, Lx=LX_PAPER, Lz=LZ_PAPER, Re=400.0, dt=0.25, dtau_hat=0.25, modes_per_block=0,
                 solve_kind=0):
-        """grids: list of (nx, ny, nz, count)."""
+        """grids: list of (nx, ny, nz, count) or (nx, ny, nz, count, base_flow)."""
         import torch
         self = cls.__new__(cls)
         self.lib = load_library()
         arr = (_Params * len(grids))()
-        for k, (nx, ny, nz, cnt) in enumerate(grids):
+        for k, g in enumerate(grids):
+            nx, ny, nz, cnt = g[:4]
             arr[k] = _Params(nx, ny, nz, cnt, Lx, Lz, Re, dt, dtau_hat, 0, modes_per_block if k == 0 else 0,
-                             solve_kind, 0)
+                             solve_kind, g[4] if len(g) > 4 else COUETTE)
         h = ctypes.c_void_p()
         _check(self.lib.pcf_batch_create(arr, len(grids), _stream(), ctypes.byref(h)))
         self._h = h
@@ -169,7 +172,7 @@ class Solver:
 
     def view(self, flat, b):
         """Instance b of a flat batch tensor as [3, Mx, Mz, ny]."""
-        nx, ny, nz, _ = self.grids[b]
+        nx, ny, nz = self.grids[b][:3]
         return flat[self.offsets[b]:self.offsets[b + 1]].view(state_shape(nx, ny, nz, 1)[1:])
 
     def mode_tile(self):

@@ -555,12 +555,12 @@ long long pcf_psi_len(int nx, int ny, int nz) {
 static bool params_ok(const pcf_params* prm) {
   return grid_ok(prm->nx, prm->ny, prm->nz) && prm->batch >= 1 && prm->Re > 0 && prm->dt > 0 &&
          prm->dtau_hat > 0 && prm->Lx > 0 && prm->Lz > 0 && prm->solve_kind >= 0 && prm->solve_kind <= 2 &&
-         prm->modes_per_block >= 0;
+         prm->modes_per_block >= 0 && (prm->base_flow == PCF_COUETTE || prm->base_flow == PCF_POISEUILLE);
 }
 
 // Device tables of one grid (shared by every instance on that grid).
 struct GridTables {
-  double *cheb, *rco, *ccw, *kx, *kz, *y, *tab0, *tab1, *dense0, *dense1;
+  double *cheb, *rco, *ccw, *kx, *kz, *y, *ub, *tab0, *tab1, *dense0, *dense1;
   double2 *twx, *twz;
   float2 *twxf = nullptr, *twzf = nullptr;
   uint16_t* tcA = nullptr;
@@ -575,17 +575,24 @@ static pcf_status build_tables(pcf_ctx* c, const pcf_params* prm, GridTables* g)
   for (int i = 0; i < Mx; ++i) kx[i] = 2.0 * kPi * (i <= Kx ? i : i - Mx) / prm->Lx;
   for (int p = 0; p < Mz; ++p) kz[p] = 2.0 * kPi * p / prm->Lz;
   for (int j = 0; j < ny; ++j) yg[j] = cospi_frac(j, N);
+  // base-flow profile U(y_j), U'(y_j) (one explicit fma, so every host rounds alike)
+  std::vector<double> ub(2 * (size_t)ny);
+  for (int j = 0; j < ny; ++j) {
+    const double y = yg[j];
+    ub[j] = prm->base_flow == PCF_POISEUILLE ? std::fma(-y, y, 1.0) : y;
+    ub[ny + j] = prm->base_flow == PCF_POISEUILLE ? -2.0 * y : 1.0;
+  }
   const std::vector<double> cheb = make_cheb(N), rco = make_rco(N), ccw = make_ccw(N);
   g->sig[0] = 1.0 / (nu * prm->dt);
   g->sig[1] = 1.0 / (nu * prm->dtau_hat);
   const std::vector<double> tab0 = make_mode_tables(N, kx, kz, g->sig[0], rco);
   const std::vector<double2> twx = make_twiddles(nx), twz = make_twiddles(nz);
   if (upload(cheb, &g->cheb) || upload(rco, &g->rco) || upload(ccw, &g->ccw) || upload(kx, &g->kx) ||
-      upload(kz, &g->kz) || upload(yg, &g->y) || upload(twx, &g->twx) || upload(twz, &g->twz) ||
-      upload(tab0, &g->tab0))
+      upload(kz, &g->kz) || upload(yg, &g->y) || upload(ub, &g->ub) || upload(twx, &g->twx) ||
+      upload(twz, &g->twz) || upload(tab0, &g->tab0))
     return PCF_ECUDA;
   for (void* p : {(void*)g->cheb, (void*)g->rco, (void*)g->ccw, (void*)g->kx, (void*)g->kz, (void*)g->y,
-                  (void*)g->twx, (void*)g->twz, (void*)g->tab0})
+                  (void*)g->ub, (void*)g->twx, (void*)g->twz, (void*)g->tab0})
     c->allocs.push_back(p);
   std::vector<double> tab1;
   if (prm->dtau_hat == prm->dt) {
@@ -835,7 +842,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
     for (int q = 0; q < k; ++q) {
       const pcf_params &a = list[k], &p = list[q];
       if (a.nx == p.nx && a.ny == p.ny && a.nz == p.nz && a.Lx == p.Lx && a.Lz == p.Lz && a.Re == p.Re &&
-          a.dt == p.dt && a.dtau_hat == p.dtau_hat && a.solve_kind == p.solve_kind) {
+          a.dt == p.dt && a.dtau_hat == p.dtau_hat && a.solve_kind == p.solve_kind && a.base_flow == p.base_flow) {
         found = grid_of[q];
         break;
       }
@@ -901,7 +908,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       I.nu = 1.0 / p.Re; I.dt = p.dt; I.dtau_hat = p.dtau_hat; I.dtau = 0.0;
       I.inv_nu = 1.0 / I.nu; I.inv_dt = 1.0 / I.dt; I.inv_dtau_hat = 1.0 / I.dtau_hat;
       I.inv_nxnz = 1.0 / ((double)p.nx * p.nz);
-      I.cheb = g.cheb; I.rco = g.rco; I.ygrid = g.y; I.ccw = g.ccw; I.kx = g.kx; I.kz = g.kz;
+      I.cheb = g.cheb; I.rco = g.rco; I.ygrid = g.y; I.ubase = g.ub; I.ccw = g.ccw; I.kx = g.kx; I.kz = g.kz;
       I.twx = g.twx; I.twz = g.twz;
       I.tab[0] = g.tab0; I.tab[1] = g.tab1;
       I.dense[0] = g.dense0; I.dense[1] = g.dense1;

@@ -88,6 +88,7 @@ struct Inst {
   const double* cheb;
   const double* rco;
   const double* ygrid;
+  const double* ubase;  // [2][ny]: base-flow profile U(y_j) and U'(y_j)
   const double* ccw;
   const double* kx;   // [Mx]
   const double* kz;   // [Mz]

@@ -297,26 +297,27 @@ __device__ __forceinline__ T grad_at(const T* const* F, int c, int d, int e) {
 }
 
 // Pointwise products of the plane, row pairs packed as complex values.
+// Ub, dUb: the base-flow profile U(y_j) and U'(y_j) of the plane (u_b = (U(y), 0, 0)).
 template <class T, bool ADJ>
-__device__ __forceinline__ void product_pair(const Inst& I, const T* const* U, const T* const* Q, int c, T y, int e0,
-                                             int e1, T* m, double* sq) {
+__device__ __forceinline__ void product_pair(const Inst& I, const T* const* U, const T* const* Q, int c, T Ub,
+                                             T dUb, int e0, int e1, T* m, double* sq) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int e = h == 0 ? e0 : e1;
     const T u = U[0][e], v = U[1][e], w = U[2][e];
     if (!ADJ) {
       const T gx = grad_at<T>(U, c, 0, e), gy = grad_at<T>(U, c, 1, e), gz = grad_at<T>(U, c, 2, e);
-      T val = -fma(y + u, gx, fma(v, gy, w * gz));
-      if (c == 0) val -= v;
+      T val = -fma(Ub + u, gx, fma(v, gy, w * gz));
+      if (c == 0) val -= dUb * v;
       m[h] = val;
     } else {
       const T q0 = Q[0][e], q1 = Q[1][e], q2 = Q[2][e];
       const T qc = Q[c][e];
       *sq = fma((double)qc, (double)qc, *sq);
-      const T adv = fma(y + u, grad_at<T>(Q, c, 0, e), fma(v, grad_at<T>(Q, c, 1, e), w * grad_at<T>(Q, c, 2, e)));
+      const T adv = fma(Ub + u, grad_at<T>(Q, c, 0, e), fma(v, grad_at<T>(Q, c, 1, e), w * grad_at<T>(Q, c, 2, e)));
       const T tr = fma(q0, grad_at<T>(U, 0, c, e), fma(q1, grad_at<T>(U, 1, c, e), q2 * grad_at<T>(U, 2, c, e)));
       T val = adv - tr;
-      if (c == 1) val -= q0;
+      if (c == 1) val -= dUb * q0;
       m[h] = val;
     }
   }
@@ -325,19 +326,19 @@ __device__ __forceinline__ void product_pair(const Inst& I, const T* const* U, c
 // Products of the rows r0 .. r0 + nrc - 1 of a plane for component CC (a compile-time
 // constant, so that the field indices fold and the plane pointers stay in registers).
 template <class T, bool ADJ, int CC>
-__device__ __forceinline__ void product_rows(const Inst& I, const T* const* U, const T* const* Q, T y, int r0,
+__device__ __forceinline__ void product_rows(const Inst& I, const T* const* U, const T* const* Q, T Ub, T dUb, int r0,
                                              int nrc, int nz, int LZ, typename Cx<T>::c* Z0, double* sq) {
   for (int t = threadIdx.x; t < nrc * nz; t += blockDim.x) {
     const int r = t / nz, z = t - r * nz;
     const int e0 = (2 * (r0 + r)) * nz + z, e1 = e0 + nz;
     T m[2];
-    product_pair<T, ADJ>(I, U, Q, CC, y, e0, e1, m, sq);
+    product_pair<T, ADJ>(I, U, Q, CC, Ub, dUb, e0, e1, m, sq);
     Z0[r * LZ + z] = Cx<T>::mk(m[0], m[1]);
   }
 }
 
 // CTA = (instance, plane j, component c): product component c on the plane (M(u) or
-// N(q) with U = (y + u, v, w)), forward FFT in z then x, 2/3 truncation.  ADJ also sums
+// N(q) with W = u_b + u = (U(y) + u, v, w)), forward FFT in z then x, 2/3 truncation.  ADJ also sums
 // q_c^2 over the plane (in FP64) for J.
 template <class T, bool ADJ>
 __global__ void __launch_bounds__(128) k_prod_t(LaunchInfo li) {
@@ -364,7 +365,7 @@ __global__ void __launch_bounds__(128) k_prod_t(LaunchInfo li) {
     U[f] = fplane<T>(I, 0, f, j);
     Q[f] = ADJ ? fplane<T>(I, 1, f, j) : nullptr;
   }
-  const T y = (T)I.ygrid[j];
+  const T Ub = (T)I.ubase[j], dUb = (T)I.ubase[I.ny + j];
   const int nr = nx / 2, LX = pp.LX, LZ = pp.LZ;
   const bool whole = pp.chunk == nr;
   // the x-stage input X[p][x] lives in B0 when chunked (z chunks use B1), else decided below
@@ -375,9 +376,9 @@ __global__ void __launch_bounds__(128) k_prod_t(LaunchInfo li) {
     const int nrc = min(pp.chunk, nr - r0);
     C* Z0 = whole ? B0 : B1;
     C* Z1 = whole ? B1 : B1 + pp.chunk * LZ;
-    if (c == 0) product_rows<T, ADJ, 0>(I, U, Q, y, r0, nrc, nz, LZ, Z0, &sq);
-    else if (c == 1) product_rows<T, ADJ, 1>(I, U, Q, y, r0, nrc, nz, LZ, Z0, &sq);
-    else product_rows<T, ADJ, 2>(I, U, Q, y, r0, nrc, nz, LZ, Z0, &sq);
+    if (c == 0) product_rows<T, ADJ, 0>(I, U, Q, Ub, dUb, r0, nrc, nz, LZ, Z0, &sq);
+    else if (c == 1) product_rows<T, ADJ, 1>(I, U, Q, Ub, dUb, r0, nrc, nz, LZ, Z0, &sq);
+    else product_rows<T, ADJ, 2>(I, U, Q, Ub, dUb, r0, nrc, nz, LZ, Z0, &sq);
     __syncthreads();
     C* R = fft_run<C>(Z0, Z1, nz, LZ, nrc, I.rz, I.nrz, twz, false);
     if (whole) X = (R == B0) ? B1 : B0;
