@@ -72,8 +72,10 @@ typedef struct pcf_params {
                            0 = autotuned */
   int solve_kind;       /* 0: dense per-mode operators when ny <= 129, else banded sweeps (FP64
                            form, ny <= 97: the per-mode work as separate analysis, solve and
-                           synthesis kernels over instance groups); 1: banded sweeps; 2: dense
-                           operators inside the single per-mode kernel (same results as 0) */
+                           synthesis kernels over instance groups; mixed form: timed against
+                           the sweeps at creation, see pcf_solve_variant); 1: banded sweeps;
+                           2: dense operators inside the single per-mode kernel (FP64 form:
+                           same results as 0) */
   int base_flow;        /* pcf_base_flow: the laminar base flow u_b = (U(y), 0, 0) */
 } pcf_params;
 
@@ -126,6 +128,13 @@ long long pcf_state_offset(const pcf_ctx* ctx, int instance);
 /* Fourier modes per CTA chosen for the per-mode kernels of the descent step (by the
  * autotuner or the caller). */
 int pcf_mode_tile(const pcf_ctx* ctx);
+
+/* Stokes solve the descent step uses: 0 banded tau sweeps inside the per-mode kernel,
+ * 1 dense per-mode operators inside the per-mode kernel, 2 dense operators in the split
+ * analysis / solve / synthesis kernels over instance groups (FP64 form).  With
+ * solve_kind 0 the mixed-precision form times 0 against 1 at creation and keeps the faster.
+ * -1 for a NULL context. */
+int pcf_solve_variant(const pcf_ctx* ctx);
 
 /* Release a context (waits for its stream).  NULL is ignored. */
 void pcf_destroy(pcf_ctx* ctx);

@@ -81,6 +81,7 @@ def load_library(path=None):
         "pcf_set_kernel_timing": (I, [P, I]),
         "pcf_kernel_times": (I, [P, P, P, I]),
         "pcf_launches_per_step": (I, [P]),
+        "pcf_solve_variant": (I, [P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -286,6 +287,10 @@ class Solver:
         cnt = (ctypes.c_longlong * n)()
         _check(self.lib.pcf_kernel_times(self._h, ms, cnt, n))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(self.KERNEL_CLASSES)}
+
+    def solve_variant(self):
+        """0 banded sweeps, 1 dense operators (single per-mode kernel), 2 dense split kernels."""
+        return int(self.lib.pcf_solve_variant(self._h))
 
     def launches_per_step(self):
         return int(self.lib.pcf_launches_per_step(self._h))

@@ -759,20 +759,11 @@ static pcf_status autotune_split(pcf_ctx* c) {
   return set_split_groups(c, best);
 }
 
-// Autotuner: time the Stokes-step mode kernel on the batch (laminar input) for each
-// candidate tile and keep the fastest.
-static pcf_status autotune_tiles(pcf_ctx* c) {
+// Time the Stokes-step mode kernel on the batch for each candidate tile; keep the fastest.
+static pcf_status time_mode_tiles(pcf_ctx* c, cudaEvent_t a, cudaEvent_t b, int* best, float* best_ms) {
   const int cand[] = {1, 2, 3, 4, 6, 8};
-  double2* z = nullptr;
-  PCF_CUDA(cudaMalloc(&z, sizeof(double2) * (size_t)c->total_state));
-  PCF_CUDA(cudaMemset(z, 0, sizeof(double2) * (size_t)c->total_state));
-  set_pointers(c, (const double*)z, (const double*)c->r_int, nullptr);
-  PCF_TRY(push_descriptors(c));
-  cudaEvent_t a, b;
-  PCF_CUDA(cudaEventCreate(&a));
-  PCF_CUDA(cudaEventCreate(&b));
-  int best = 4;
-  float best_ms = 1e30f;
+  *best = 4;
+  *best_ms = 1e30f;
   for (int mpc : cand) {
     if (set_mode_tiles(c, mpc) != PCF_OK) continue;
     PCF_TRY(push_descriptors(c));
@@ -784,9 +775,48 @@ static pcf_status autotune_tiles(pcf_ctx* c) {
     PCF_CUDA(cudaEventSynchronize(b));
     float ms = 0.f;
     PCF_CUDA(cudaEventElapsedTime(&ms, a, b));
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = mpc;
+    if (ms < *best_ms) {
+      *best_ms = ms;
+      *best = mpc;
+    }
+  }
+  return PCF_OK;
+}
+
+// Autotuner (laminar input): the mode tile and, for the mixed-precision form, the Stokes
+// solve variant.  The dense per-mode operators keep the FP64 pipe full; the banded sweeps
+// need ~20x fewer FP64 operations but run as sequential chains and no operator tables stream
+// from memory; which one is faster depends on the grid and the batch, so both are timed.
+static pcf_status autotune_tiles(pcf_ctx* c) {
+  double2* z = nullptr;
+  PCF_CUDA(cudaMalloc(&z, sizeof(double2) * (size_t)c->total_state));
+  PCF_CUDA(cudaMemset(z, 0, sizeof(double2) * (size_t)c->total_state));
+  set_pointers(c, (const double*)z, (const double*)c->r_int, nullptr);
+  PCF_TRY(push_descriptors(c));
+  cudaEvent_t a, b;
+  PCF_CUDA(cudaEventCreate(&a));
+  PCF_CUDA(cudaEventCreate(&b));
+  int best = 4;
+  float best_ms = 1e30f;
+  PCF_TRY(time_mode_tiles(c, a, b, &best, &best_ms));
+  if (c->mixed && c->hinst[0].dense[0]) {
+    std::vector<const double*> saved;
+    for (Inst& I : c->hinst) {
+      saved.push_back(I.dense[0]);
+      saved.push_back(I.dense[1]);
+      I.dense[0] = I.dense[1] = nullptr;
+    }
+    int best2 = 4;
+    float ms2 = 1e30f;
+    PCF_TRY(time_mode_tiles(c, a, b, &best2, &ms2));
+    if (ms2 < best_ms) {
+      best = best2;
+      best_ms = ms2;
+    } else {
+      for (size_t i = 0; i < c->hinst.size(); ++i) {
+        c->hinst[i].dense[0] = saved[2 * i];
+        c->hinst[i].dense[1] = saved[2 * i + 1];
+      }
     }
   }
   cudaEventDestroy(a);
@@ -973,6 +1003,12 @@ long long pcf_state_offset(const pcf_ctx* c, int instance) {
 }
 
 int pcf_mode_tile(const pcf_ctx* c) { return c ? (c->split ? c->sgrp : c->mpc) : 0; }
+
+int pcf_solve_variant(const pcf_ctx* c) {
+  if (!c) return -1;
+  if (c->split) return 2;
+  return c->hinst[0].dense[0] ? 1 : 0;
+}
 
 void pcf_destroy(pcf_ctx* c) {
   if (!c) return;
