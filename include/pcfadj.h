@@ -70,12 +70,13 @@ typedef struct pcf_params {
   int modes_per_block;  /* tile of the per-mode kernels (Fourier modes per CTA of the single
                            per-mode kernel; instances per group of the split kernels);
                            0 = autotuned */
-  int solve_kind;       /* 0: dense per-mode operators when ny <= 129, else banded sweeps (FP64
-                           form, ny <= 97: the per-mode work as separate analysis, solve and
-                           synthesis kernels over instance groups; mixed form: timed against
-                           the sweeps at creation, see pcf_solve_variant); 1: banded sweeps;
-                           2: dense operators inside the single per-mode kernel (FP64 form:
-                           same results as 0) */
+  int solve_kind;       /* 0: dense per-mode operators when ny <= 129, else banded sweeps; the
+                           autotuner picks the kernel organisation (FP64 form, ny <= 97: split
+                           or fused kernels over instance groups; mixed form: dense against
+                           sweeps), see pcf_solve_variant.  1: banded sweeps.  2: dense
+                           operators inside the single per-mode kernel.  3: FP64 split
+                           analysis / solve / synthesis kernels.  4: FP64 fused per-mode
+                           half-step kernel.  2, 3 and 4 give bit-identical results. */
   int base_flow;        /* pcf_base_flow: the laminar base flow u_b = (U(y), 0, 0) */
 } pcf_params;
 
@@ -131,9 +132,10 @@ int pcf_mode_tile(const pcf_ctx* ctx);
 
 /* Stokes solve the descent step uses: 0 banded tau sweeps inside the per-mode kernel,
  * 1 dense per-mode operators inside the per-mode kernel, 2 dense operators in the split
- * analysis / solve / synthesis kernels over instance groups (FP64 form).  With
- * solve_kind 0 the mixed-precision form times 0 against 1 at creation and keeps the faster.
- * -1 for a NULL context. */
+ * analysis / solve / synthesis kernels over instance groups, 3 dense operators in the fused
+ * per-mode half-step kernel over instance groups (2 and 3: FP64 form).  With solve_kind 0
+ * the FP64 form times 2 against 3 and the mixed-precision form 0 against 1 at creation,
+ * and each keeps the faster.  -1 for a NULL context. */
 int pcf_solve_variant(const pcf_ctx* ctx);
 
 /* Release a context (waits for its stream).  NULL is ignored. */

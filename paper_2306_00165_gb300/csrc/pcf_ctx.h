@@ -39,6 +39,10 @@ struct pcf_ctx {
   int* pre_yy = nullptr;
   int cta_ya = 0, cta_ys = 0, cta_yy = 0;
   int grid_ys = 0, buf_ys = 0, rows_ys = 0;  // persistent solve: CTAs, stage buffer, scratch rows
+  bool fused = false;           // the step runs the fused per-mode kernel (k_ystep)
+  int* pre_yf = nullptr;        // its CTA prefix over groups [B + 1]
+  int cta_yf = 0;
+  size_t sm_yf = 0;
   size_t sm_ya = 0, sm_ys = 0, sm_yy = 0;
   double tuned_split_ms = 0.0;
   double2* r_int = nullptr;    // internal r1 buffer for descent

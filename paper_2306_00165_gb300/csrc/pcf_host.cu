@@ -432,6 +432,10 @@ pcf_status launch_split_solve(pcf_ctx* c, int op) {
     launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_of(c, c->pre_ys), op);
   });
 }
+pcf_status launch_fused_step(pcf_ctx* c, int op) {
+  return timed(c, op == MODE_PHI ? 3 : 6,
+               [&] { launch_ystep(c->cta_yf, c->sm_yf, c->cs, gl_of(c, c->pre_yf), op); });
+}
 pcf_status launch_split_jnorm(pcf_ctx* c, int step_index) {
   return timed(c, 9, [&] { launch_jnorm(c->B, c->cs, c->dinst, step_index); });
 }
@@ -495,6 +499,16 @@ pcf_status step_body(pcf_ctx* c, int s) {
     PCF_TRY(launch_mode(c, MODE_PSI_UPDATE, 1, s));
     return PCF_OK;
   }
+  if (c->split && c->fused) {
+    PCF_TRY(launch_synth(c, 0, kFieldsSynth));
+    PCF_TRY(launch_prodM(c));
+    PCF_TRY(launch_fused_step(c, MODE_PHI));
+    PCF_TRY(launch_synth(c, 1, kFieldsSynth));
+    PCF_TRY(launch_prodN(c));
+    PCF_TRY(launch_split_jnorm(c, s));
+    PCF_TRY(launch_fused_step(c, MODE_PSI_UPDATE));
+    return PCF_OK;
+  }
   if (c->split) {
     PCF_TRY(launch_synth(c, 0, kFieldsSynth));
     PCF_TRY(launch_prodM(c));
@@ -554,7 +568,7 @@ long long pcf_psi_len(int nx, int ny, int nz) {
 
 static bool params_ok(const pcf_params* prm) {
   return grid_ok(prm->nx, prm->ny, prm->nz) && prm->batch >= 1 && prm->Re > 0 && prm->dt > 0 &&
-         prm->dtau_hat > 0 && prm->Lx > 0 && prm->Lz > 0 && prm->solve_kind >= 0 && prm->solve_kind <= 2 &&
+         prm->dtau_hat > 0 && prm->Lx > 0 && prm->Lz > 0 && prm->solve_kind >= 0 && prm->solve_kind <= 4 &&
          prm->modes_per_block >= 0 && (prm->base_flow == PCF_COUETTE || prm->base_flow == PCF_POISEUILLE);
 }
 
@@ -677,11 +691,12 @@ static pcf_status set_split_groups(pcf_ctx* c, int G) {
     if (fresh) groups.push_back(make_int2(b, 1)); else groups.back().y += 1;
   }
   const int ng = (int)groups.size();
-  std::vector<int> pa(ng + 1, 0), ps(ng + 1, 0), py(ng + 1, 0);
+  std::vector<int> pa(ng + 1, 0), ps(ng + 1, 0), py(ng + 1, 0), pf(ng + 1, 0);
   size_t sa = 0, sy = 0;
   int gmax = 1;
   for (int q = 0; q < ng; ++q) {
     const Inst& I = c->hinst[groups[q].x];
+    pf[q + 1] = pf[q] + I.nmodes;
     pa[q + 1] = pa[q] + split_ctas_per_group(0, I.nmodes);
     ps[q + 1] = ps[q] + split_ctas_per_group(1, I.nmodes);
     py[q + 1] = py[q] + split_ctas_per_group(2, I.nmodes);
@@ -694,9 +709,13 @@ static pcf_status set_split_groups(pcf_ctx* c, int G) {
   if (std::max(sa, std::max(ss, sy)) > 227 * 1024) return PCF_ENOTSUP;
   if (!c->d_groups) {
     if (ctx_alloc(c, &c->d_groups, (size_t)c->B) || ctx_alloc(c, &c->pre_ya, (size_t)c->B + 1) ||
-        ctx_alloc(c, &c->pre_ys, (size_t)c->B + 1) || ctx_alloc(c, &c->pre_yy, (size_t)c->B + 1))
+        ctx_alloc(c, &c->pre_ys, (size_t)c->B + 1) || ctx_alloc(c, &c->pre_yy, (size_t)c->B + 1) ||
+        ctx_alloc(c, &c->pre_yf, (size_t)c->B + 1))
       return PCF_ENOMEM;
   }
+  PCF_CUDA(cudaMemcpy(c->pre_yf, pf.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
+  c->cta_yf = pf[ng];
+  c->sm_yf = smem_ystep(Nmax, gmax);
   PCF_CUDA(cudaMemcpy(c->d_groups, groups.data(), sizeof(int2) * ng, cudaMemcpyHostToDevice));
   PCF_CUDA(cudaMemcpy(c->pre_ya, pa.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
   PCF_CUDA(cudaMemcpy(c->pre_ys, ps.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
@@ -712,6 +731,7 @@ static pcf_status set_split_groups(pcf_ctx* c, int G) {
   c->buf_ys = (int)ysolve_buffer(Nmax, gmax);
   c->rows_ys = Nmax / 2 + 1;
   PCF_CUDA(set_split_smem(sa, ss, sy));
+  if (c->sm_yf <= 227 * 1024) PCF_CUDA(set_ystep_smem(c->sm_yf));
   int dev = 0, nsm = 0;
   PCF_CUDA(cudaGetDevice(&dev));
   PCF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -728,6 +748,7 @@ static pcf_status autotune_split(pcf_ctx* c) {
   PCF_CUDA(cudaEventCreate(&a));
   PCF_CUDA(cudaEventCreate(&b));
   int best = 2;
+  bool best_fused = false;
   float best_ms = 1e30f;
   int last = 0;
   for (int G0 : cand) {
@@ -736,27 +757,39 @@ static pcf_status autotune_split(pcf_ctx* c) {
     last = G;
     if (set_split_groups(c, G) != PCF_OK) continue;
     if (c->sgrp != G) continue;
-    auto seq = [&] {
-      launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), MODE_PHI);
-      launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_of(c, c->pre_ys), MODE_PHI);
-      launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), 1, 1);
-    };
-    seq();
-    PCF_CUDA(cudaEventRecord(a, c->cs));
-    for (int r = 0; r < 3; ++r) seq();
-    PCF_CUDA(cudaEventRecord(b, c->cs));
-    PCF_CUDA(cudaEventSynchronize(b));
-    float ms = 0.f;
-    PCF_CUDA(cudaEventElapsedTime(&ms, a, b));
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = G;
+    for (int fuse = 0; fuse < 2; ++fuse) {
+      if (fuse && c->sm_yf > 227 * 1024) continue;
+      if ((c->prm.solve_kind == 3 && fuse) || (c->prm.solve_kind == 4 && !fuse)) continue;
+      auto seq = [&] {
+        if (fuse) {
+          launch_ystep(c->cta_yf, c->sm_yf, c->cs, gl_of(c, c->pre_yf), MODE_PHI);
+          return;
+        }
+        launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), MODE_PHI);
+        launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_of(c, c->pre_ys),
+                      MODE_PHI);
+        launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), 1, 1);
+      };
+      seq();
+      PCF_CUDA(cudaEventRecord(a, c->cs));
+      for (int r = 0; r < 3; ++r) seq();
+      PCF_CUDA(cudaEventRecord(b, c->cs));
+      PCF_CUDA(cudaEventSynchronize(b));
+      float ms = 0.f;
+      PCF_CUDA(cudaEventElapsedTime(&ms, a, b));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = G;
+        best_fused = fuse != 0;
+      }
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   c->tuned_split_ms = best_ms / 3.0;
-  return set_split_groups(c, best);
+  const pcf_status st = set_split_groups(c, best);
+  c->fused = st == PCF_OK && best_fused;
+  return st;
 }
 
 // Time the Stokes-step mode kernel on the batch for each candidate tile; keep the fastest.
@@ -981,7 +1014,10 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
     return fail(PCF_ECUDA);
   const int want = list[0].modes_per_block;
   st = want > 0 ? set_mode_tiles(c, want) : autotune_tiles(c);
-  if (st == PCF_OK && want > 0 && c->split) st = set_split_groups(c, want);
+  if (st == PCF_OK && want > 0 && c->split) {
+    st = set_split_groups(c, want);
+    c->fused = st == PCF_OK && c->prm.solve_kind == 4 && c->sm_yf <= 227 * 1024;
+  }
   if (st != PCF_OK) return fail(st);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(PCF_ECUDA);
   *out = c;
@@ -1006,7 +1042,7 @@ int pcf_mode_tile(const pcf_ctx* c) { return c ? (c->split ? c->sgrp : c->mpc) :
 
 int pcf_solve_variant(const pcf_ctx* c) {
   if (!c) return -1;
-  if (c->split) return 2;
+  if (c->split) return c->fused ? 3 : 2;
   return c->hinst[0].dense[0] ? 1 : 0;
 }
 
@@ -1234,7 +1270,7 @@ pcf_status pcf_kernel_times(pcf_ctx* c, double* ms, long long* launches, int n) 
   return PCF_OK;
 }
 
-int pcf_launches_per_step(pcf_ctx* c) { return c ? (c->split ? 11 : c->mixed ? 10 : 6) : 0; }
+int pcf_launches_per_step(pcf_ctx* c) { return c ? (c->split ? (c->fused ? 7 : 11) : c->mixed ? 10 : 6) : 0; }
 
 pcf_status pcf_probe_fp64_peak(void* stream, double* gflops) {
   if (!gflops) return PCF_EINVAL;

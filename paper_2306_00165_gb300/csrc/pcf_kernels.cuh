@@ -86,5 +86,9 @@ void launch_jnorm(int ninst, cudaStream_t s, const Inst* insts, int step_index);
 int ysolve_ctas_per_sm(size_t smem);
 void launch_ysynth_split(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int slot, int check_active);
 cudaError_t set_split_smem(size_t analysis, size_t solve, size_t synth);
+// The fused per-mode half-step (analysis + solve + synthesis), one CTA per (group, mode).
+size_t smem_ystep(int N, int G);
+void launch_ystep(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op);
+cudaError_t set_ystep_smem(size_t smem);
 
 }  // namespace pcf

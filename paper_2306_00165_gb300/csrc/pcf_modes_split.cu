@@ -171,6 +171,7 @@ __device__ __forceinline__ void cp_async16(double* dst, const double* src) {
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 struct SolveItem {
   int first, nI, m, g;
@@ -492,6 +493,357 @@ static size_t col_pad_host(int G) {
   while (sp < 2 * (size_t)G) sp <<= 1;
   return sp;
 }
+// ---------------------------------------------------------------- fused per-mode half-step
+// CTA = (instance group, mode m): the whole per-mode work of one half-step of the descent
+// (PHI: the NSE Stokes step and r1; PSI_UPDATE: the dummy-dynamics Stokes step, f and the
+// update) for the group's instances, with every intermediate in shared memory:
+//   analysis (3 components) -> Stokes solve (parity groups 0, 1) -> epilogue (r1 or the new
+//   u, to global memory and to shared memory) -> synthesis (V_u V_v V_w W_u W_w of r1 or u).
+// The lane mappings, and the operations of every output, are those of k_yanalysis, k_ysolve
+// and k_ysynth, so the results are bit-identical to the split kernels.
+constexpr int kStepThreads = 256;
+
+struct StepLayout {
+  int cheb, dense, v, fr, st, uh, sc, out, total;  // offsets in doubles
+};
+__host__ __device__ inline StepLayout step_layout(int N, int SP) {
+  const int H = N / 2 + 1, ny = N + 1, XS = SP + 1, L2 = 2 * H;
+  StepLayout L;
+  L.cheb = 0;
+  L.dense = L.cheb + ((6 * H * H + 1) & ~1);
+  L.v = L.dense + ((10 * H * H + 1) & ~1);
+  L.fr = L.v + 3 * 2 * H * XS;
+  L.st = L.fr + (SP / 2) * 6 * L2;
+  L.uh = L.st + 3 * ny * XS;
+  L.sc = L.uh + 3 * ny * XS;
+  L.out = L.sc + 6 * H * XS;
+  L.total = L.out + 3 * 2 * H * XS;
+  return L;
+}
+
+__global__ void __launch_bounds__(kStepThreads) k_ystep(GroupLaunch gl, int op) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ int live[kMaxGroup];
+  __shared__ double ik2_sh;
+  int m;
+  const int2 grp = gl.groups[find_group(gl, blockIdx.x, &m)];
+  const int first = grp.x, nI = grp.y;
+  const Inst& I0 = gl.insts[first];
+  const int N = I0.N, H = N / 2 + 1, Mh = H, L2 = 2 * H, ny = I0.ny, nm = I0.nmodes, Mz = I0.Mz, half = N / 2;
+  const int SP = col_pad(nI), XS = SP + 1, RW = 32 / SP;
+  const bool phi = op == MODE_PHI;
+  const int sig = phi ? 0 : 1;
+  const DenseLayout DL(N);
+  const ChebLayout CL(N);
+  const StepLayout SL = step_layout(N, SP);
+  double* CH = sm + SL.cheb;   // Chebyshev tables (Ce Co De Do Ae Ao)
+  double* D = sm + SL.dense;   // the 10 operator blocks of mode m
+  double* V = sm + SL.v;       // [3][2H][XS] folded product values: P rows 0..H-1, Q rows H..H+N/2-1
+  double* FR = sm + SL.fr;     // [SP/2][3][2][L2] right-hand sides (class-split)
+  double* ST = sm + SL.st;     // [3][ny][XS] state of the step (uhat for PHI, rhat = r1 for PSI)
+  double* UH = sm + SL.uh;     // [3][ny][XS] uhat (PSI)
+  double* SC = sm + SL.sc;     // [6][Mh][XS] solve scratch
+  double* OUT = sm + SL.out;   // [3][2H][XS] new coefficients, class-split rows (even 0..H-1, odd H..)
+  // read-only tables, asynchronously
+  {
+    const double* src = I0.dense[sig] + (size_t)m * DL.per_mode();
+    for (int t = threadIdx.x; t < 10 * Mh * Mh; t += blockDim.x) cp_async8(D + t, src + t);
+    for (int t = threadIdx.x; t < CL.total(); t += blockDim.x) cp_async8(CH + t, I0.cheb + t);
+    cp_commit();
+  }
+  if (threadIdx.x < nI) live[threadIdx.x] = inst_active(gl.insts[first + threadIdx.x]) ? 1 : 0;
+  if (threadIdx.x == 32) {
+    const int ix0 = m / Mz;
+    const double kx0 = I0.kx[ix0], kz0 = I0.kz[m - ix0 * Mz];
+    ik2_sh = (kx0 == 0.0 && kz0 == 0.0) ? 0.0 : 1.0 / (kx0 * kx0 + kz0 * kz0);
+  }
+  // state columns and folded product values (column s = 2 i + part; padding columns zero)
+  for (int t = threadIdx.x; t < 3 * ny * (SP / 2); t += blockDim.x) {
+    const int n = t % ny, r = t / ny, i = r % (SP / 2), c = r / (SP / 2);
+    double2 a = make_double2(0.0, 0.0), u = a;
+    if (i < nI) {
+      const Inst& I = gl.insts[first + i];
+      const size_t gi = ((size_t)c * nm + m) * ny + n;
+      a = (phi ? I.uhat : I.rhat)[gi];
+      if (!phi) u = I.uhat[gi];
+    }
+    double* d = ST + (c * ny + n) * XS + 2 * i;
+    d[0] = a.x;
+    d[1] = a.y;
+    if (!phi) {
+      double* e = UH + (c * ny + n) * XS + 2 * i;
+      e[0] = u.x;
+      e[1] = u.y;
+    }
+  }
+  for (int t = threadIdx.x; t < 3 * H * (SP / 2); t += blockDim.x) {
+    const int i = t % (SP / 2), r = t / (SP / 2), j = r % H, c = r / H;
+    double2 a = make_double2(0.0, 0.0), b = a;
+    if (i < nI) {
+      const double2* xz = gl.insts[first + i].xz + (size_t)c * ny * nm + m;
+      a = xz[(size_t)j * nm];
+      if (j < half) b = xz[(size_t)(N - j) * nm];
+    }
+    double* Vc = V + c * 2 * H * XS;
+    double* p = Vc + j * XS + 2 * i;
+    if (j < half) {
+      p[0] = a.x + b.x;
+      p[1] = a.y + b.y;
+      double* q = Vc + (H + j) * XS + 2 * i;
+      q[0] = a.x - b.x;
+      q[1] = a.y - b.y;
+    } else {
+      p[0] = a.x;
+      p[1] = a.y;
+    }
+  }
+  cp_wait_all();
+  __syncthreads();
+  const double inv_step = phi ? I0.inv_dt : I0.inv_dtau_hat, inv_nu = I0.inv_nu;
+  // ---- analysis: F = (state/step + Chebyshev coefficients of the products)/nu (class-split)
+  {
+    const int hE = (H + 1) / 2, hO = (half + 1) / 2;
+    const int ER = round_up(hE, RW), OR = round_up(hO, RW), per = ER + OR;
+    const double* Ae = CH + CL.Ae();
+    const double* Ao = CH + CL.Ao();
+    for (int t = threadIdx.x; t < 3 * per * SP; t += blockDim.x) {
+      const int sc = t % SP, rr = t / SP, c = rr / per, rs = rr - c * per;
+      const bool even = rs < ER;
+      const int nrow = even ? H : half, hh = even ? hE : hO;
+      const int k0 = even ? rs : rs - ER, k1 = k0 + hh;
+      const bool v0 = k0 < hh, v1 = v0 && k1 < nrow;
+      const double* row0 = (even ? Ae : Ao) + (v0 ? k0 : 0) * H;
+      const double* row1 = (even ? Ae : Ao) + (v1 ? k1 : 0) * H;
+      const double* v = V + c * 2 * H * XS + (even ? 0 : H) * XS + sc;
+      const int len = even ? H : half;
+      double a0 = 0.0, a1 = 0.0;
+      for (int j = 0; j < len; ++j) {
+        const double x = v[j * XS];
+        a0 = fma(row0[j], x, a0);
+        a1 = fma(row1[j], x, a1);
+      }
+      const int i = sc >> 1, part = sc & 1;
+      if (i >= nI) continue;
+      double* fr = FR + (i * 3 + c) * 2 * L2 + part * L2;
+      const double* st = ST + c * ny * XS + sc;
+      if (v0) fr[even ? k0 : Mh + k0] = fma(st[(even ? 2 * k0 : 2 * k0 + 1) * XS], inv_step, a0) * inv_nu;
+      if (v1) fr[even ? k1 : Mh + k1] = fma(st[(even ? 2 * k1 : 2 * k1 + 1) * XS], inv_step, a1) * inv_nu;
+    }
+  }
+  __syncthreads();
+  // ---- Stokes solve per parity group g, epilogue into global memory and OUT
+  const int ix = m / Mz, p = m - ix * Mz;
+  const double kx = I0.kx[ix], kz = I0.kz[p];
+  const bool mean = kx == 0.0 && kz == 0.0;
+  const double ik2 = ik2_sh;
+  const int MM = Mh * Mh, per6 = 6 * L2;
+  double* FV = SC;
+  double* GG = FV + Mh * XS;
+  double* HV = GG + Mh * XS;
+  double* OV = HV + Mh * XS;
+  double* OX = OV + Mh * XS;
+  double* OE = OX + Mh * XS;
+  for (int g = 0; g < 2; ++g) {
+    const int pv = g, pP = 1 - g, McV = (N - pv) / 2 + 1, McP = (N - pP) / 2 + 1;
+    const double* Dg = D + DL.block(g, 0);
+    for (int t = threadIdx.x; t < Mh * SP; t += blockDim.x) {
+      const int s = t % SP, j = t / SP, i = s >> 1, rho = s & 1;
+      double fv = 0.0, gg = 0.0, hh = 0.0;
+      if (i < nI) {
+        const double* fr = FR + i * per6;
+        if (mean) {
+          const int Mc = (N - g) / 2 + 1;
+          if (j < Mc) {
+            fv = fr[(0 * 2 + rho) * L2 + g * Mh + j];
+            gg = fr[(2 * 2 + rho) * L2 + g * Mh + j];
+          }
+        } else {
+          if (j < McV) fv = fr[(1 * 2 + rho) * L2 + pv * Mh + j];
+          if (j < McP) {
+            const double fu = fr[(0 * 2 + (1 - rho)) * L2 + pP * Mh + j];
+            const double fw = fr[(2 * 2 + (1 - rho)) * L2 + pP * Mh + j];
+            const double sgn = rho == 0 ? -1.0 : 1.0;  // Re(i a) = -Im a, Im(i a) = Re a
+            gg = sgn * fma(kx, fu, kz * fw);
+            hh = sgn * fma(kz, fu, -kx * fw);
+          }
+        }
+      }
+      FV[j * XS + s] = fv;
+      GG[j * XS + s] = gg;
+      HV[j * XS + s] = hh;
+    }
+    __syncthreads();
+    {
+      const int Mc0 = (N - g) / 2 + 1;
+      const int nA = mean ? 2 * Mc0 : McV + McP, nB = mean ? 0 : McP;
+      const int hA = (nA + 1) / 2, hB = (nB + 1) / 2;
+      const int PA = round_up(hA, RW), PB = round_up(hB, RW);
+      for (int t = threadIdx.x; t < (PA + PB) * SP; t += blockDim.x) {
+        const int sc = t % SP, rs = t / SP;
+        double a0 = 0.0, a1 = 0.0;
+        double *out0, *out1;
+        bool v0, v1;
+        if (rs < PA) {
+          v0 = rs < hA;
+          v1 = v0 && rs + hA < nA;
+          const int r0 = v0 ? rs : 0, r1 = v1 ? rs + hA : 0;
+          if (mean) {
+            const double* col0 = Dg + 4 * MM + r0;
+            const double* col1 = Dg + 4 * MM + (v1 ? r1 - Mc0 : 0);
+            for (int j = 0; j < Mc0; ++j) {
+              a0 = fma(col0[j * Mh], FV[j * XS + sc], a0);
+              a1 = fma(col1[j * Mh], GG[j * XS + sc], a1);
+            }
+            out0 = OV + r0 * XS + sc;
+            out1 = OX + (v1 ? r1 - Mc0 : 0) * XS + sc;
+          } else {
+            const bool isv0 = r0 < McV, isv1 = r1 < McV;
+            const int rr0 = isv0 ? r0 : r0 - McV, rr1 = isv1 ? r1 : r1 - McV;
+            const double* cA0 = Dg + (isv0 ? 0 : 2) * MM + rr0;
+            const double* cA1 = Dg + (isv1 ? 0 : 2) * MM + rr1;
+            for (int j = 0; j < McV; ++j) {
+              const double x = FV[j * XS + sc];
+              a0 = fma(cA0[j * Mh], x, a0);
+              a1 = fma(cA1[j * Mh], x, a1);
+            }
+            const double* cG0 = cA0 + MM;
+            const double* cG1 = cA1 + MM;
+            for (int j = 0; j < McP; ++j) {
+              const double x = GG[j * XS + sc];
+              a0 = fma(cG0[j * Mh], x, a0);
+              a1 = fma(cG1[j * Mh], x, a1);
+            }
+            out0 = (isv0 ? OV : OX) + rr0 * XS + sc;
+            out1 = (isv1 ? OV : OX) + rr1 * XS + sc;
+          }
+        } else {
+          const int q = rs - PA;
+          v0 = q < hB;
+          v1 = v0 && q + hB < nB;
+          const int r0 = v0 ? q : 0, r1 = v1 ? q + hB : 0;
+          const double* c0 = Dg + 4 * MM + r0;
+          const double* c1 = Dg + 4 * MM + r1;
+          for (int j = 0; j < McP; ++j) {
+            const double x = HV[j * XS + sc];
+            a0 = fma(c0[j * Mh], x, a0);
+            a1 = fma(c1[j * Mh], x, a1);
+          }
+          out0 = OE + r0 * XS + sc;
+          out1 = OE + r1 * XS + sc;
+        }
+        if (v0) *out0 = a0;
+        if (v1) *out1 = a1;
+      }
+    }
+    __syncthreads();
+    // assembly: v (class g) and u, w (class 1-g); mean mode: u, v = 0, w (class g)
+    const int nV = mean ? (N - g) / 2 + 1 : McV;
+    const int nU = mean ? nV : McP;
+    const int nout = nV + 2 * nU;
+    for (int t = threadIdx.x; t < nI * nout; t += blockDim.x) {
+      const int i = t / nout, kk = t - i * nout;
+      if (!live[i]) continue;
+      int comp, row, n;
+      double vr, vi;
+      if (kk < nV) {
+        comp = 1;
+        row = kk;
+        n = (mean ? g : pv) + 2 * row;
+        vr = mean ? 0.0 : OV[row * XS + 2 * i];
+        vi = mean ? 0.0 : OV[row * XS + 2 * i + 1];
+      } else {
+        const bool isu = kk < nV + nU;
+        comp = isu ? 0 : 2;
+        row = kk - nV - (isu ? 0 : nU);
+        n = (mean ? g : pP) + 2 * row;
+        if (mean) {
+          const double* src = isu ? OV : OX;
+          vr = src[row * XS + 2 * i];
+          vi = src[row * XS + 2 * i + 1];
+        } else {
+          const double xr = OX[row * XS + 2 * i], xi = OX[row * XS + 2 * i + 1];
+          const double er = OE[row * XS + 2 * i], ei = OE[row * XS + 2 * i + 1];
+          if (isu) {
+            vr = fma(kx, xi, kz * ei) * ik2;
+            vi = -fma(kx, xr, kz * er) * ik2;
+          } else {
+            vr = fma(kz, xi, -kx * ei) * ik2;
+            vi = fma(-kz, xr, kx * er) * ik2;
+          }
+        }
+      }
+      const Inst& I = gl.insts[first + i];
+      const size_t gidx = ((size_t)comp * nm + m) * ny + n;
+      const double* st = ST + (comp * ny + n) * XS + 2 * i;
+      double nr, ni;
+      if (phi) {
+        nr = (vr - st[0]) * inv_step;
+        ni = (vi - st[1]) * inv_step;
+        I.rhat[gidx] = make_double2(nr, ni);
+      } else {
+        const double* uo = UH + (comp * ny + n) * XS + 2 * i;
+        const double fr = -(vr - st[0]) * inv_step;
+        const double fi = -(vi - st[1]) * inv_step;
+        nr = fma(I.dtau, fr, uo[0]);
+        ni = fma(I.dtau, fi, uo[1]);
+        I.uhat[gidx] = make_double2(nr, ni);
+      }
+      double* o = OUT + (comp * 2 * H + (n & 1) * H + (n >> 1)) * XS + 2 * i;
+      o[0] = nr;
+      o[1] = ni;
+    }
+    // the next group's right-hand sides do not touch OV/OX/OE; its products wait at the barrier
+  }
+  __syncthreads();
+  // ---- synthesis of the new coefficients: V_c (values) and W_c (y-derivative values)
+  {
+    const int hJ = (H + 1) / 2, JR = round_up(hJ, RW);
+    const int slot = phi ? 1 : 0;
+    for (int t = threadIdx.x; t < kFieldsY * JR * SP; t += blockDim.x) {
+      const int sc = t % SP, rr = t / SP, qf = rr / JR, j0 = rr - qf * JR, j1 = j0 + hJ;
+      const int c = qf < 3 ? qf : (qf == 3 ? 0 : 2);
+      const bool deriv = qf >= 3;
+      const bool v0 = j0 < hJ, v1 = v0 && j1 < H;
+      const double* ME = CH + (deriv ? CL.De() : CL.Ce());
+      const double* MO = CH + (deriv ? CL.Do() : CL.Co());
+      const double* re0 = ME + (v0 ? j0 : 0) * H;
+      const double* ro0 = MO + (v0 ? j0 : 0) * H;
+      const double* re1 = ME + (v1 ? j1 : 0) * H;
+      const double* ro1 = MO + (v1 ? j1 : 0) * H;
+      const double* AE = OUT + c * 2 * H * XS + sc;
+      const double* AO = AE + H * XS;
+      double e0 = 0.0, o0 = 0.0, e1 = 0.0, o1 = 0.0;
+      for (int k = 0; k < H; ++k) {
+        const double x = AE[k * XS];
+        e0 = fma(re0[k], x, e0);
+        e1 = fma(re1[k], x, e1);
+      }
+      for (int k = 0; k < H - 1; ++k) {
+        const double x = AO[k * XS];
+        o0 = fma(ro0[k], x, o0);
+        o1 = fma(ro1[k], x, o1);
+      }
+      const int i = sc >> 1, part = sc & 1;
+      if (!v0 || i >= nI || !live[i]) continue;
+      double* dst = reinterpret_cast<double*>(gl.insts[first + i].yv + ((size_t)slot * kFieldsY + qf) * ny * nm + m) + part;
+      dst[(size_t)j0 * nm * 2] = e0 + o0;
+      if (j0 < half) dst[(size_t)(N - j0) * nm * 2] = deriv ? o0 - e0 : e0 - o0;
+      if (v1) {
+        dst[(size_t)j1 * nm * 2] = e1 + o1;
+        if (j1 < half) dst[(size_t)(N - j1) * nm * 2] = deriv ? o1 - e1 : e1 - o1;
+      }
+    }
+  }
+}
+
+size_t smem_ystep(int N, int G) { return sizeof(double) * (size_t)step_layout(N, (int)col_pad_host(G)).total; }
+void launch_ystep(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op) {
+  k_ystep<<<ctas, kStepThreads, smem, s>>>(gl, op);
+}
+cudaError_t set_ystep_smem(size_t smem) {
+  return cudaFuncSetAttribute(k_ystep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 size_t smem_yanalysis(int N, int G) {
   const size_t H = N / 2 + 1, XS = col_pad_host(G) + 1;
   return sizeof(double) * (2 * H * H + (2 * H) * XS);

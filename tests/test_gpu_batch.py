@@ -109,16 +109,19 @@ def test_uneven_64_instance_batch(pcf):
         assert _rel(got, ref) <= TOL
 
 
-def test_split_mode_kernels_match_the_single_mode_kernel(pcf):
-    # solve_kind 0 runs the per-mode work of a step as analysis, solve and synthesis
-    # kernels; solve_kind 2 keeps it in one kernel.  Same operations per mode: same bits.
+@pytest.mark.parametrize("tile", [0, 3])
+def test_kernel_organisations_give_the_same_bits(pcf, tile):
+    """The per-mode work of a step as one per-mode kernel (solve_kind 2), as analysis, solve
+    and synthesis kernels (3), or as one fused half-step kernel over instance groups (4):
+    the same operations per output, so the same bits."""
     us = _mixed_inputs()
     outs, hists = [], []
-    for kind in (0, 2):
-        s = pcf.Solver.batched(MIXED, solve_kind=kind)
-        assert s.launches_per_step() == (11 if kind == 0 else 6)
+    for kind, launches, variant in ((2, 6, 1), (3, 11, 2), (4, 7, 3)):
+        s = pcf.Solver.batched(MIXED, solve_kind=kind, modes_per_block=tile)
+        assert s.launches_per_step() == launches and s.solve_variant() == variant
         u = _flat(us)
         hists.append(s.descent_step(u, 0.01, 4).cpu().numpy())
         outs.append(u.cpu().numpy())
-    assert np.array_equal(outs[0], outs[1])
-    assert np.array_equal(hists[0], hists[1])
+    for k in (1, 2):
+        assert np.array_equal(outs[0], outs[k])
+        assert np.array_equal(hists[0], hists[k])
