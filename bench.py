@@ -239,6 +239,26 @@ def run_forms(pcf, gi, flush, stream, dev, args):
                                    "32x33x32, Re 400, FP64",
                          "gradient_evals_per_s": BATCH * 50 / (ms * 1e-3), "ms_per_step": ms / 50}
     sq.close()
+    # float-float form (x-z transforms and products in pairs of FP32) vs the FP64 path
+    u8 = gi.batch(gi.streak_roll, range(BATCH), *GRID)
+    res = {}
+    for name, prec in (("fp64", pcf.FP64), ("ff", pcf.FLOAT_FLOAT)):
+        sf = pcf.Solver(*GRID, batch=BATCH, Re=RE, dt=DT, dtau_hat=DTAU_HAT, precision=prec)
+        uf = torch.from_numpy(u8.copy()).to(dev)
+        sf.descent_step(uf, DTAU, 3)
+        ms = _timed_steps(sf, uf, DTAU, 100, flush, stream)
+        r, J = sf.residual(torch.from_numpy(u8.copy()).to(dev))
+        res[name] = (ms / 100, r.cpu().numpy(), J.cpu().numpy())
+        sf.close()
+    rf, r64 = res["ff"][1], res["fp64"][1]
+    out["float_float"] = {
+        "config": "8 streak/roll guesses, 32x33x32, Re 400; x-z FFTs and products in float-float (pairs of FP32, "
+                  "~48 bits) on the FP32 pipe, Chebyshev transforms / solves / norms / state FP64",
+        "gradient_evals_per_s": BATCH * 1e3 / res["ff"][0], "ms_per_step": res["ff"][0],
+        "fp64_ms_per_step": res["fp64"][0], "speedup_vs_fp64": res["fp64"][0] / res["ff"][0],
+        "r1_rel_error_vs_fp64_path_per_component": {
+            c: float(np.max(np.abs(rf[:, i] - r64[:, i])) / np.max(np.abs(r64[:, i]))) for i, c in enumerate("uvw")},
+        "J_rel_error_vs_fp64_path": float(np.max(np.abs(res["ff"][2] - res["fp64"][2]) / res["fp64"][2]))}
     # mixed precision vs FP64 at 128x97x128, Re 1000
     g4 = (128, 97, 128)
     u4 = gi.random_perturbation(*g4, 0.1, 0)[None]

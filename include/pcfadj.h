@@ -54,7 +54,13 @@ typedef enum {
   PCF_ENOTSUP = 7     /* valid request this build does not provide */
 } pcf_status;
 
-typedef enum { PCF_FP64 = 0, PCF_MIXED = 1 } pcf_precision;
+typedef enum {
+  PCF_FP64 = 0,         /* the plain method: FP64 throughout */
+  PCF_MIXED = 1,        /* FP32 x-z transforms and products, split-BF16 tensor-core Chebyshev
+                           transforms, FP64 Stokes solves, norms and state */
+  PCF_FLOAT_FLOAT = 2   /* x-z transforms and products in float-float arithmetic (pairs of
+                           FP32, ~48 significant bits) on the FP32 pipe; everything else FP64 */
+} pcf_precision;
 
 /* Problem description; all instances of a context share one grid.
  * Re: Reynolds number (nu = 1/Re); Lx, Lz: box lengths; dt: physical step of the

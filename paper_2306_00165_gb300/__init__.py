@@ -33,6 +33,7 @@ class _Params(ctypes.Structure):
                 ("solve_kind", ctypes.c_int), ("base_flow", ctypes.c_int)]
 
 COUETTE, POISEUILLE = 0, 1   # laminar base flows u_b = (y,0,0) and (1-y^2,0,0)
+FP64, MIXED, FLOAT_FLOAT = 0, 1, 2   # precision forms (pcf_precision)
 
 
 def load_library(path=None):
@@ -148,7 +149,7 @@ class Solver:
 
     @classmethod
     def batched(cls, grids, Lx=LX_PAPER, Lz=LZ_PAPER, Re=400.0, dt=0.25, dtau_hat=0.25, modes_per_block=0,
-                solve_kind=0):
+                solve_kind=0, precision=0):
         """grids: list of (nx, ny, nz, count) or (nx, ny, nz, count, base_flow)."""
         import torch
         self = cls.__new__(cls)
@@ -156,7 +157,7 @@ class Solver:
         arr = (_Params * len(grids))()
         for k, g in enumerate(grids):
             nx, ny, nz, cnt = g[:4]
-            arr[k] = _Params(nx, ny, nz, cnt, Lx, Lz, Re, dt, dtau_hat, 0, modes_per_block if k == 0 else 0,
+            arr[k] = _Params(nx, ny, nz, cnt, Lx, Lz, Re, dt, dtau_hat, precision, modes_per_block if k == 0 else 0,
                              solve_kind, g[4] if len(g) > 4 else COUETTE)
         h = ctypes.c_void_p()
         _check(self.lib.pcf_batch_create(arr, len(grids), _stream(), ctypes.byref(h)))

@@ -13,6 +13,7 @@ struct pcf_ctx {
   long long total_state = 0;
   bool uniform = true;   // every instance on the same problem
   bool mixed = false;    // mixed-precision form (FP32 planes, split-BF16 Chebyshev, FP64 solves)
+  int plane_kind = 0;    // arithmetic of the x-z plane kernels: 0 FP64, 1 FP32, 2 float-float
   double tuned_ms = 0.0; // autotuner: time of the chosen mode-kernel launch
   cudaStream_t user = nullptr, cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;

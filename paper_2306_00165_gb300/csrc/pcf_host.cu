@@ -407,13 +407,13 @@ pcf_status launch_synth(pcf_ctx* c, int slot, int nf) {
   const int* pre = nf == kFieldsSynth ? c->pre_synth11 : c->pre_synth3;
   const int ctas = nf == kFieldsSynth ? c->cta_synth11 : c->cta_synth3;
   return timed(c, slot == 0 ? 1 : 4,
-               [&] { launch_xzsynth(c->mixed, ctas, c->sm_synth, c->cs, li_of(c, pre), slot, nf); });
+               [&] { launch_xzsynth(c->plane_kind, ctas, c->sm_synth, c->cs, li_of(c, pre), slot, nf); });
 }
 pcf_status launch_prodM(pcf_ctx* c) {
-  return timed(c, 2, [&] { launch_prod(c->mixed, false, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod)); });
+  return timed(c, 2, [&] { launch_prod(c->plane_kind, false, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod)); });
 }
 pcf_status launch_prodN(pcf_ctx* c) {
-  return timed(c, 5, [&] { launch_prod(c->mixed, true, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod)); });
+  return timed(c, 5, [&] { launch_prod(c->plane_kind, true, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod)); });
 }
 
 pcf_status launch_tc_synth(pcf_ctx* c, int slot) {
@@ -870,7 +870,8 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
   int B = 0;
   for (int k = 0; k < nlist; ++k) {
     if (!params_ok(&list[k])) return PCF_EINVAL;
-    if (list[k].precision != PCF_FP64 && list[k].precision != PCF_MIXED) return PCF_ENOTSUP;
+    if (list[k].precision != PCF_FP64 && list[k].precision != PCF_MIXED && list[k].precision != PCF_FLOAT_FLOAT)
+      return PCF_ENOTSUP;
     if (list[k].precision != list[0].precision) return PCF_EINVAL;
     if (list[k].precision == PCF_MIXED && list[k].ny > 113) return PCF_ENOTSUP;
     B += list[k].batch;
@@ -888,6 +889,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
   c->state_len = 3LL * c->nm * list[0].ny;
   c->user = (cudaStream_t)stream;
   c->mixed = list[0].precision == PCF_MIXED;
+  c->plane_kind = c->mixed ? 1 : list[0].precision == PCF_FLOAT_FLOAT ? 2 : 0;
   auto fail = [&](pcf_status s) {
     pcf_destroy(c);
     return s;
@@ -1010,7 +1012,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       (st = upload_prefix(c, per_tca, &c->pre_tca, &c->cta_tca)) != PCF_OK)
     return fail(st);
   if (c->mixed && set_cheb_tc_smem(c->sm_tc)) return fail(PCF_ECUDA);
-  if (set_plane_smem(c->mixed, c->sm_synth, c->sm_prod))
+  if (set_plane_smem(c->plane_kind, c->sm_synth, c->sm_prod))
     return fail(PCF_ECUDA);
   const int want = list[0].modes_per_block;
   st = want > 0 ? set_mode_tiles(c, want) : autotune_tiles(c);
@@ -1072,7 +1074,7 @@ pcf_status pcf_residual(pcf_ctx* c, const double* u, double* r, double* rnorm) {
   if (rnorm) {
     if (c->mixed) PCF_TRY(launch_tc_synth(c, 1));
     PCF_TRY(launch_synth(c, 1, 3));
-    launch_norm_planes(c->mixed, c->cta_synth3, c->cs, li_of(c, c->pre_synth3));
+    launch_norm_planes(c->plane_kind, c->cta_synth3, c->cs, li_of(c, c->pre_synth3));
     k_norm_final<<<1, 32, 0, c->cs>>>(li_of(c, c->pre_inst), rnorm);
   }
   PCF_TRY(check_launch());

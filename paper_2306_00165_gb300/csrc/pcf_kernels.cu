@@ -13,6 +13,7 @@
 // kernels on one y-plane of one field (or product component) per CTA.  All arithmetic is
 // FP64; the FP64 pipe is the bound on GB300, so the transforms are radix-4/2/3 Stockham
 // FFTs in shared memory (x, z) and parity-folded dense Chebyshev matrices (y).
+#include "pcf_ff.cuh"
 #include "pcf_kernels.cuh"
 
 namespace pcf {
@@ -35,6 +36,10 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
+__device__ __forceinline__ ff2 cmul(ff2 a, ff2 b) { return ff2{fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x)}; }
+__device__ __forceinline__ ff2 cadd(ff2 a, ff2 b) { return ff2{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ ff2 csub(ff2 a, ff2 b) { return ff2{a.x - b.x, a.y - b.y}; }
+
 template <class T> struct Cx;
 template <> struct Cx<double> {
   using c = double2;
@@ -44,23 +49,53 @@ template <> struct Cx<float> {
   using c = float2;
   static __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
 };
+template <> struct Cx<ff> {
+  using c = ff2;
+  static __device__ __forceinline__ ff2 mk(ff a, ff b) { return ff2{a, b}; }
+};
+
+// Element type of the y-values, the transformed products and the twiddle tables in memory:
+// the compute type's complex, except in the float-float form, whose plane kernels read and
+// write the FP64 arrays of the y transforms and convert at the boundary.
+template <class T> struct Sto { using c = typename Cx<T>::c; };
+template <> struct Sto<ff> { using c = double2; };
+template <class T> __device__ __forceinline__ typename Cx<T>::c load_c(const typename Sto<T>::c& v) { return v; }
+template <> __device__ __forceinline__ ff2 load_c<ff>(const double2& v) { return ff2{ff(v.x), ff(v.y)}; }
+template <class T> __device__ __forceinline__ typename Sto<T>::c store_c(const typename Cx<T>::c& v) { return v; }
+template <> __device__ __forceinline__ double2 store_c<ff>(const ff2& v) {
+  return make_double2(to_double(v.x), to_double(v.y));
+}
+
+// Accumulator of the plane sums of q^2 (FP64; float-float in the float-float form)
+template <class T> struct Acc { using type = double; };
+template <> struct Acc<ff> { using type = ff; };
+__device__ __forceinline__ void acc_sq(double* s, double q) { *s = fma(q, q, *s); }
+__device__ __forceinline__ void acc_sq(double* s, float q) { *s = fma((double)q, (double)q, *s); }
+__device__ __forceinline__ void acc_sq(ff* s, ff q) { *s = fma(q, q, *s); }
+__device__ __forceinline__ double acc_value(double s) { return s; }
+__device__ __forceinline__ double acc_value(ff s) { return to_double(s); }
 
 // typed views of an instance's plane buffers and twiddles
 template <class T> __device__ __forceinline__ T* phys_of(const Inst& I);
 template <> __device__ __forceinline__ double* phys_of<double>(const Inst& I) { return I.phys; }
 template <> __device__ __forceinline__ float* phys_of<float>(const Inst& I) { return I.physf; }
-template <class T> __device__ __forceinline__ const typename Cx<T>::c* yv_of(const Inst& I);
+template <> __device__ __forceinline__ ff* phys_of<ff>(const Inst& I) { return reinterpret_cast<ff*>(I.phys); }
+template <class T> __device__ __forceinline__ const typename Sto<T>::c* yv_of(const Inst& I);
 template <> __device__ __forceinline__ const double2* yv_of<double>(const Inst& I) { return I.yv; }
 template <> __device__ __forceinline__ const float2* yv_of<float>(const Inst& I) { return I.yvf; }
-template <class T> __device__ __forceinline__ typename Cx<T>::c* xz_of(const Inst& I);
+template <> __device__ __forceinline__ const double2* yv_of<ff>(const Inst& I) { return I.yv; }
+template <class T> __device__ __forceinline__ typename Sto<T>::c* xz_of(const Inst& I);
 template <> __device__ __forceinline__ double2* xz_of<double>(const Inst& I) { return I.xz; }
 template <> __device__ __forceinline__ float2* xz_of<float>(const Inst& I) { return I.xzf; }
-template <class T> __device__ __forceinline__ const typename Cx<T>::c* twx_of(const Inst& I);
+template <> __device__ __forceinline__ double2* xz_of<ff>(const Inst& I) { return I.xz; }
+template <class T> __device__ __forceinline__ const typename Sto<T>::c* twx_of(const Inst& I);
 template <> __device__ __forceinline__ const double2* twx_of<double>(const Inst& I) { return I.twx; }
 template <> __device__ __forceinline__ const float2* twx_of<float>(const Inst& I) { return I.twxf; }
-template <class T> __device__ __forceinline__ const typename Cx<T>::c* twz_of(const Inst& I);
+template <> __device__ __forceinline__ const double2* twx_of<ff>(const Inst& I) { return I.twx; }
+template <class T> __device__ __forceinline__ const typename Sto<T>::c* twz_of(const Inst& I);
 template <> __device__ __forceinline__ const double2* twz_of<double>(const Inst& I) { return I.twz; }
 template <> __device__ __forceinline__ const float2* twz_of<float>(const Inst& I) { return I.twzf; }
+template <> __device__ __forceinline__ const double2* twz_of<ff>(const Inst& I) { return I.twz; }
 
 // ------------------------------------------------------------------ Stockham FFT in shared memory
 template <int R, class C>
@@ -92,7 +127,15 @@ __device__ __forceinline__ void butterfly4(C* v, bool inv) {
   v[3] = csub(t1, t3);
 }
 template <>
+__device__ __forceinline__ void butterfly<2, ff2>(ff2* v, bool) {
+  const ff2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+template <>
 __device__ __forceinline__ void butterfly<4, double2>(double2* v, bool inv) { butterfly4<4, double2>(v, inv); }
+template <>
+__device__ __forceinline__ void butterfly<4, ff2>(ff2* v, bool inv) { butterfly4<4, ff2>(v, inv); }
 template <>
 __device__ __forceinline__ void butterfly<4, float2>(float2* v, bool inv) { butterfly4<4, float2>(v, inv); }
 
@@ -116,6 +159,8 @@ template <>
 __device__ __forceinline__ void butterfly<3, double2>(double2* v, bool inv) { butterfly3(v, inv); }
 template <>
 __device__ __forceinline__ void butterfly<3, float2>(float2* v, bool inv) { butterfly3(v, inv); }
+template <>
+__device__ __forceinline__ void butterfly<3, ff2>(ff2* v, bool inv) { butterfly3(v, inv); }
 
 // One radix-R pass over nb batches of length L, batch b at b LS (Stockham autosort).  The
 // plane kernels use LS = L + 1: a warp that walks down a column of a batch array then meets
@@ -170,10 +215,10 @@ __device__ C* fft_run(C* a, C* b, int L, int LS, int nb, const int* radix, int n
 
 template <class T>
 __device__ __forceinline__ void load_twiddles(const Inst& I, typename Cx<T>::c* twx, typename Cx<T>::c* twz) {
-  const typename Cx<T>::c* sx = twx_of<T>(I);
-  const typename Cx<T>::c* sz = twz_of<T>(I);
-  for (int t = threadIdx.x; t < I.nx; t += blockDim.x) twx[t] = sx[t];
-  for (int t = threadIdx.x; t < I.nz; t += blockDim.x) twz[t] = sz[t];
+  const typename Sto<T>::c* sx = twx_of<T>(I);
+  const typename Sto<T>::c* sz = twz_of<T>(I);
+  for (int t = threadIdx.x; t < I.nx; t += blockDim.x) twx[t] = load_c<T>(sx[t]);
+  for (int t = threadIdx.x; t < I.nz; t += blockDim.x) twz[t] = load_c<T>(sz[t]);
 }
 
 // Shared-memory plan of a plane transform: two buffers of PB complex values; x-stage
@@ -233,11 +278,11 @@ __global__ void __launch_bounds__(128) k_xzsynth_t(LaunchInfo li, int slot, int 
   const int LX = pp.LX, LZ = pp.LZ;
   for (int t = threadIdx.x; t < Mz * LX; t += blockDim.x) B0[t] = Cx<T>::mk(0, 0);
   __syncthreads();
-  const C* src = yv_of<T>(I) + (((size_t)slot * kFieldsY + c_src[f]) * I.ny + j) * (size_t)I.nmodes;
+  const typename Sto<T>::c* src = yv_of<T>(I) + (((size_t)slot * kFieldsY + c_src[f]) * I.ny + j) * (size_t)I.nmodes;
   const int fac = c_fac[f];
   for (int t = threadIdx.x; t < I.nmodes; t += blockDim.x) {
     const int i = t / Mz, p = t - i * Mz;
-    C s = src[t];
+    C s = load_c<T>(src[t]);
     if (fac == 1) { const T k = (T)I.kx[i]; s = Cx<T>::mk(-k * s.y, k * s.x); }
     else if (fac == 2) { const T k = (T)I.kz[p]; s = Cx<T>::mk(-k * s.y, k * s.x); }
     B0[p * LX + xbin(i, Kx, Mx, nx)] = s;
@@ -300,7 +345,7 @@ __device__ __forceinline__ T grad_at(const T* const* F, int c, int d, int e) {
 // Ub, dUb: the base-flow profile U(y_j) and U'(y_j) of the plane (u_b = (U(y), 0, 0)).
 template <class T, bool ADJ>
 __device__ __forceinline__ void product_pair(const Inst& I, const T* const* U, const T* const* Q, int c, T Ub,
-                                             T dUb, int e0, int e1, T* m, double* sq) {
+                                             T dUb, int e0, int e1, T* m, typename Acc<T>::type* sq) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int e = h == 0 ? e0 : e1;
@@ -313,7 +358,7 @@ __device__ __forceinline__ void product_pair(const Inst& I, const T* const* U, c
     } else {
       const T q0 = Q[0][e], q1 = Q[1][e], q2 = Q[2][e];
       const T qc = Q[c][e];
-      *sq = fma((double)qc, (double)qc, *sq);
+      acc_sq(sq, qc);
       const T adv = fma(Ub + u, grad_at<T>(Q, c, 0, e), fma(v, grad_at<T>(Q, c, 1, e), w * grad_at<T>(Q, c, 2, e)));
       const T tr = fma(q0, grad_at<T>(U, 0, c, e), fma(q1, grad_at<T>(U, 1, c, e), q2 * grad_at<T>(U, 2, c, e)));
       T val = adv - tr;
@@ -327,7 +372,8 @@ __device__ __forceinline__ void product_pair(const Inst& I, const T* const* U, c
 // constant, so that the field indices fold and the plane pointers stay in registers).
 template <class T, bool ADJ, int CC>
 __device__ __forceinline__ void product_rows(const Inst& I, const T* const* U, const T* const* Q, T Ub, T dUb, int r0,
-                                             int nrc, int nz, int LZ, typename Cx<T>::c* Z0, double* sq) {
+                                             int nrc, int nz, int LZ, typename Cx<T>::c* Z0,
+                                             typename Acc<T>::type* sq) {
   for (int t = threadIdx.x; t < nrc * nz; t += blockDim.x) {
     const int r = t / nz, z = t - r * nz;
     const int e0 = (2 * (r0 + r)) * nz + z, e1 = e0 + nz;
@@ -370,7 +416,7 @@ __global__ void __launch_bounds__(128) k_prod_t(LaunchInfo li) {
   const bool whole = pp.chunk == nr;
   // the x-stage input X[p][x] lives in B0 when chunked (z chunks use B1), else decided below
   C* X = B0;
-  double sq = 0.0;
+  typename Acc<T>::type sq = 0.0;
   __syncthreads();
   for (int r0 = 0; r0 < nr; r0 += pp.chunk) {
     const int nrc = min(pp.chunk, nr - r0);
@@ -393,8 +439,9 @@ __global__ void __launch_bounds__(128) k_prod_t(LaunchInfo li) {
     __syncthreads();
   }
   if (ADJ) {
-    for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+    double sqd = acc_value(sq);
+    for (int o = 16; o > 0; o >>= 1) sqd += __shfl_down_sync(0xffffffffu, sqd, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sqd;
     __syncthreads();
     if (threadIdx.x == 0) {
       double s = 0.0;
@@ -404,11 +451,11 @@ __global__ void __launch_bounds__(128) k_prod_t(LaunchInfo li) {
   }
   C* Y = fft_run<C>(X, X == B0 ? B1 : B0, nx, LX, Mz, I.rx, I.nrx, twx, false);
   const T sc = (T)I.inv_nxnz;
-  C* dst = xz_of<T>(I) + ((size_t)c * I.ny + j) * I.nmodes;
+  typename Sto<T>::c* dst = xz_of<T>(I) + ((size_t)c * I.ny + j) * I.nmodes;
   for (int t = threadIdx.x; t < I.nmodes; t += blockDim.x) {
     const int i = t / Mz, p = t - i * Mz;
     const C v = Y[p * LX + xbin(i, Kx, Mx, nx)];
-    dst[t] = Cx<T>::mk(v.x * sc, v.y * sc);
+    dst[t] = store_c<T>(Cx<T>::mk(v.x * sc, v.y * sc));
   }
 }
 
@@ -421,8 +468,9 @@ __global__ void __launch_bounds__(128) k_norm_planes_t(LaunchInfo li) {
   const Inst& I = li.insts[b];
   const int c = local % 3, j = local / 3;
   const T* q = fplane<T>(I, 1, c, j);
-  double sq = 0.0;
-  for (int t = threadIdx.x; t < I.nx * I.nz; t += blockDim.x) sq = fma((double)q[t], (double)q[t], sq);
+  typename Acc<T>::type sa = 0.0;
+  for (int t = threadIdx.x; t < I.nx * I.nz; t += blockDim.x) acc_sq(&sa, q[t]);
+  double sq = acc_value(sa);
   for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
   __syncthreads();
@@ -434,33 +482,40 @@ __global__ void __launch_bounds__(128) k_norm_planes_t(LaunchInfo li) {
 }
 
 // host launchers (the kernel templates are instantiated in this translation unit only)
-void launch_xzsynth(bool f32, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int slot, int nf) {
-  if (f32) k_xzsynth_t<float><<<ctas, 128, smem, s>>>(li, slot, nf);
+// plane arithmetic: 0 FP64, 1 FP32 (mixed form), 2 float-float
+void launch_xzsynth(int kind, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int slot, int nf) {
+  if (kind == 1) k_xzsynth_t<float><<<ctas, 128, smem, s>>>(li, slot, nf);
+  else if (kind == 2) k_xzsynth_t<ff><<<ctas, 128, smem, s>>>(li, slot, nf);
   else k_xzsynth_t<double><<<ctas, 128, smem, s>>>(li, slot, nf);
 }
-void launch_prod(bool f32, bool adj, int ctas, size_t smem, cudaStream_t s, LaunchInfo li) {
-  if (f32) {
+void launch_prod(int kind, bool adj, int ctas, size_t smem, cudaStream_t s, LaunchInfo li) {
+  if (kind == 1) {
     if (adj) k_prod_t<float, true><<<ctas, 128, smem, s>>>(li);
     else k_prod_t<float, false><<<ctas, 128, smem, s>>>(li);
+  } else if (kind == 2) {
+    if (adj) k_prod_t<ff, true><<<ctas, 128, smem, s>>>(li);
+    else k_prod_t<ff, false><<<ctas, 128, smem, s>>>(li);
   } else {
     if (adj) k_prod_t<double, true><<<ctas, 128, smem, s>>>(li);
     else k_prod_t<double, false><<<ctas, 128, smem, s>>>(li);
   }
 }
-void launch_norm_planes(bool f32, int ctas, cudaStream_t s, LaunchInfo li) {
-  if (f32) k_norm_planes_t<float><<<ctas, 128, 0, s>>>(li);
+void launch_norm_planes(int kind, int ctas, cudaStream_t s, LaunchInfo li) {
+  if (kind == 1) k_norm_planes_t<float><<<ctas, 128, 0, s>>>(li);
+  else if (kind == 2) k_norm_planes_t<ff><<<ctas, 128, 0, s>>>(li);
   else k_norm_planes_t<double><<<ctas, 128, 0, s>>>(li);
 }
-cudaError_t set_plane_smem(bool f32, size_t synth, size_t prod) {
+template <class T>
+static cudaError_t set_plane_smem_t(size_t synth, size_t prod) {
   cudaError_t e;
-  if (f32) {
-    if ((e = cudaFuncSetAttribute(k_xzsynth_t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)synth))) return e;
-    if ((e = cudaFuncSetAttribute(k_prod_t<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prod))) return e;
-    return cudaFuncSetAttribute(k_prod_t<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prod);
-  }
-  if ((e = cudaFuncSetAttribute(k_xzsynth_t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)synth))) return e;
-  if ((e = cudaFuncSetAttribute(k_prod_t<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prod))) return e;
-  return cudaFuncSetAttribute(k_prod_t<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prod);
+  if ((e = cudaFuncSetAttribute(k_xzsynth_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)synth))) return e;
+  if ((e = cudaFuncSetAttribute(k_prod_t<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prod))) return e;
+  return cudaFuncSetAttribute(k_prod_t<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prod);
+}
+cudaError_t set_plane_smem(int kind, size_t synth, size_t prod) {
+  if (kind == 1) return set_plane_smem_t<float>(synth, prod);
+  if (kind == 2) return set_plane_smem_t<ff>(synth, prod);
+  return set_plane_smem_t<double>(synth, prod);
 }
 
 __global__ void k_norm_final(LaunchInfo li, double* out) {

@@ -49,10 +49,11 @@ __device__ __forceinline__ double norm_from_parts(const Inst& I) {
   return sqrt(0.5 * I.inv_nxnz * s);
 }
 
-void launch_xzsynth(bool f32, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int slot, int nf);
-void launch_prod(bool f32, bool adj, int ctas, size_t smem, cudaStream_t s, LaunchInfo li);
-void launch_norm_planes(bool f32, int ctas, cudaStream_t s, LaunchInfo li);
-cudaError_t set_plane_smem(bool f32, size_t synth, size_t prod);
+// kind: plane arithmetic, 0 FP64, 1 FP32 (mixed form), 2 float-float
+void launch_xzsynth(int kind, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int slot, int nf);
+void launch_prod(int kind, bool adj, int ctas, size_t smem, cudaStream_t s, LaunchInfo li);
+void launch_norm_planes(int kind, int ctas, cudaStream_t s, LaunchInfo li);
+cudaError_t set_plane_smem(int kind, size_t synth, size_t prod);
 __global__ void k_mode(LaunchInfo li, int op, int sig, int mpc, int step_index);
 __global__ void k_norm_final(LaunchInfo li, double* out);
 __global__ void k_fp64_probe(double* out, int iters);
