@@ -31,6 +31,7 @@ struct ff {
 };
 
 __device__ __forceinline__ double to_double(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double to_double(double a) { return a; }
 
 __device__ __forceinline__ ff ff_renorm(float s, float e) {
   const float hi = __fadd_rn(s, e);

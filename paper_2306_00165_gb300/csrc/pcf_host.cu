@@ -425,7 +425,8 @@ pcf_status launch_tc_analysis(pcf_ctx* c) {
 // split mode kernels of the FP64 descent step
 GroupLaunch gl_of(pcf_ctx* c, const int* pre) { return GroupLaunch{c->dinst, pre, c->d_groups, c->ngroups}; }
 pcf_status launch_split_analysis(pcf_ctx* c, int op) {
-  return timed(c, 7, [&] { launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), op); });
+  return timed(c, 7,
+               [&] { launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), op, c->plane_kind == 2); });
 }
 pcf_status launch_split_solve(pcf_ctx* c, int op) {
   return timed(c, op == MODE_PHI ? 3 : 6, [&] {
@@ -441,7 +442,10 @@ pcf_status launch_split_jnorm(pcf_ctx* c, int step_index) {
 }
 pcf_status launch_split_synth(pcf_ctx* c, int slot, int in_step) {
   return timed(c, in_step ? 8 : 0,
-               [&] { launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), slot, in_step); });
+               [&] {
+                 launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), slot, in_step,
+                                     c->plane_kind == 2);
+               });
 }
 
 // y-synthesis of the state (slot 0) or of r1 (slot 1) in either form
@@ -575,6 +579,7 @@ static bool params_ok(const pcf_params* prm) {
 // Device tables of one grid (shared by every instance on that grid).
 struct GridTables {
   double *cheb, *rco, *ccw, *kx, *kz, *y, *ub, *tab0, *tab1, *dense0, *dense1;
+  float2* cheb_ff = nullptr;
   double2 *twx, *twz;
   float2 *twxf = nullptr, *twzf = nullptr;
   uint16_t* tcA = nullptr;
@@ -615,6 +620,16 @@ static pcf_status build_tables(pcf_ctx* c, const pcf_params* prm, GridTables* g)
     tab1 = make_mode_tables(N, kx, kz, g->sig[1], rco);
     if (upload(tab1, &g->tab1)) return PCF_ECUDA;
     c->allocs.push_back(g->tab1);
+  }
+  if (prm->precision == PCF_FLOAT_FLOAT) {
+    // nearest float-float pairs: hi = fl(x), lo = fl(x - hi)
+    std::vector<float2> cf(cheb.size());
+    for (size_t i = 0; i < cheb.size(); ++i) {
+      const float hi = static_cast<float>(cheb[i]);
+      cf[i] = make_float2(hi, static_cast<float>(cheb[i] - (double)hi));
+    }
+    if (upload(cf, &g->cheb_ff)) return PCF_ECUDA;
+    c->allocs.push_back(g->cheb_ff);
   }
   if (prm->precision == PCF_MIXED) {
     if (upload(to_float2(twx), &g->twxf) || upload(to_float2(twz), &g->twzf) ||
@@ -765,10 +780,10 @@ static pcf_status autotune_split(pcf_ctx* c) {
           launch_ystep(c->cta_yf, c->sm_yf, c->cs, gl_of(c, c->pre_yf), MODE_PHI);
           return;
         }
-        launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), MODE_PHI);
+        launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), MODE_PHI, c->plane_kind == 2);
         launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_of(c, c->pre_ys),
                       MODE_PHI);
-        launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), 1, 1);
+        launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), 1, 1, c->plane_kind == 2);
       };
       seq();
       PCF_CUDA(cudaEventRecord(a, c->cs));
@@ -973,7 +988,8 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       I.nu = 1.0 / p.Re; I.dt = p.dt; I.dtau_hat = p.dtau_hat; I.dtau = 0.0;
       I.inv_nu = 1.0 / I.nu; I.inv_dt = 1.0 / I.dt; I.inv_dtau_hat = 1.0 / I.dtau_hat;
       I.inv_nxnz = 1.0 / ((double)p.nx * p.nz);
-      I.cheb = g.cheb; I.rco = g.rco; I.ygrid = g.y; I.ubase = g.ub; I.ccw = g.ccw; I.kx = g.kx; I.kz = g.kz;
+      I.cheb = g.cheb; I.cheb_ff = g.cheb_ff; I.rco = g.rco; I.ygrid = g.y; I.ubase = g.ub; I.ccw = g.ccw;
+      I.kx = g.kx; I.kz = g.kz;
       I.twx = g.twx; I.twz = g.twz;
       I.tab[0] = g.tab0; I.tab[1] = g.tab1;
       I.dense[0] = g.dense0; I.dense[1] = g.dense1;

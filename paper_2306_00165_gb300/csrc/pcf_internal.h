@@ -86,6 +86,7 @@ struct Inst {
   double inv_nu, inv_dt, inv_dtau_hat;  // 1/nu, 1/dt, 1/dtau_hat (IEEE quotients, set on the host)
   // tables (device)
   const double* cheb;
+  const float2* cheb_ff;  // the same table as float-float pairs (hi, lo), for the float-float form
   const double* rco;
   const double* ygrid;
   const double* ubase;  // [2][ny]: base-flow profile U(y_j) and U'(y_j)

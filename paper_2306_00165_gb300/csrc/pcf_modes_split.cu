@@ -26,7 +26,9 @@
 // output is the same sequence of operations as in k_mode, so both paths give bit-identical
 // results.
 #include <algorithm>
+#include <type_traits>
 
+#include "pcf_ff.cuh"
 #include "pcf_kernels.cuh"
 
 namespace pcf {
@@ -56,12 +58,54 @@ __device__ __forceinline__ int col_pad(int nI) {
 }
 __device__ __forceinline__ int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
+// Element t of the Chebyshev table in the arithmetic A (float-float: the precomputed pairs)
+template <class A> __device__ __forceinline__ A cheb_at(const Inst& I, int t);
+template <> __device__ __forceinline__ double cheb_at<double>(const Inst& I, int t) { return I.cheb[t]; }
+template <> __device__ __forceinline__ ff cheb_at<ff>(const Inst& I, int t) {
+  const float2 v = I.cheb_ff[t];
+  return ff(v.x, v.y);
+}
+
+// Dot products of two matrix rows r0, r1 with one column x (stride s) over len terms.  FP64:
+// one chain per row, in index order (the order of k_mode).  Float-float: each row's sum is
+// split over even and odd indices, four independent chains, because a float-float FMA is a
+// chain of ~12 dependent FP32 operations whose latency one chain per row would expose.
+template <class A>
+__device__ __forceinline__ void dot2(const A* r0, const A* r1, const A* x, int s, int len, A& a0, A& a1) {
+  if constexpr (std::is_same<A, ff>::value) {
+    A p0 = A(0.0), p1 = A(0.0), q0 = A(0.0), q1 = A(0.0);
+    int j = 0;
+    for (; j + 1 < len; j += 2) {
+      const A x0 = x[j * s], x1 = x[(j + 1) * s];
+      p0 = fma(r0[j], x0, p0);
+      p1 = fma(r1[j], x0, p1);
+      q0 = fma(r0[j + 1], x1, q0);
+      q1 = fma(r1[j + 1], x1, q1);
+    }
+    if (j < len) {
+      const A x0 = x[j * s];
+      p0 = fma(r0[j], x0, p0);
+      p1 = fma(r1[j], x0, p1);
+    }
+    a0 = a0 + (p0 + q0);
+    a1 = a1 + (p1 + q1);
+  } else {
+    for (int j = 0; j < len; ++j) {
+      const A x0 = x[j * s];
+      a0 = fma(r0[j], x0, a0);
+      a1 = fma(r1[j], x0, a1);
+    }
+  }
+}
+
 // Per-instance flags of a group in shared memory: live[i] = instance takes part in this
 // launch (active; in the dummy-dynamics step the mask already holds this step's J < tol).
 __device__ __forceinline__ void group_flags(const GroupLaunch& gl, int first, int nI, int* live) {
   if (threadIdx.x < nI) live[threadIdx.x] = inst_active(gl.insts[first + threadIdx.x]) ? 1 : 0;
 }
 
+// A: arithmetic of the Chebyshev dot products (double, or ff in the float-float form)
+template <class A>
 __global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int op) {
   extern __shared__ double sm[];
   __shared__ int live[kMaxGroup];
@@ -73,12 +117,12 @@ __global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int
   const int m = local / 3, c = local - 3 * m;
   const int SP = col_pad(nI), XS = SP + 1, RW = 32 / SP;
   const ChebLayout CL(N);
-  double* Ae = sm;                 // [H][H]
-  double* Ao = Ae + H * H;         // [H][H] (rows < H-1 used)
-  double* VP = Ao + H * H;         // [H][XS]    P_j = V_j + V_{N-j} (j < N/2), V_{N/2}
-  double* VQ = VP + H * XS;        // [half][XS] Q_j = V_j - V_{N-j}
+  A* Ae = reinterpret_cast<A*>(sm);  // [H][H]
+  A* Ao = Ae + H * H;                // [H][H] (rows < H-1 used)
+  A* VP = Ao + H * H;                // [H][XS]    P_j = V_j + V_{N-j} (j < N/2), V_{N/2}
+  A* VQ = VP + H * XS;               // [half][XS] Q_j = V_j - V_{N-j}
   group_flags(gl, first, nI, live);
-  for (int t = threadIdx.x; t < 2 * H * H; t += blockDim.x) Ae[t] = I0.cheb[CL.Ae() + t];
+  for (int t = threadIdx.x; t < 2 * H * H; t += blockDim.x) Ae[t] = cheb_at<A>(I0, CL.Ae() + t);
   for (int t = threadIdx.x; t < H * SP / 2; t += blockDim.x) {
     const int i = t % (SP / 2), j = t / (SP / 2);
     double2 a = make_double2(0.0, 0.0), b = a;
@@ -87,16 +131,16 @@ __global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int
       a = xz[(size_t)j * nm];
       if (j < half) b = xz[(size_t)(N - j) * nm];
     }
-    double* p = VP + j * XS + 2 * i;
+    A* p = VP + j * XS + 2 * i;
     if (j < half) {
-      p[0] = a.x + b.x;
-      p[1] = a.y + b.y;
-      double* q = VQ + j * XS + 2 * i;
-      q[0] = a.x - b.x;
-      q[1] = a.y - b.y;
+      p[0] = A(a.x + b.x);
+      p[1] = A(a.y + b.y);
+      A* q = VQ + j * XS + 2 * i;
+      q[0] = A(a.x - b.x);
+      q[1] = A(a.y - b.y);
     } else {
-      p[0] = a.x;
-      p[1] = a.y;
+      p[0] = A(a.x);
+      p[1] = A(a.y);
     }
   }
   __syncthreads();
@@ -121,20 +165,16 @@ __global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int
       if (v0) u0a = st[2 * (even ? 2 * k0 : 2 * k0 + 1)];
       if (v1) u0b = st[2 * (even ? 2 * k1 : 2 * k1 + 1)];
     }
-    const double* row0 = (even ? Ae : Ao) + (v0 ? k0 : 0) * H;
-    const double* row1 = (even ? Ae : Ao) + (v1 ? k1 : 0) * H;
-    const double* v = (even ? VP : VQ) + sc;
+    const A* row0 = (even ? Ae : Ao) + (v0 ? k0 : 0) * H;
+    const A* row1 = (even ? Ae : Ao) + (v1 ? k1 : 0) * H;
+    const A* v = (even ? VP : VQ) + sc;
     const int len = even ? H : half;  // P_j for j < H, Q_j for j < N/2
-    double a0 = 0.0, a1 = 0.0;
-    for (int j = 0; j < len; ++j) {
-      const double x = v[j * XS];
-      a0 = fma(row0[j], x, a0);
-      a1 = fma(row1[j], x, a1);
-    }
+    A a0 = A(0.0), a1 = A(0.0);
+    dot2(row0, row1, v, XS, len, a0, a1);
     if (!out) continue;
     double* fr = gl.insts[first + i].frg + ((size_t)m * 3 + c) * 2 * L2 + part * L2;
-    if (v0) fr[even ? k0 : Mh + k0] = fma(u0a, inv_step, a0) * inv_nu;
-    if (v1) fr[even ? k1 : Mh + k1] = fma(u0b, inv_step, a1) * inv_nu;
+    if (v0) fr[even ? k0 : Mh + k0] = fma(u0a, inv_step, to_double(a0)) * inv_nu;
+    if (v1) fr[even ? k1 : Mh + k1] = fma(u0b, inv_step, to_double(a1)) * inv_nu;
   }
 }
 
@@ -418,6 +458,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_ysolve(GroupLaunch gl, int op
 }
 
 // slot 0: synthesis of uhat, slot 1: of rhat.  q = 0..4: V_u V_v V_w W_u W_w.
+template <class A>
 __global__ void __launch_bounds__(kSplitThreads) k_ysynth(GroupLaunch gl, int slot, int check_active) {
   extern __shared__ double sm[];
   __shared__ int live[kMaxGroup];
@@ -431,24 +472,23 @@ __global__ void __launch_bounds__(kSplitThreads) k_ysynth(GroupLaunch gl, int sl
   const bool deriv = qf >= 3;
   const int SP = col_pad(nI), XS = SP + 1, RW = 32 / SP;
   const ChebLayout CL(N);
-  double* ME = sm;                  // [H][H] Ce or De
-  double* MO = ME + H * H;          // [H][H] Co or Do (columns < H-1 used)
-  double* AE = MO + H * H;          // [H][XS] even coefficients a_{2k}
-  double* AO = AE + H * XS;         // [H-1][XS] odd coefficients a_{2k+1}
+  A* ME = reinterpret_cast<A*>(sm);  // [H][H] Ce or De
+  A* MO = ME + H * H;                // [H][H] Co or Do (columns < H-1 used)
+  A* AE = MO + H * H;                // [H][XS] even coefficients a_{2k}
+  A* AO = AE + H * XS;               // [H-1][XS] odd coefficients a_{2k+1}
   if (threadIdx.x < nI) live[threadIdx.x] = (!check_active || inst_active(gl.insts[first + threadIdx.x])) ? 1 : 0;
-  const double* tabE = I0.cheb + (deriv ? CL.De() : CL.Ce());
-  const double* tabO = I0.cheb + (deriv ? CL.Do() : CL.Co());
+  const int tabE = deriv ? CL.De() : CL.Ce(), tabO = deriv ? CL.Do() : CL.Co();
   for (int t = threadIdx.x; t < H * H; t += blockDim.x) {
-    ME[t] = tabE[t];
-    MO[t] = tabO[t];
+    ME[t] = cheb_at<A>(I0, tabE + t);
+    MO[t] = cheb_at<A>(I0, tabO + t);
   }
   for (int t = threadIdx.x; t < ny * (SP / 2); t += blockDim.x) {
     const int n = t % ny, i = t / ny;
     double2 v = make_double2(0.0, 0.0);
     if (i < nI) v = (slot == 0 ? gl.insts[first + i].uhat : gl.insts[first + i].rhat)[((size_t)c * nm + m) * ny + n];
-    double* d = ((n & 1) ? AO : AE) + (n >> 1) * XS + 2 * i;
-    d[0] = v.x;
-    d[1] = v.y;
+    A* d = ((n & 1) ? AO : AE) + (n >> 1) * XS + 2 * i;
+    d[0] = A(v.x);
+    d[1] = A(v.y);
   }
   __syncthreads();
   // rows j and j + hJ of the output (hJ = H/2 rounded up), values at y_j and y_{N-j}
@@ -456,30 +496,22 @@ __global__ void __launch_bounds__(kSplitThreads) k_ysynth(GroupLaunch gl, int sl
   for (int t = threadIdx.x; t < JR * SP; t += blockDim.x) {
     const int sc = t % SP, j0 = t / SP, j1 = j0 + hJ;
     const bool v0 = j0 < hJ, v1 = v0 && j1 < H;
-    const double* re0 = ME + (v0 ? j0 : 0) * H;
-    const double* ro0 = MO + (v0 ? j0 : 0) * H;
-    const double* re1 = ME + (v1 ? j1 : 0) * H;
-    const double* ro1 = MO + (v1 ? j1 : 0) * H;
-    double e0 = 0.0, o0 = 0.0, e1 = 0.0, o1 = 0.0;
-    for (int k = 0; k < H; ++k) {
-      const double x = AE[k * XS + sc];
-      e0 = fma(re0[k], x, e0);
-      e1 = fma(re1[k], x, e1);
-    }
-    for (int k = 0; k < H - 1; ++k) {
-      const double x = AO[k * XS + sc];
-      o0 = fma(ro0[k], x, o0);
-      o1 = fma(ro1[k], x, o1);
-    }
+    const A* re0 = ME + (v0 ? j0 : 0) * H;
+    const A* ro0 = MO + (v0 ? j0 : 0) * H;
+    const A* re1 = ME + (v1 ? j1 : 0) * H;
+    const A* ro1 = MO + (v1 ? j1 : 0) * H;
+    A e0 = A(0.0), o0 = A(0.0), e1 = A(0.0), o1 = A(0.0);
+    dot2(re0, re1, AE + sc, XS, H, e0, e1);
+    dot2(ro0, ro1, AO + sc, XS, H - 1, o0, o1);
     const int i = sc >> 1, part = sc & 1;
     if (!v0 || i >= nI || !live[i]) continue;
     double* dst = reinterpret_cast<double*>(gl.insts[first + i].yv + ((size_t)slot * kFieldsY + qf) * ny * nm + m) + part;
     // T_{2k} even, T_{2k+1} odd in y; T'_{2k} odd, T'_{2k+1} even
-    dst[(size_t)j0 * nm * 2] = e0 + o0;
-    if (j0 < half) dst[(size_t)(N - j0) * nm * 2] = deriv ? o0 - e0 : e0 - o0;
+    dst[(size_t)j0 * nm * 2] = to_double(e0 + o0);
+    if (j0 < half) dst[(size_t)(N - j0) * nm * 2] = to_double(deriv ? o0 - e0 : e0 - o0);
     if (v1) {
-      dst[(size_t)j1 * nm * 2] = e1 + o1;
-      if (j1 < half) dst[(size_t)(N - j1) * nm * 2] = deriv ? o1 - e1 : e1 - o1;
+      dst[(size_t)j1 * nm * 2] = to_double(e1 + o1);
+      if (j1 < half) dst[(size_t)(N - j1) * nm * 2] = to_double(deriv ? o1 - e1 : e1 - o1);
     }
   }
 }
@@ -861,8 +893,9 @@ size_t smem_ysynth(int N, int G) {
   const size_t H = N / 2 + 1, XS = col_pad_host(G) + 1;
   return sizeof(double) * (2 * H * H + (2 * H) * XS);
 }
-void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op) {
-  k_yanalysis<<<ctas, kSplitThreads, smem, s>>>(gl, op);
+void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith) {
+  if (ff_arith) k_yanalysis<ff><<<ctas, kSplitThreads, smem, s>>>(gl, op);
+  else k_yanalysis<double><<<ctas, kSplitThreads, smem, s>>>(gl, op);
 }
 void launch_ysolve(int ctas, int nitems, int bufsz, int scr_rows, size_t smem, cudaStream_t s, GroupLaunch gl,
                    int op) {
@@ -876,14 +909,19 @@ int ysolve_ctas_per_sm(size_t smem) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ysolve, kSolveThreads, smem) != cudaSuccess) return 0;
   return n;
 }
-void launch_ysynth_split(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int slot, int check_active) {
-  k_ysynth<<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active);
+void launch_ysynth_split(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int slot, int check_active,
+                         bool ff_arith) {
+  if (ff_arith) k_ysynth<ff><<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active);
+  else k_ysynth<double><<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active);
 }
 cudaError_t set_split_smem(size_t analysis, size_t solve, size_t synth) {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_yanalysis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)analysis))) return e;
+  if ((e = cudaFuncSetAttribute(k_yanalysis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)analysis)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_yanalysis<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)analysis))) return e;
   if ((e = cudaFuncSetAttribute(k_ysolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve))) return e;
-  return cudaFuncSetAttribute(k_ysynth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)synth);
+  if ((e = cudaFuncSetAttribute(k_ysynth<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)synth))) return e;
+  return cudaFuncSetAttribute(k_ysynth<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)synth);
 }
 
 }  // namespace pcf
