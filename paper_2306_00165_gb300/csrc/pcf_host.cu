@@ -426,7 +426,7 @@ pcf_status launch_tc_analysis(pcf_ctx* c) {
 GroupLaunch gl_of(pcf_ctx* c, const int* pre) { return GroupLaunch{c->dinst, pre, c->d_groups, c->ngroups}; }
 pcf_status launch_split_analysis(pcf_ctx* c, int op) {
   return timed(c, 7,
-               [&] { launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), op, c->plane_kind == 2); });
+               [&] { launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), op, c->plane_kind == 2, c->smt); });
 }
 pcf_status launch_split_solve(pcf_ctx* c, int op) {
   return timed(c, op == MODE_PHI ? 3 : 6, [&] {
@@ -444,7 +444,7 @@ pcf_status launch_split_synth(pcf_ctx* c, int slot, int in_step) {
   return timed(c, in_step ? 8 : 0,
                [&] {
                  launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), slot, in_step,
-                                     c->plane_kind == 2);
+                                     c->plane_kind == 2, c->smt);
                });
 }
 
@@ -690,7 +690,7 @@ static pcf_status set_mode_tiles(pcf_ctx* c, int want) {
 
 // Instance groups of the split mode kernels: runs of consecutive instances on the same grid,
 // at most G per group, and the derived launch geometry.
-static pcf_status set_split_groups(pcf_ctx* c, int G) {
+static pcf_status set_split_groups(pcf_ctx* c, int G, int mt = 1) {
   int Nmax = 0;
   for (const Inst& I : c->hinst) Nmax = std::max(Nmax, I.N);
   G = std::max(1, std::min(G, split_max_group(Nmax)));
@@ -706,18 +706,20 @@ static pcf_status set_split_groups(pcf_ctx* c, int G) {
     if (fresh) groups.push_back(make_int2(b, 1)); else groups.back().y += 1;
   }
   const int ng = (int)groups.size();
+  int gmax = 1;
+  for (const int2& gq : groups) gmax = std::max(gmax, gq.y);
+  mt = std::max(1, mt);
+  while (mt > 1 && split_col_pad(gmax) * mt > 32) mt >>= 1;
   std::vector<int> pa(ng + 1, 0), ps(ng + 1, 0), py(ng + 1, 0), pf(ng + 1, 0);
   size_t sa = 0, sy = 0;
-  int gmax = 1;
   for (int q = 0; q < ng; ++q) {
     const Inst& I = c->hinst[groups[q].x];
     pf[q + 1] = pf[q] + I.nmodes;
-    pa[q + 1] = pa[q] + split_ctas_per_group(0, I.nmodes);
-    ps[q + 1] = ps[q] + split_ctas_per_group(1, I.nmodes);
-    py[q + 1] = py[q] + split_ctas_per_group(2, I.nmodes);
-    sa = std::max(sa, smem_yanalysis(I.N, groups[q].y));
-    sy = std::max(sy, smem_ysynth(I.N, groups[q].y));
-    gmax = std::max(gmax, groups[q].y);
+    pa[q + 1] = pa[q] + split_ctas_per_group(0, I.nmodes, mt);
+    ps[q + 1] = ps[q] + split_ctas_per_group(1, I.nmodes, mt);
+    py[q + 1] = py[q] + split_ctas_per_group(2, I.nmodes, mt);
+    sa = std::max(sa, smem_yanalysis(I.N, groups[q].y, mt));
+    sy = std::max(sy, smem_ysynth(I.N, groups[q].y, mt));
   }
   // the persistent solve lays out every item in buffers sized for the largest grid and group
   const size_t ss = smem_ysolve(Nmax, gmax);
@@ -736,6 +738,7 @@ static pcf_status set_split_groups(pcf_ctx* c, int G) {
   PCF_CUDA(cudaMemcpy(c->pre_ys, ps.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
   PCF_CUDA(cudaMemcpy(c->pre_yy, py.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
   c->sgrp = G;
+  c->smt = mt;
   c->ngroups = ng;
   c->cta_ya = pa[ng];
   c->cta_ys = ps[ng];
@@ -762,7 +765,7 @@ static pcf_status autotune_split(pcf_ctx* c) {
   cudaEvent_t a, b;
   PCF_CUDA(cudaEventCreate(&a));
   PCF_CUDA(cudaEventCreate(&b));
-  int best = 2;
+  int best = 2, best_mt = 1;
   bool best_fused = false;
   float best_ms = 1e30f;
   int last = 0;
@@ -770,39 +773,41 @@ static pcf_status autotune_split(pcf_ctx* c) {
     const int G = std::min(G0, c->B);
     if (G == last) continue;
     last = G;
-    if (set_split_groups(c, G) != PCF_OK) continue;
-    if (c->sgrp != G) continue;
-    for (int fuse = 0; fuse < 2; ++fuse) {
-      if (fuse && c->sm_yf > 227 * 1024) continue;
-      if ((c->prm.solve_kind == 3 && fuse) || (c->prm.solve_kind == 4 && !fuse)) continue;
-      auto seq = [&] {
-        if (fuse) {
-          launch_ystep(c->cta_yf, c->sm_yf, c->cs, gl_of(c, c->pre_yf), MODE_PHI);
-          return;
+    for (int mt = 1; mt <= 16 && split_col_pad(G) * mt <= 32; mt *= 2) {
+      if (set_split_groups(c, G, mt) != PCF_OK || c->sgrp != G || c->smt != mt) continue;
+      for (int fuse = 0; fuse < 2; ++fuse) {
+        if (fuse && (mt > 1 || c->sm_yf > 227 * 1024)) continue;  // the fused kernel has no mode tile
+        if ((c->prm.solve_kind == 3 && fuse) || (c->prm.solve_kind == 4 && !fuse)) continue;
+        auto seq = [&] {
+          if (fuse) {
+            launch_ystep(c->cta_yf, c->sm_yf, c->cs, gl_of(c, c->pre_yf), MODE_PHI);
+            return;
+          }
+          launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), MODE_PHI, c->plane_kind == 2, c->smt);
+          launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_of(c, c->pre_ys),
+                        MODE_PHI);
+          launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), 1, 1, c->plane_kind == 2, c->smt);
+        };
+        seq();
+        PCF_CUDA(cudaEventRecord(a, c->cs));
+        for (int r = 0; r < 3; ++r) seq();
+        PCF_CUDA(cudaEventRecord(b, c->cs));
+        PCF_CUDA(cudaEventSynchronize(b));
+        float ms = 0.f;
+        PCF_CUDA(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = G;
+          best_mt = mt;
+          best_fused = fuse != 0;
         }
-        launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), MODE_PHI, c->plane_kind == 2);
-        launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_of(c, c->pre_ys),
-                      MODE_PHI);
-        launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), 1, 1, c->plane_kind == 2);
-      };
-      seq();
-      PCF_CUDA(cudaEventRecord(a, c->cs));
-      for (int r = 0; r < 3; ++r) seq();
-      PCF_CUDA(cudaEventRecord(b, c->cs));
-      PCF_CUDA(cudaEventSynchronize(b));
-      float ms = 0.f;
-      PCF_CUDA(cudaEventElapsedTime(&ms, a, b));
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = G;
-        best_fused = fuse != 0;
       }
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   c->tuned_split_ms = best_ms / 3.0;
-  const pcf_status st = set_split_groups(c, best);
+  const pcf_status st = set_split_groups(c, best, best_mt);
   c->fused = st == PCF_OK && best_fused;
   return st;
 }

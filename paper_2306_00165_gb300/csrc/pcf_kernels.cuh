@@ -74,20 +74,22 @@ int cheb_tc_tiles(int nmodes);
 // kind: 0 analysis, 1 solve, 2 synthesis.
 // The solve kernel is persistent (ctas <= nitems CTAs loop over the (group, mode, parity)
 // items, double-buffering each item's operands in shared memory).
-int split_ctas_per_group(int kind, int nmodes);
+int split_ctas_per_group(int kind, int nmodes, int mt);
+int split_col_pad(int G);  // columns of a group of G instances (2 G rounded up to a power of two)
 int split_max_group(int N);
-size_t smem_yanalysis(int N, int G);
+size_t smem_yanalysis(int N, int G, int mt);
 size_t ysolve_buffer(int N, int G);
 size_t smem_ysolve(int N, int G);
-size_t smem_ysynth(int N, int G);
+size_t smem_ysynth(int N, int G, int mt);
 // ff_arith: the Chebyshev dot products in float-float arithmetic (float-float form)
-void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith);
+// mt: consecutive modes per CTA of the analysis and synthesis kernels (col_pad(G) mt <= 32)
+void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith, int mt);
 void launch_ysolve(int ctas, int nitems, int bufsz, int scr_rows, size_t smem, cudaStream_t s, GroupLaunch gl,
                    int op);
 void launch_jnorm(int ninst, cudaStream_t s, const Inst* insts, int step_index);
 int ysolve_ctas_per_sm(size_t smem);
 void launch_ysynth_split(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int slot, int check_active,
-                         bool ff_arith);
+                         bool ff_arith, int mt);
 cudaError_t set_split_smem(size_t analysis, size_t solve, size_t synth);
 // The fused per-mode half-step (analysis + solve + synthesis), one CTA per (group, mode).
 size_t smem_ystep(int N, int G);

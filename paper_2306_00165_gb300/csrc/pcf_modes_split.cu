@@ -106,7 +106,7 @@ __device__ __forceinline__ void group_flags(const GroupLaunch& gl, int first, in
 
 // A: arithmetic of the Chebyshev dot products (double, or ff in the float-float form)
 template <class A>
-__global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int op) {
+__global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int op, int mt) {
   extern __shared__ double sm[];
   __shared__ int live[kMaxGroup];
   int local;
@@ -114,8 +114,9 @@ __global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int
   const int first = grp.x, nI = grp.y;
   const Inst& I0 = gl.insts[first];
   const int N = I0.N, H = N / 2 + 1, Mh = H, L2 = 2 * H, ny = I0.ny, nm = I0.nmodes, half = N / 2;
-  const int m = local / 3, c = local - 3 * m;
-  const int SP = col_pad(nI), XS = SP + 1, RW = 32 / SP;
+  const int tile = local / 3, c = local - 3 * tile, m0 = tile * mt;
+  // columns: (mode m0 + mm, instance i, part) = mm SP + 2 i + part, SPt = SP mt <= 32
+  const int SP = col_pad(nI), SPt = SP * mt, XS = SPt + 1, RW = 32 / SPt;
   const ChebLayout CL(N);
   A* Ae = reinterpret_cast<A*>(sm);  // [H][H]
   A* Ao = Ae + H * H;                // [H][H] (rows < H-1 used)
@@ -123,19 +124,20 @@ __global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int
   A* VQ = VP + H * XS;               // [half][XS] Q_j = V_j - V_{N-j}
   group_flags(gl, first, nI, live);
   for (int t = threadIdx.x; t < 2 * H * H; t += blockDim.x) Ae[t] = cheb_at<A>(I0, CL.Ae() + t);
-  for (int t = threadIdx.x; t < H * SP / 2; t += blockDim.x) {
-    const int i = t % (SP / 2), j = t / (SP / 2);
+  for (int t = threadIdx.x; t < H * SPt / 2; t += blockDim.x) {
+    const int pr = t % (SPt / 2), j = t / (SPt / 2), mm = pr / (SP / 2), i = pr - mm * (SP / 2);
+    const int m = m0 + mm;
     double2 a = make_double2(0.0, 0.0), b = a;
-    if (i < nI) {
+    if (i < nI && m < nm) {
       const double2* xz = gl.insts[first + i].xz + (size_t)c * ny * nm + m;
       a = xz[(size_t)j * nm];
       if (j < half) b = xz[(size_t)(N - j) * nm];
     }
-    A* p = VP + j * XS + 2 * i;
+    A* p = VP + j * XS + 2 * pr;
     if (j < half) {
       p[0] = A(a.x + b.x);
       p[1] = A(a.y + b.y);
-      A* q = VQ + j * XS + 2 * i;
+      A* q = VQ + j * XS + 2 * pr;
       q[0] = A(a.x - b.x);
       q[1] = A(a.y - b.y);
     } else {
@@ -149,14 +151,14 @@ __global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int
   // (k, k + hO) of the odd coefficients n = 2k+1 (k < N/2, from Q)
   const int hE = (H + 1) / 2, hO = (half + 1) / 2;
   const int ER = round_up(hE, RW), OR = round_up(hO, RW);
-  for (int t = threadIdx.x; t < (ER + OR) * SP; t += blockDim.x) {
-    const int sc = t % SP, rs = t / SP;
+  for (int t = threadIdx.x; t < (ER + OR) * SPt; t += blockDim.x) {
+    const int sc = t % SPt, rs = t / SPt, mm = sc / SP, m = m0 + mm;
     const bool even = rs < ER;
     const int nrow = even ? H : half, hh = even ? hE : hO;
     const int k0 = even ? rs : rs - ER, k1 = k0 + hh;
     const bool v0 = k0 < hh, v1 = v0 && k1 < nrow;
-    const int i = sc >> 1, part = sc & 1;
-    const bool out = i < nI && live[i];
+    const int i = (sc - mm * SP) >> 1, part = sc & 1;
+    const bool out = i < nI && m < nm && live[i];
     const double* st = nullptr;
     double u0a = 0.0, u0b = 0.0;
     if (out) {
@@ -459,7 +461,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_ysolve(GroupLaunch gl, int op
 
 // slot 0: synthesis of uhat, slot 1: of rhat.  q = 0..4: V_u V_v V_w W_u W_w.
 template <class A>
-__global__ void __launch_bounds__(kSplitThreads) k_ysynth(GroupLaunch gl, int slot, int check_active) {
+__global__ void __launch_bounds__(kSplitThreads) k_ysynth(GroupLaunch gl, int slot, int check_active, int mt) {
   extern __shared__ double sm[];
   __shared__ int live[kMaxGroup];
   int local;
@@ -467,10 +469,11 @@ __global__ void __launch_bounds__(kSplitThreads) k_ysynth(GroupLaunch gl, int sl
   const int first = grp.x, nI = grp.y;
   const Inst& I0 = gl.insts[first];
   const int N = I0.N, H = N / 2 + 1, ny = I0.ny, nm = I0.nmodes, half = N / 2;
-  const int m = local / kFieldsY, qf = local - kFieldsY * m;
+  const int tile = local / kFieldsY, qf = local - kFieldsY * tile, m0 = tile * mt;
   const int c = qf < 3 ? qf : (qf == 3 ? 0 : 2);
   const bool deriv = qf >= 3;
-  const int SP = col_pad(nI), XS = SP + 1, RW = 32 / SP;
+  // columns: (mode m0 + mm, instance i, part) = mm SP + 2 i + part, SPt = SP mt <= 32
+  const int SP = col_pad(nI), SPt = SP * mt, XS = SPt + 1, RW = 32 / SPt;
   const ChebLayout CL(N);
   A* ME = reinterpret_cast<A*>(sm);  // [H][H] Ce or De
   A* MO = ME + H * H;                // [H][H] Co or Do (columns < H-1 used)
@@ -482,19 +485,20 @@ __global__ void __launch_bounds__(kSplitThreads) k_ysynth(GroupLaunch gl, int sl
     ME[t] = cheb_at<A>(I0, tabE + t);
     MO[t] = cheb_at<A>(I0, tabO + t);
   }
-  for (int t = threadIdx.x; t < ny * (SP / 2); t += blockDim.x) {
-    const int n = t % ny, i = t / ny;
+  for (int t = threadIdx.x; t < ny * (SPt / 2); t += blockDim.x) {
+    const int n = t % ny, pr = t / ny, mm = pr / (SP / 2), i = pr - mm * (SP / 2), m = m0 + mm;
     double2 v = make_double2(0.0, 0.0);
-    if (i < nI) v = (slot == 0 ? gl.insts[first + i].uhat : gl.insts[first + i].rhat)[((size_t)c * nm + m) * ny + n];
-    A* d = ((n & 1) ? AO : AE) + (n >> 1) * XS + 2 * i;
+    if (i < nI && m < nm)
+      v = (slot == 0 ? gl.insts[first + i].uhat : gl.insts[first + i].rhat)[((size_t)c * nm + m) * ny + n];
+    A* d = ((n & 1) ? AO : AE) + (n >> 1) * XS + 2 * pr;
     d[0] = A(v.x);
     d[1] = A(v.y);
   }
   __syncthreads();
   // rows j and j + hJ of the output (hJ = H/2 rounded up), values at y_j and y_{N-j}
   const int hJ = (H + 1) / 2, JR = round_up(hJ, RW);
-  for (int t = threadIdx.x; t < JR * SP; t += blockDim.x) {
-    const int sc = t % SP, j0 = t / SP, j1 = j0 + hJ;
+  for (int t = threadIdx.x; t < JR * SPt; t += blockDim.x) {
+    const int sc = t % SPt, j0 = t / SPt, j1 = j0 + hJ, mm = sc / SP, m = m0 + mm;
     const bool v0 = j0 < hJ, v1 = v0 && j1 < H;
     const A* re0 = ME + (v0 ? j0 : 0) * H;
     const A* ro0 = MO + (v0 ? j0 : 0) * H;
@@ -503,8 +507,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_ysynth(GroupLaunch gl, int sl
     A e0 = A(0.0), o0 = A(0.0), e1 = A(0.0), o1 = A(0.0);
     dot2(re0, re1, AE + sc, XS, H, e0, e1);
     dot2(ro0, ro1, AO + sc, XS, H - 1, o0, o1);
-    const int i = sc >> 1, part = sc & 1;
-    if (!v0 || i >= nI || !live[i]) continue;
+    const int i = (sc - mm * SP) >> 1, part = sc & 1;
+    if (!v0 || i >= nI || m >= nm || !live[i]) continue;
     double* dst = reinterpret_cast<double*>(gl.insts[first + i].yv + ((size_t)slot * kFieldsY + qf) * ny * nm + m) + part;
     // T_{2k} even, T_{2k+1} odd in y; T'_{2k} odd, T'_{2k+1} even
     dst[(size_t)j0 * nm * 2] = to_double(e0 + o0);
@@ -516,7 +520,10 @@ __global__ void __launch_bounds__(kSplitThreads) k_ysynth(GroupLaunch gl, int sl
   }
 }
 
-int split_ctas_per_group(int kind, int nmodes) { return nmodes * (kind == 0 ? 3 : kind == 1 ? 2 : kFieldsY); }
+int split_ctas_per_group(int kind, int nmodes, int mt) {
+  const int tiles = (nmodes + mt - 1) / mt;
+  return kind == 0 ? 3 * tiles : kind == 1 ? 2 * nmodes : kFieldsY * tiles;
+}
 // Largest group on a grid: kMaxGroup, and the solve's four outputs per thread
 // (G (N/2 + 1) 3 <= 4 kSolveThreads).
 int split_max_group(int N) { return std::min(kMaxGroup, 4 * kSolveThreads / (3 * (N / 2 + 1))); }
@@ -525,6 +532,7 @@ static size_t col_pad_host(int G) {
   while (sp < 2 * (size_t)G) sp <<= 1;
   return sp;
 }
+int split_col_pad(int G) { return (int)col_pad_host(G); }
 // ---------------------------------------------------------------- fused per-mode half-step
 // CTA = (instance group, mode m): the whole per-mode work of one half-step of the descent
 // (PHI: the NSE Stokes step and r1; PSI_UPDATE: the dummy-dynamics Stokes step, f and the
@@ -876,8 +884,8 @@ cudaError_t set_ystep_smem(size_t smem) {
   return cudaFuncSetAttribute(k_ystep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-size_t smem_yanalysis(int N, int G) {
-  const size_t H = N / 2 + 1, XS = col_pad_host(G) + 1;
+size_t smem_yanalysis(int N, int G, int mt) {
+  const size_t H = N / 2 + 1, XS = col_pad_host(G) * mt + 1;
   return sizeof(double) * (2 * H * H + (2 * H) * XS);
 }
 // Stage buffer of the persistent solve (doubles): operator blocks + right-hand sides of G instances.
@@ -889,13 +897,13 @@ size_t smem_ysolve(int N, int G) {
   const size_t Mh = N / 2 + 1, XS = col_pad_host(G) + 1;
   return sizeof(double) * (2 * ysolve_buffer(N, G) + 6 * Mh * XS);
 }
-size_t smem_ysynth(int N, int G) {
-  const size_t H = N / 2 + 1, XS = col_pad_host(G) + 1;
+size_t smem_ysynth(int N, int G, int mt) {
+  const size_t H = N / 2 + 1, XS = col_pad_host(G) * mt + 1;
   return sizeof(double) * (2 * H * H + (2 * H) * XS);
 }
-void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith) {
-  if (ff_arith) k_yanalysis<ff><<<ctas, kSplitThreads, smem, s>>>(gl, op);
-  else k_yanalysis<double><<<ctas, kSplitThreads, smem, s>>>(gl, op);
+void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith, int mt) {
+  if (ff_arith) k_yanalysis<ff><<<ctas, kSplitThreads, smem, s>>>(gl, op, mt);
+  else k_yanalysis<double><<<ctas, kSplitThreads, smem, s>>>(gl, op, mt);
 }
 void launch_ysolve(int ctas, int nitems, int bufsz, int scr_rows, size_t smem, cudaStream_t s, GroupLaunch gl,
                    int op) {
@@ -910,9 +918,9 @@ int ysolve_ctas_per_sm(size_t smem) {
   return n;
 }
 void launch_ysynth_split(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int slot, int check_active,
-                         bool ff_arith) {
-  if (ff_arith) k_ysynth<ff><<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active);
-  else k_ysynth<double><<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active);
+                         bool ff_arith, int mt) {
+  if (ff_arith) k_ysynth<ff><<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active, mt);
+  else k_ysynth<double><<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active, mt);
 }
 cudaError_t set_split_smem(size_t analysis, size_t solve, size_t synth) {
   cudaError_t e;
