@@ -30,6 +30,13 @@ What it computes (Ashtari & Schneider, arXiv 2306.00165):
   5. u    <- u + dtau f                                   -- Eq. (forward_Euler_update)
 * Cost J = ||r1|| with the volume-normalised L2 norm (1/(2 Lx Lz)) int |r1|^2,
   Clenshaw-Curtis weights in y and the uniform mean in x, z (§2, Fig. 1: J = ||r(u)||).
+* Symmetries of §5.1: s1 [u,v,w](x,y,z) = [-u,-v,w](-x+Lx/2, -y, z+Lz/2) and
+  s2 [u,v,w](x,y,z) = [u,v,-w](x+Lx/2, y, -z), applied literally on the collocation grid
+  (each is an exact permutation of the grid points there).  The symmetric subspace of a
+  set of them is the image of the group average (§3.4: the descent preserves it).
+* Direct numerical simulation for the guesses of §5.2: the Stokes step of step 1 used as
+  a time stepper, u <- u^dt = u + dt r1, with the local extrema in time of ||u|| taken as
+  guesses (discrete extrema: (h_s - h_{s-1}) (h_{s+1} - h_s) < 0).
 """
 import math
 
@@ -289,6 +296,55 @@ class PCFOracle:
             u, J, _, _ = self.descent_step(u, dtau)
             hist.append(J)
         return u, np.array(hist)
+
+    # ---------------------------------------------------------------- symmetries (§5.1)
+    def _grid_map(self, a, ix, iy, iz, signs):
+        """Field g with g_c(x_i, y_j, z_k) = signs_c * a_c(x_ix[i], y_iy[j], z_iz[k])."""
+        val = self.to_phys(a)
+        g = val[:, iy][:, :, ix][:, :, :, iz] * np.asarray(signs, float)[:, None, None, None]
+        return self.to_spec(g)
+
+    def s1(self, a):
+        """s1 [u,v,w](x,y,z) = [-u,-v,w](-x + Lx/2, -y, z + Lz/2) (§5.1).  On the grid:
+        x_i -> x at index (nx/2 - i) mod nx, y_j -> y_{N-j}, z_k -> z at (k + nz/2) mod nz."""
+        ix = (self.nx // 2 - np.arange(self.nx)) % self.nx
+        iy = self.N - np.arange(self.N + 1)
+        iz = (np.arange(self.nz) + self.nz // 2) % self.nz
+        return self._grid_map(a, ix, iy, iz, (-1.0, -1.0, 1.0))
+
+    def s2(self, a):
+        """s2 [u,v,w](x,y,z) = [u,v,-w](x + Lx/2, y, -z) (§5.1)."""
+        ix = (np.arange(self.nx) + self.nx // 2) % self.nx
+        iy = np.arange(self.N + 1)
+        iz = (-np.arange(self.nz)) % self.nz
+        return self._grid_map(a, ix, iy, iz, (1.0, 1.0, -1.0))
+
+    def symmetrize(self, a, mask):
+        """Group average over the symmetries selected by mask (bit 0: s1, bit 1: s2): the
+        projection onto the subspace invariant under all of them."""
+        terms = [a]
+        if mask & 1:
+            terms.append(self.s1(a))
+        if mask & 2:
+            terms += [self.s2(t) for t in terms]
+        return sum(terms) / len(terms)
+
+    # ---------------------------------------------------------------- DNS (§5.2)
+    def dns(self, uhat, nsteps):
+        """nsteps of u <- u^dt = u + dt r1 (the Stokes step of §4 step 1 as a time stepper).
+        Returns the final state and h_s = ||u_s|| for s = 0..nsteps-1 (before each step)."""
+        u = uhat
+        h = []
+        for _ in range(nsteps):
+            h.append(self.norm(u))
+            r1, _ = self.residual(u)
+            u = u + self.dt * r1
+        return u, np.array(h)
+
+    @staticmethod
+    def extrema(h):
+        """Steps s (1 <= s <= len(h) - 2) where h has a strict local extremum."""
+        return [s for s in range(1, len(h) - 1) if (h[s] - h[s - 1]) * (h[s + 1] - h[s]) < 0]
 
     # ---------------------------------------------------------------- checks
     def divergence(self, ahat):

@@ -484,3 +484,88 @@ def test_dmd_recovers_affine_fixed_point():
     assert np.max(np.abs(psi_s - star)) <= 1e-9 * np.max(np.abs(star))
     best, r, costs = dmd.dmd_extrapolate(S, lambda p: np.linalg.norm(p - star), 1e-10)
     assert r == rstar and costs[r] < 1e-8
+
+
+# ------------------------------------------------------------------ symmetric subspace (§5.1, §3.4)
+def test_symmetries_match_their_spectral_form(o16):
+    """The oracle's s1, s2 (applied literally on the collocation grid) equal their
+    coefficient-space forms written from the definitions: s1 = shift(Lx/2, Lz/2) sigma1,
+    s2 = shift(Lx/2, 0) sigma2."""
+    u = gi.random_perturbation(16, 17, 16, 0.1, 11)
+    s1 = _shift(o16, _sigma1(o16, u), LX / 2, LZ / 2)
+    s2 = _shift(o16, _sigma2(o16, u), LX / 2, 0.0)
+    assert np.max(np.abs(o16.s1(u) - s1)) < 1e-16 * 100
+    assert np.max(np.abs(o16.s2(u) - s2)) < 1e-16 * 100
+
+
+def test_symmetry_group(o16):
+    """s1 and s2 are commuting involutions, so {e, s1, s2, s1 s2} is a group of order 4 and
+    its average is a projection."""
+    u = gi.random_perturbation(16, 17, 16, 0.1, 12)
+    assert np.max(np.abs(o16.s1(o16.s1(u)) - u)) < 1e-15
+    assert np.max(np.abs(o16.s2(o16.s2(u)) - u)) < 1e-15
+    assert np.max(np.abs(o16.s1(o16.s2(u)) - o16.s2(o16.s1(u)))) < 1e-15
+
+
+def _inner(o, a, b):
+    return 0.25 * (o.norm(a + b) ** 2 - o.norm(a - b) ** 2)
+
+
+@pytest.mark.parametrize("mask", [1, 2, 3])
+def test_symmetrize_is_an_orthogonal_projection(o16, mask):
+    """Idempotent, invariant under each selected symmetry, self-adjoint in the L2 inner
+    product of the norm (the symmetries are isometries), and admissible."""
+    a = gi.random_perturbation(16, 17, 16, 0.1, 13)
+    b = gi.random_perturbation(16, 17, 16, 0.1, 14)
+    Pa, Pb = o16.symmetrize(a, mask), o16.symmetrize(b, mask)
+    assert np.max(np.abs(o16.symmetrize(Pa, mask) - Pa)) < 1e-16 * 10
+    if mask & 1:
+        assert np.max(np.abs(o16.s1(Pa) - Pa)) < 1e-16 * 10
+    if mask & 2:
+        assert np.max(np.abs(o16.s2(Pa) - Pa)) < 1e-16 * 10
+    assert abs(_inner(o16, Pa, b) - _inner(o16, a, Pb)) < 1e-14 * o16.norm(a) * o16.norm(b)
+    assert 0.1 * o16.norm(a) < o16.norm(Pa) < o16.norm(a)
+    lo, hi = o16.wall_values(Pa)
+    assert np.max(np.abs(lo)) < 1e-15 and np.max(np.abs(hi)) < 1e-15
+    assert np.max(np.abs(o16.divergence(Pa))) < 1e-13
+
+
+def test_descent_preserves_the_symmetric_subspace(o16):
+    """§5.1: a guess symmetric under s1 and s2 stays symmetric along the descent without the
+    symmetries being enforced (§3.4: the descent is equivariant under them)."""
+    u = o16.symmetrize(gi.random_perturbation(16, 17, 16, 0.1, 15), 3)
+    uT, hist = o16.run(u, 0.01, 20)
+    assert hist[-1] < hist[0]
+    assert np.max(np.abs(o16.symmetrize(uT, 3) - uT)) < 1e-14 * np.max(np.abs(uT))
+
+
+def test_s1_is_not_a_symmetry_of_poiseuille_flow():
+    """s1 turns U = 1 - y^2 into -(1 - y^2): it maps plane Poiseuille flow to another flow, so
+    the descent there is not s1-equivariant; s2 leaves U(y) alone and still is."""
+    o = PCFOracle(16, 17, 16, base_flow="poiseuille")
+    u = gi.random_perturbation(16, 17, 16, 0.1, 16)
+    gap1 = np.max(np.abs(o.s1(o.descent_step(u, 0.01)[0]) - o.descent_step(o.s1(u), 0.01)[0]))
+    gap2 = np.max(np.abs(o.s2(o.descent_step(u, 0.01)[0]) - o.descent_step(o.s2(u), 0.01)[0]))
+    assert gap1 > 1e-6 and gap2 < 1e-14
+
+
+# ------------------------------------------------------------------ DNS with the Stokes step (§5.2)
+def test_dns_of_a_mean_flow_perturbation_is_the_implicit_heat_step():
+    """For u = (f(y), 0, 0) all terms of M vanish and the Stokes step is implicit Euler for
+    df/dt = nu f''.  f = cos(pi y / 2) is the slowest Dirichlet mode, so each DNS step
+    multiplies it by 1 / (1 + nu dt pi^2 / 4) (to the tau method's spectral accuracy)."""
+    o = PCFOracle(16, 17, 16, dt=0.05)
+    u = np.zeros((3, o.Mx, o.Mz, o.ny), np.complex128)
+    u[0, 0, 0] = o.Cinv @ np.cos(0.5 * math.pi * o.y)
+    u[2, 0, 0] = -0.5 * u[0, 0, 0]
+    uT, h = o.dns(u, 8)
+    g = 1.0 / (1.0 + o.nu * o.dt * math.pi ** 2 / 4)
+    assert np.max(np.abs(uT - g ** 8 * u)) < 1e-13
+    assert np.allclose(h[1:] / h[:-1], g, rtol=0, atol=1e-13)
+
+
+def test_extrema_brute_force():
+    """Strict discrete extrema only; plateaus and the end points are not extrema."""
+    h = [3.0, 2.0, 1.0, 2.0, 3.0, 2.0, 2.0, 1.0, 1.5]
+    assert PCFOracle.extrema(h) == [2, 4, 7]
+    assert PCFOracle.extrema([1.0, 2.0]) == []
