@@ -209,6 +209,32 @@ def _timed_steps(s, u, dtau, nsteps, flush, stream):
     return tot
 
 
+def run_robustness(pcf, gi, dev, args):
+    """§5.2's robustness experiment, bounded: DNS from random fields of norm 0.2 (the Stokes
+    step as a time stepper, dt 0.005), guesses at the extrema of ||u||(t), then descent with
+    DMD from every guess for a fixed step budget."""
+    import numpy as np
+    import torch
+    from paper_2306_00165_gb300 import robustness as rb
+    u0 = torch.from_numpy(gi.batch(gi.random_perturbation, range(4), *GRID, amplitude=0.2)).to(dev)
+    d = rb.dns_guesses(u0, GRID, Re=RE, dt=0.005, t_end=args.robust_t, max_guesses=16)
+    res, jumps, wall = rb.descend(d["guesses"], GRID, Re=RE, dtau=DTAU, max_steps=args.robust_steps,
+                                  dmd_period=100, dmd_snapshots=20)
+    J0 = np.array([r[0] for r in res])
+    J1 = np.array([r[1] for r in res])
+    return {"config": f"DNS of 4 random fields (||u|| = 0.2, seeds 0-3), 32x33x32, Re 400, dt 0.005, "
+                      f"t = {args.robust_t:g}; guesses = states at the extrema of ||u||(t) (at most 16 per "
+                      f"trajectory); descent with DMD (every 100 steps, 20 snapshots) for {args.robust_steps} "
+                      f"steps of dtau {DTAU} from every guess",
+            "dns_us_per_step_4_instances": 1e6 * d["wall_s"] / d["steps"],
+            "extrema_per_trajectory": d["extrema"], "laminarised_at_step": d["laminar_step"],
+            "guesses": len(res), "descent_s": wall, "dmd_jumps": jumps,
+            "converged_J_below_1e-10": int(sum(1 for r in res if r[2] >= 0)),
+            "J_start_median": float(np.median(J0)), "J_end_median": float(np.median(J1)),
+            "J_reduction_geomean": float(np.exp(np.mean(np.log(J1 / J0)))),
+            "norm_u_end": [round(r[3], 4) for r in res]}
+
+
 def run_forms(pcf, gi, flush, stream, dev, args):
     """The batched, mixed-precision and learned forms of the method, each next to the plain
     FP64 method on the same work."""
@@ -239,6 +265,18 @@ def run_forms(pcf, gi, flush, stream, dev, args):
                                    "32x33x32, Re 400, FP64",
                          "gradient_evals_per_s": BATCH * 50 / (ms * 1e-3), "ms_per_step": ms / 50}
     sq.close()
+    # symmetric subspace (s1 and s2 of §5.1 enforced): projection at entry and after each update
+    ss = pcf.Solver(*GRID, batch=BATCH, Re=RE, dt=DT, dtau_hat=DTAU_HAT, symmetry=pcf.SYM_S1 | pcf.SYM_S2)
+    us_ = torch.from_numpy(gi.batch(gi.streak_roll, range(BATCH), *GRID)).to(dev)
+    ss.descent_step(us_, DTAU, 3)
+    ms = _timed_steps(ss, us_, DTAU, 50, flush, stream)
+    out["symmetric"] = {"config": "8 streak/roll guesses projected onto the s1,s2-symmetric subspace and kept there "
+                                  "(one projection launch per step), 32x33x32, Re 400, FP64",
+                        "gradient_evals_per_s": BATCH * 50 / (ms * 1e-3), "ms_per_step": ms / 50,
+                        "launches_per_step": ss.launches_per_step()}
+    ss.close()
+    if not args.no_robust:
+        out["robustness"] = run_robustness(pcf, gi, dev, args)
     # float-float form (x-z transforms and products in pairs of FP32) vs the FP64 path
     u8 = gi.batch(gi.streak_roll, range(BATCH), *GRID)
     res = {}
@@ -423,6 +461,22 @@ def run_ours(args):
                          "converged": sum(1 for x in steps if x >= 0), "of": BATCH, "steps": steps,
                          "J_final": [float(x) for x in J], "dmd_jumps": jumps,
                          "J_reduction_geomean": float(np.exp(np.mean(np.log(np.array(J) / np.array(J0)))))}
+        # the paper's schedule shape (§6.2: first jump once J is low enough, M = 100 snapshots,
+        # then a gap 7.5x the collection window), with its time axis scaled to this budget:
+        # spacing 10 steps (0.1 tau), gap 7500 steps (75 tau), threshold J < 1e-3
+        ut = torch.from_numpy(u0.copy()).to(dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps, J, jumps = s.run_schedule(ut, DTAU, args.ttc_steps, tol=1e-10, snapshots=101, spacing=10, gap=7500,
+                                         j_start=1e-3, rank_tol=1e-12)
+        torch.cuda.synchronize()
+        wt = time.perf_counter() - t0
+        ttc["dmd_paper_schedule_scaled"] = {
+            "wall_s": round(wt, 3), "max_steps": args.ttc_steps, "tol": 1e-10,
+            "schedule": "101 snapshots every 10 steps, first jump once J < 1e-3, 7500 steps of gap after each jump",
+            "converged": sum(1 for x in steps if x >= 0), "of": BATCH, "steps": steps,
+            "J_final": [float(x) for x in J], "dmd_jumps": jumps,
+            "J_reduction_geomean": float(np.exp(np.mean(np.log(np.array(J) / np.array(J0)))))}
 
     # per-kernel CUDA-event timing (eager launches, same steps, same stream) for the roofline
     s.set_kernel_timing(True)
@@ -486,6 +540,9 @@ def main():
     ap.add_argument("--ttc-steps", type=int, default=20000)
     ap.add_argument("--no-forms", action="store_true", help="skip the batched/mixed/learned forms")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal form")
+    ap.add_argument("--no-robust", action="store_true", help="skip the DNS-guess robustness experiment")
+    ap.add_argument("--robust-t", type=float, default=300.0, help="DNS time of the robustness experiment")
+    ap.add_argument("--robust-steps", type=int, default=5000, help="descent steps per guess there")
     ap.add_argument("--learn-lag", type=int, default=5000, help="steps between a training pair's states")
     ap.add_argument("--learn-iters", type=int, default=3000)
     ap.add_argument("--learn-steps", type=int, default=4000)

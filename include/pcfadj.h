@@ -84,6 +84,9 @@ typedef struct pcf_params {
                            analysis / solve / synthesis kernels.  4: FP64 fused per-mode
                            half-step kernel.  2, 3 and 4 give bit-identical results. */
   int base_flow;        /* pcf_base_flow: the laminar base flow u_b = (U(y), 0, 0) */
+  int symmetry;         /* pcf_symmetry mask enforced along the descent and the DNS (0: none).
+                           s1 requires PCF_COUETTE (it maps the Poiseuille profile to its
+                           negative); PCF_EINVAL otherwise. */
 } pcf_params;
 
 /* Base flows (§3.1 derives the method for a general laminar base flow u_b; §7 names plane
@@ -94,6 +97,20 @@ typedef enum {
   PCF_COUETTE = 0,     /* plane Couette flow:    U = y       (walls moving at +-1) */
   PCF_POISEUILLE = 1   /* plane Poiseuille flow: U = 1 - y^2 (pressure-driven) */
 } pcf_base_flow;
+
+/* Symmetries of §5.1 (bit mask).  s1 = shift-and-rotate, s2 = shift-and-reflect:
+ *   s1 [u,v,w](x,y,z) = [-u,-v,w](-x + Lx/2, -y, z + Lz/2)
+ *   s2 [u,v,w](x,y,z) = [u,v,-w](x + Lx/2, y, -z)
+ * They commute and are involutions; the subspace invariant under a mask is the image of the
+ * group average over {e, s1}, {e, s2} or {e, s1, s2, s1 s2} (an orthogonal projection).
+ * The descent is equivariant under them (§3.4), so it preserves that subspace; enforcing it
+ * (pcf_params.symmetry) projects the state at the start of every call and after every
+ * update, which removes only rounding drift out of the subspace. */
+typedef enum {
+  PCF_SYM_NONE = 0,
+  PCF_SYM_S1 = 1,
+  PCF_SYM_S2 = 2
+} pcf_symmetry;
 
 typedef struct pcf_ctx pcf_ctx;
 
@@ -185,6 +202,34 @@ pcf_status pcf_descent_step_host(pcf_ctx* ctx, double* u_hat_host, double dtau, 
  * w coefficients 0..ny-3. */
 pcf_status pcf_snapshot(pcf_ctx* ctx, const double* u_hat, double* psi);
 
+/* Volume-normalised L2 norm ||u|| of every instance (the norm of J, §2; Table 2 lists
+ * ||u|| of the equilibria found).  norm: device double[batch]. */
+pcf_status pcf_norm(pcf_ctx* ctx, const double* u_hat, double* norm);
+
+/* Project u_hat (every instance, in place) onto the subspace invariant under the symmetries
+ * of mask (pcf_symmetry bits, 0..3; 0 leaves u_hat unchanged): the group average of §5.1's
+ * s1 and s2.  Admissible inputs give admissible outputs.  PCF_EINVAL for a mask outside 0..3. */
+pcf_status pcf_symmetrize(pcf_ctx* ctx, double* u_hat, int mask);
+
+/* Direct numerical simulation with the Stokes step of §4 step 1 as the time stepper (IMEX
+ * Euler: implicit viscous term and pressure, explicit M, step pcf_params.dt):
+ *   u <- u^dt = u + dt r1(u),  nsteps times, in place on u_hat.
+ * §5.2 takes its guesses for the robustness experiment from such a run: the states where
+ * ||u|| (volume-normalised L2) has a local extremum in time.
+ * norm_hist: device [nsteps][batch] doubles, ||u_s|| before step s, or NULL.
+ * guesses: device room for max_guesses batch states ([max_guesses][total state] complex, the
+ *   uhat layout of the whole batch per guess); the state u_s of instance b at each strict
+ *   discrete extremum ((h_s - h_{s-1}) (h_{s+1} - h_s) < 0, 1 <= s <= nsteps - 2) is stored
+ *   at guess k = the number of earlier extrema of b, while k < max_guesses.  May be NULL
+ *   when max_guesses = 0.
+ * n_guesses: device int[batch], zeroed by the call, then the number of extrema found per
+ *   instance (may exceed max_guesses), or NULL.
+ * With pcf_params.symmetry set, the state is projected at the start and after each step.
+ * The explicit advection of Euler's method needs dt <= 2 nu / max|U + u|^2 for the longest
+ * waves (e.g. dt <= 0.005 at Re = 400); the dt = 0.25 of the descent is not a DNS step. */
+pcf_status pcf_dns(pcf_ctx* ctx, double* u_hat, int nsteps, double* norm_hist, double* guesses, int max_guesses,
+                   int* n_guesses);
+
 /* Inverse of pcf_snapshot: completes the wall conditions and rebuilds u_hat. */
 pcf_status pcf_from_snapshot(pcf_ctx* ctx, const double* psi, double* u_hat);
 
@@ -214,6 +259,29 @@ pcf_status pcf_dmd_extrapolate(pcf_ctx* ctx, const double* snapshots, long long 
  * instance's J became non-finite. */
 pcf_status pcf_run(pcf_ctx* ctx, double* u_hat, double dtau, int max_steps, double tol, int dmd_period,
                    int dmd_snapshots, double rank_tol, int* steps_out, double* j_out, int* dmd_jumps);
+
+/* DMD schedule of §6.2.  The paper lets J fall to log J = -4.5 before the first
+ * extrapolation, builds each linear model from M = 100 snapshots 200 time units apart, and
+ * integrates 1.5e5 time units after each jump before it collects again.  Here:
+ * snapshots are taken every `spacing` descent steps; before the first extrapolation they
+ * fill a sliding window of the latest `snapshots`, and the first extrapolation happens at
+ * the first snapshot point where the window is full and the last J < j_start (+INFINITY:
+ * as soon as the window is full); after a jump the descent runs `gap` steps (rounded up to a
+ * multiple of spacing), then collects `snapshots` fresh snapshots and jumps again.
+ * pcf_run(dmd_period P, dmd_snapshots S) is this schedule with spacing P/S, gap 0 and
+ * j_start = +INFINITY. */
+typedef struct pcf_dmd_schedule {
+  int snapshots;     /* stored snapshots per extrapolation, M + 1 >= 3 */
+  int spacing;       /* descent steps between snapshots, >= 1 */
+  int gap;           /* descent steps from a jump to the start of the next collection, >= 0 */
+  double j_start;    /* threshold on J for the first extrapolation (not NaN) */
+  double rank_tol;   /* rank threshold of pcf_dmd_extrapolate, > 0 */
+} pcf_dmd_schedule;
+
+/* pcf_run with a general DMD schedule (NULL: no DMD).  Same outputs, synchronisation and
+ * errors as pcf_run; the snapshot ring holds schedule->snapshots states per instance. */
+pcf_status pcf_run_schedule(pcf_ctx* ctx, double* u_hat, double dtau, int max_steps, double tol,
+                            const pcf_dmd_schedule* schedule, int* steps_out, double* j_out, int* dmd_jumps);
 
 /* The Stokes solve of pcf_influence_matrix_solve for callers that cannot allocate device
  * memory (the paper has no counterpart; this is a library service).  Such callers - an

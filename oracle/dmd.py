@@ -53,3 +53,46 @@ def dmd_extrapolate(S, cost, rank_tol=1e-12, dtau=1.0):
     if best is None:
         return None, 0, costs
     return best[0], best[2], costs
+
+
+def run_schedule(u, step, to_psi, from_psi, cost, max_steps, tol, snapshots, spacing, gap, j_start, rank_tol):
+    """Descent with the DMD schedule of §6.2 (plain host loop).
+
+    step(u, n) -> (u after n descent steps, costs J before each of them).  The run advances in
+    chunks of ``spacing`` steps and stops at the first step whose J < tol.  Before the first
+    extrapolation, the snapshots after every chunk fill a sliding window of the latest
+    ``snapshots``; the first extrapolation happens at the first chunk end where the window is
+    full and the chunk's last J < j_start (§6.2: J falls to the threshold first).  After a
+    jump the descent runs ``gap`` steps (rounded up to whole chunks) and then collects
+    ``snapshots`` fresh snapshots, one per chunk, before the next jump.  A jump is skipped when
+    no candidate has a finite cost.
+
+    Returns (u, steps to J < tol or -1, last J, jump steps)."""
+    import collections
+    window = collections.deque(maxlen=snapshots)
+    phase, wait = "first", 0
+    jumps, taken, J = [], 0, float("nan")
+    gap_chunks = -(-gap // spacing)
+    while taken < max_steps:
+        n = min(spacing, max_steps - taken)
+        u, hist = step(u, n)
+        for s, v in enumerate(hist):
+            J = v
+            if v < tol:
+                return u, taken + s, J, jumps
+        taken += n
+        if phase == "gap":
+            wait -= 1
+            if wait <= 0:
+                phase = "collect"
+            continue
+        window.append(to_psi(u))
+        ready = len(window) == snapshots and (phase == "collect" or J < j_start)
+        if ready:
+            psi, _, _ = dmd_extrapolate(np.stack(window, axis=1), cost, rank_tol)
+            window.clear()
+            if psi is not None:
+                u = from_psi(psi)
+                jumps.append(taken)
+            phase, wait = ("gap", gap_chunks) if gap_chunks > 0 else ("collect", 0)
+    return u, -1, J, jumps

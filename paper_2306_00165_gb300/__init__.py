@@ -25,14 +25,20 @@ class PCFError(RuntimeError):
     pass
 
 
+class _Schedule(ctypes.Structure):
+    _fields_ = [("snapshots", ctypes.c_int), ("spacing", ctypes.c_int), ("gap", ctypes.c_int),
+                ("j_start", ctypes.c_double), ("rank_tol", ctypes.c_double)]
+
+
 class _Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("batch", ctypes.c_int),
                 ("Lx", ctypes.c_double), ("Lz", ctypes.c_double), ("Re", ctypes.c_double),
                 ("dt", ctypes.c_double), ("dtau_hat", ctypes.c_double),
                 ("precision", ctypes.c_int), ("modes_per_block", ctypes.c_int),
-                ("solve_kind", ctypes.c_int), ("base_flow", ctypes.c_int)]
+                ("solve_kind", ctypes.c_int), ("base_flow", ctypes.c_int), ("symmetry", ctypes.c_int)]
 
 COUETTE, POISEUILLE = 0, 1   # laminar base flows u_b = (y,0,0) and (1-y^2,0,0)
+SYM_S1, SYM_S2 = 1, 2        # symmetries of §5.1 (bit mask): shift-and-rotate, shift-and-reflect
 FP64, MIXED, FLOAT_FLOAT = 0, 1, 2   # precision forms (pcf_precision)
 
 
@@ -66,8 +72,12 @@ def load_library(path=None):
         "pcf_descent_step_host": (I, [P, P, D, I, P]),
         "pcf_snapshot": (I, [P, P, P]),
         "pcf_from_snapshot": (I, [P, P, P]),
+        "pcf_symmetrize": (I, [P, P, I]),
+        "pcf_norm": (I, [P, P, P]),
+        "pcf_dns": (I, [P, P, I, P, P, I, P]),
         "pcf_dmd_extrapolate": (I, [P, P, ctypes.c_longlong, I, D, P, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "pcf_run": (I, [P, P, D, I, D, I, I, D, P, P, ctypes.POINTER(I)]),
+        "pcf_run_schedule": (I, [P, P, D, I, D, ctypes.POINTER(_Schedule), P, P, ctypes.POINTER(I)]),
         "pcf_probe_fp64_peak": (I, [P, ctypes.POINTER(D)]),
         "pcf_fno_create": (I, [I, I, I, I, ctypes.c_ulonglong, P, ctypes.POINTER(P)]),
         "pcf_fno_destroy": (None, [P]),
@@ -131,16 +141,17 @@ class Solver:
     states are one flat complex128 tensor (``flat_len`` values, instance views via ``view``)."""
 
     KERNEL_CLASSES = ["ysynth", "xzsynth_u", "prod_M", "mode_phi", "xzsynth_q", "prod_N", "mode_psi",
-                      "yanalysis", "ysynth_step", "jnorm"]
+                      "yanalysis", "ysynth_step", "jnorm", "symmetrize", "dns_aux"]
 
     def __init__(self, nx, ny, nz, batch=1, Lx=LX_PAPER, Lz=LZ_PAPER, Re=400.0, dt=0.25, dtau_hat=0.25,
-                 precision=0, modes_per_block=0, solve_kind=0, base_flow=COUETTE):
+                 precision=0, modes_per_block=0, solve_kind=0, base_flow=COUETTE, symmetry=0):
         import torch
         self.lib = load_library()
         self.shape = state_shape(nx, ny, nz, batch)
         self.nx, self.ny, self.nz, self.batch = nx, ny, nz, batch
         self.dt, self.dtau_hat = dt, dtau_hat
-        p = _Params(nx, ny, nz, batch, Lx, Lz, Re, dt, dtau_hat, precision, modes_per_block, solve_kind, base_flow)
+        p = _Params(nx, ny, nz, batch, Lx, Lz, Re, dt, dtau_hat, precision, modes_per_block, solve_kind, base_flow,
+                    symmetry)
         h = ctypes.c_void_p()
         _check(self.lib.pcf_create(ctypes.byref(p), _stream(), ctypes.byref(h)))
         self._h = h
@@ -150,7 +161,7 @@ class Solver:
     @classmethod
     def batched(cls, grids, Lx=LX_PAPER, Lz=LZ_PAPER, Re=400.0, dt=0.25, dtau_hat=0.25, modes_per_block=0,
                 solve_kind=0, precision=0):
-        """grids: list of (nx, ny, nz, count) or (nx, ny, nz, count, base_flow)."""
+        """grids: list of (nx, ny, nz, count[, base_flow[, symmetry]])."""
         import torch
         self = cls.__new__(cls)
         self.lib = load_library()
@@ -158,7 +169,7 @@ class Solver:
         for k, g in enumerate(grids):
             nx, ny, nz, cnt = g[:4]
             arr[k] = _Params(nx, ny, nz, cnt, Lx, Lz, Re, dt, dtau_hat, precision, modes_per_block if k == 0 else 0,
-                             solve_kind, g[4] if len(g) > 4 else COUETTE)
+                             solve_kind, g[4] if len(g) > 4 else COUETTE, g[5] if len(g) > 5 else 0)
         h = ctypes.c_void_p()
         _check(self.lib.pcf_batch_create(arr, len(grids), _stream(), ctypes.byref(h)))
         self._h = h
@@ -253,6 +264,33 @@ class Solver:
         _check(self.lib.pcf_from_snapshot(self._h, _ptr(psi), _ptr(u)))
         return u
 
+    def norm(self, u):
+        """Volume-normalised L2 norm of every instance: float64 tensor [batch]."""
+        import torch
+        self._chk(u)
+        out = torch.empty(self.batch, dtype=torch.float64, device=self.device)
+        _check(self.lib.pcf_norm(self._h, _ptr(u), _ptr(out)))
+        return out
+
+    def symmetrize(self, u, mask):
+        """Project u in place onto the subspace invariant under the symmetries of mask (§5.1)."""
+        self._chk(u)
+        _check(self.lib.pcf_symmetrize(self._h, _ptr(u), int(mask)))
+        return u
+
+    def dns(self, u, nsteps, max_guesses=0, hist=True):
+        """nsteps of u <- u^dt (the Stokes step as a DNS time stepper), in place on u.
+        Returns (||u|| history [nsteps, batch], guesses [max_guesses, *state shape] or None,
+        extrema found per instance as an int32 tensor [batch])."""
+        import torch
+        self._chk(u)
+        H = torch.empty((nsteps, self.batch), dtype=torch.float64, device=self.device) if hist else None
+        G = (torch.zeros((max_guesses,) + tuple(self.shape), dtype=torch.complex128, device=self.device)
+             if max_guesses > 0 else None)
+        n = torch.zeros(self.batch, dtype=torch.int32, device=self.device)
+        _check(self.lib.pcf_dns(self._h, _ptr(u), int(nsteps), _ptr(H), _ptr(G), int(max_guesses), _ptr(n)))
+        return H, G, n
+
     def dmd_extrapolate(self, snapshots, rank_tol=1e-12, out=None, ld=None):
         """DMD steady state of §6 from snapshots (float64 [M+1, psi_len] rows = snapshots, or a
         strided view with column stride ``ld``); returns (state [1, ...] view of ``out``, rank, J)."""
@@ -277,6 +315,20 @@ class Solver:
         self._chk(u)
         _check(self.lib.pcf_run(self._h, _ptr(u), float(dtau), int(max_steps), float(tol), int(dmd_period),
                                 int(dmd_snapshots), float(rank_tol), steps, J, ctypes.byref(jumps)))
+        return list(steps), list(J), jumps.value
+
+    def run_schedule(self, u, dtau, max_steps, tol=1e-10, snapshots=101, spacing=100, gap=0, j_start=math.inf,
+                     rank_tol=1e-12, dmd=True):
+        """Descent to J < tol with the DMD schedule of §6.2 (see include/pcfadj.h); returns
+        (steps per instance, J per instance, jumps)."""
+        B = self.batch
+        steps = (ctypes.c_int * B)()
+        J = (ctypes.c_double * B)()
+        jumps = ctypes.c_int()
+        self._chk(u)
+        sc = _Schedule(snapshots, spacing, gap, j_start, rank_tol)
+        _check(self.lib.pcf_run_schedule(self._h, _ptr(u), float(dtau), int(max_steps), float(tol),
+                                         ctypes.byref(sc) if dmd else None, steps, J, ctypes.byref(jumps)))
         return list(steps), list(J), jumps.value
 
     def set_kernel_timing(self, enable):

@@ -53,6 +53,13 @@ struct pcf_ctx {
   int hist_cap = 0;
   int* active = nullptr;
   std::map<int, cudaGraphExec_t> graphs;
+  // symmetric subspace and DNS
+  bool any_sym = false;         // some instance enforces a symmetry
+  int sym_ctas = 0, dns_ctas = 0;
+  pcf::DnsInst* d_dns = nullptr;
+  double2* uprev = nullptr;
+  int* dns_count = nullptr;
+  std::map<int, cudaGraphExec_t> dns_graphs;
   // timing
   int timing = 0;
   double kms[pcf::kNumKernelClasses] = {0};

@@ -455,6 +455,11 @@ pcf_status launch_ysynth(pcf_ctx* c, int slot) {
   return launch_mode(c, MODE_SYNTH_ONLY, slot, 0);
 }
 
+// projection onto the symmetric subspace: each instance's own mask (mask_override < 0) or mask
+pcf_status launch_sym(pcf_ctx* c, int mask_override) {
+  return timed(c, 10, [&] { launch_symmetrize(c->sym_ctas, c->B, c->cs, c->dinst, mask_override); });
+}
+
 pcf_status check_launch() {
   PCF_CUDA(cudaGetLastError());
   return PCF_OK;
@@ -501,6 +506,7 @@ pcf_status step_body(pcf_ctx* c, int s) {
     PCF_TRY(launch_prodN(c));
     PCF_TRY(launch_tc_analysis(c));
     PCF_TRY(launch_mode(c, MODE_PSI_UPDATE, 1, s));
+    if (c->any_sym) PCF_TRY(launch_sym(c, -1));  // the next step's synthesis reads the projected state
     return PCF_OK;
   }
   if (c->split && c->fused) {
@@ -511,6 +517,10 @@ pcf_status step_body(pcf_ctx* c, int s) {
     PCF_TRY(launch_prodN(c));
     PCF_TRY(launch_split_jnorm(c, s));
     PCF_TRY(launch_fused_step(c, MODE_PSI_UPDATE));
+    if (c->any_sym) {
+      PCF_TRY(launch_sym(c, -1));
+      PCF_TRY(launch_ysynth(c, 0));
+    }
     return PCF_OK;
   }
   if (c->split) {
@@ -524,6 +534,7 @@ pcf_status step_body(pcf_ctx* c, int s) {
     PCF_TRY(launch_split_jnorm(c, s));
     PCF_TRY(launch_split_analysis(c, MODE_PSI_UPDATE));
     PCF_TRY(launch_split_solve(c, MODE_PSI_UPDATE));
+    if (c->any_sym) PCF_TRY(launch_sym(c, -1));
     PCF_TRY(launch_split_synth(c, 0, 1));
     return PCF_OK;
   }
@@ -533,7 +544,38 @@ pcf_status step_body(pcf_ctx* c, int s) {
   PCF_TRY(launch_synth(c, 1, kFieldsSynth));
   PCF_TRY(launch_prodN(c));
   PCF_TRY(launch_mode(c, MODE_PSI_UPDATE, 1, s));
+  if (c->any_sym) {
+    PCF_TRY(launch_sym(c, -1));
+    PCF_TRY(launch_ysynth(c, 0));
+  }
   return PCF_OK;
+}
+
+// One DNS step u <- u + dt r1 (pcf_dns): ||u|| and the extremum capture of the previous
+// step, M(u), the Stokes step of §4 step 1 (writing r1), the update, and the y-synthesis of
+// the new state for the next step.
+pcf_status dns_body(pcf_ctx* c) {
+  PCF_TRY(launch_synth(c, 0, kFieldsSynth));
+  PCF_TRY(timed(c, 11, [&] {
+    launch_norm_planes(c->plane_kind, c->cta_synth3, c->cs, li_of(c, c->pre_synth3), 0);
+    launch_dns_norm(c->B, c->cs, c->dinst, c->d_dns);
+    launch_dns_capture(c->dns_ctas, c->B, c->cs, c->dinst, c->d_dns);
+  }));
+  PCF_TRY(launch_prodM(c));
+  if (c->mixed) {
+    PCF_TRY(launch_tc_analysis(c));
+    PCF_TRY(launch_mode(c, MODE_PHI, 0, 0));
+  } else if (c->split && c->fused) {
+    PCF_TRY(launch_fused_step(c, MODE_PHI));
+  } else if (c->split) {
+    PCF_TRY(launch_split_analysis(c, MODE_PHI));
+    PCF_TRY(launch_split_solve(c, MODE_PHI));
+  } else {
+    PCF_TRY(launch_mode(c, MODE_PHI, 0, 0));
+  }
+  PCF_TRY(timed(c, 11, [&] { launch_dns_update(c->dns_ctas, c->B, c->cs, c->dinst, c->d_dns); }));
+  if (c->any_sym) PCF_TRY(launch_sym(c, -1));
+  return launch_ysynth(c, 0);
 }
 
 }  // namespace
@@ -573,7 +615,9 @@ long long pcf_psi_len(int nx, int ny, int nz) {
 static bool params_ok(const pcf_params* prm) {
   return grid_ok(prm->nx, prm->ny, prm->nz) && prm->batch >= 1 && prm->Re > 0 && prm->dt > 0 &&
          prm->dtau_hat > 0 && prm->Lx > 0 && prm->Lz > 0 && prm->solve_kind >= 0 && prm->solve_kind <= 4 &&
-         prm->modes_per_block >= 0 && (prm->base_flow == PCF_COUETTE || prm->base_flow == PCF_POISEUILLE);
+         prm->modes_per_block >= 0 && (prm->base_flow == PCF_COUETTE || prm->base_flow == PCF_POISEUILLE) &&
+         prm->symmetry >= 0 && prm->symmetry <= 3 &&
+         !((prm->symmetry & PCF_SYM_S1) && prm->base_flow != PCF_COUETTE);
 }
 
 // Device tables of one grid (shared by every instance on that grid).
@@ -1013,6 +1057,10 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       o_np += 3ULL * p.ny;
       o_fr += 6ULL * (p.ny + 1) * I.nmodes;
       I.hist_stride = B;
+      I.sym = p.symmetry;
+      if (p.symmetry) c->any_sym = true;
+      c->sym_ctas = std::max(c->sym_ctas, symmetrize_ctas(I));
+      c->dns_ctas = std::max(c->dns_ctas, dns_ctas(I));
       per11[b] = kFieldsSynth * p.ny;
       per3[b] = 3 * p.ny;
       per_tcs[b] = kFieldsY * cheb_tc_tiles(I.nmodes);
@@ -1073,6 +1121,7 @@ void pcf_destroy(pcf_ctx* c) {
   if (!c) return;
   if (c->cs) cudaStreamSynchronize(c->cs);
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : c->dns_graphs) cudaGraphExecDestroy(kv.second);
   for (void* p : c->allocs) cudaFree(p);
   if (c->u_dev) cudaFree(c->u_dev);
   if (c->hist_dev) cudaFree(c->hist_dev);
@@ -1095,7 +1144,7 @@ pcf_status pcf_residual(pcf_ctx* c, const double* u, double* r, double* rnorm) {
   if (rnorm) {
     if (c->mixed) PCF_TRY(launch_tc_synth(c, 1));
     PCF_TRY(launch_synth(c, 1, 3));
-    launch_norm_planes(c->plane_kind, c->cta_synth3, c->cs, li_of(c, c->pre_synth3));
+    launch_norm_planes(c->plane_kind, c->cta_synth3, c->cs, li_of(c, c->pre_synth3), 1);
     k_norm_final<<<1, 32, 0, c->cs>>>(li_of(c, c->pre_inst), rnorm);
   }
   PCF_TRY(check_launch());
@@ -1146,6 +1195,7 @@ static pcf_status descent_internal(pcf_ctx* c, double* u, double dtau, int nstep
   }
   PCF_TRY(enter(c));
   PCF_TRY(push_descriptors(c));
+  if (c->any_sym) PCF_TRY(launch_sym(c, -1));  // the run starts in the symmetric subspace
   if (c->timing) {
     PCF_TRY(launch_ysynth(c, 0));
     for (int s = 0; s < nsteps; ++s) PCF_TRY(step_body(c, s));
@@ -1174,48 +1224,56 @@ pcf_status pcf_descent_step(pcf_ctx* c, double* u, double dtau, int nsteps, doub
   return descent_internal(c, u, dtau, nsteps, hist, 0.0);
 }
 
-pcf_status pcf_run(pcf_ctx* c, double* u, double dtau, int max_steps, double tol, int dmd_period, int dmd_snapshots,
-                   double rank_tol, int* steps_out, double* j_out, int* dmd_jumps) {
-  if (!c || !u || max_steps < 1 || !(tol > 0) || !(dtau > 0) || dmd_period < 0) return PCF_EINVAL;
-  const bool dmd = dmd_period > 0;
+// Descent in chunks with convergence masks and the DMD schedule of §6.2 (see pcf_run_schedule).
+static pcf_status run_schedule(pcf_ctx* c, double* u, double dtau, int max_steps, double tol,
+                               const pcf_dmd_schedule* sc, int* steps_out, double* j_out, int* dmd_jumps) {
+  if (!c || !u || max_steps < 1 || !(tol > 0) || !(dtau > 0)) return PCF_EINVAL;
+  const bool dmd = sc != nullptr;
+  if (dmd && (sc->snapshots < 3 || sc->spacing < 1 || sc->gap < 0 || !(sc->rank_tol > 0) || std::isnan(sc->j_start)))
+    return PCF_EINVAL;
   if (dmd && !c->uniform) return PCF_ENOTSUP;
-  if (dmd && (dmd_snapshots < 3 || dmd_period % dmd_snapshots)) return PCF_EINVAL;
   const int B = c->B;
-  const int chunk = dmd ? dmd_period / dmd_snapshots : 100;
+  const int chunk = dmd ? sc->spacing : 100;
+  const int S = dmd ? sc->snapshots : 0;
+  const int gap_chunks = dmd ? (sc->gap + chunk - 1) / chunk : 0;
   const long long plen = pcf_psi_len(c->prm.nx, c->prm.ny, c->prm.nz);
-  double* ring = nullptr;
-  double* hist = nullptr;
-  PCF_CUDA(cudaMalloc(&hist, sizeof(double) * (size_t)chunk * B));
-  if (dmd) {
-    if (cudaMalloc(&ring, sizeof(double) * (size_t)dmd_snapshots * B * plen) != cudaSuccess) {
-      cudaFree(hist);
-      return PCF_ENOMEM;
-    }
-  }
-  std::vector<int> ones(B, 1), steps(B, 0), done(B, 0);
-  std::vector<double> J(B, NAN), hh((size_t)chunk * B);
-  int jumps = 0;
-  pcf_status st = PCF_OK;
-  auto finish = [&](pcf_status s) {
-    cudaStreamSynchronize(c->user);
+  const int sub = std::min(chunk, 256);  // steps per captured graph
+  double *ring = nullptr, *tmp = nullptr, *ordered = nullptr, *hist = nullptr;
+  auto release = [&] {
     if (hist) cudaFree(hist);
     if (ring) cudaFree(ring);
+    if (tmp) cudaFree(tmp);
+    if (ordered) cudaFree(ordered);
+  };
+  if (cudaMalloc(&hist, sizeof(double) * (size_t)chunk * B) != cudaSuccess) return PCF_ENOMEM;
+  if (dmd && (cudaMalloc(&ring, sizeof(double) * (size_t)S * B * plen) != cudaSuccess ||
+              cudaMalloc(&tmp, sizeof(double) * (size_t)B * plen) != cudaSuccess ||
+              cudaMalloc(&ordered, sizeof(double) * (size_t)S * plen) != cudaSuccess)) {
+    release();
+    return PCF_ENOMEM;
+  }
+  enum { FIRST = 0, COLLECT = 1, GAP = 2 };
+  std::vector<int> ones(B, 1), steps(B, 0), done(B, 0), phase(B, FIRST), wait(B, 0), filled(B, 0), next(B, 0);
+  std::vector<double> J(B, NAN), hh((size_t)chunk * B);
+  int jumps = 0;
+  auto finish = [&](pcf_status st) {
+    cudaStreamSynchronize(c->user);
+    release();
     for (int b = 0; b < B; ++b) {
-      if (steps_out) steps_out[b] = done[b] ? steps[b] : -1;
+      if (steps_out) steps_out[b] = done[b] == 1 ? steps[b] : -1;
       if (j_out) j_out[b] = J[b];
     }
     if (dmd_jumps) *dmd_jumps = jumps;
-    return s;
+    return st;
   };
   if (cudaMemcpyAsync(c->active, ones.data(), sizeof(int) * B, cudaMemcpyHostToDevice, c->user) != cudaSuccess)
     return finish(PCF_ECUDA);
-  int taken = 0, k = 0;
+  const size_t pbytes = sizeof(double) * (size_t)plen;
+  int taken = 0;
   while (taken < max_steps) {
     const int n = std::min(chunk, max_steps - taken);
-    st = descent_internal(c, u, dtau, n, hist, tol);
-    if (st != PCF_OK) return finish(st);
-    if (dmd) {
-      st = pcf_snapshot(c, u, ring + (size_t)k * B * plen);
+    for (int o = 0; o < n; o += sub) {
+      const pcf_status st = descent_internal(c, u, dtau, std::min(sub, n - o), hist + (size_t)o * B, tol);
       if (st != PCF_OK) return finish(st);
     }
     if (cudaMemcpyAsync(hh.data(), hist, sizeof(double) * (size_t)n * B, cudaMemcpyDeviceToHost, c->user) !=
@@ -1235,23 +1293,65 @@ pcf_status pcf_run(pcf_ctx* c, double* u, double dtau, int max_steps, double tol
     }
     taken += n;
     if (!alive) break;
-    ++k;
-    if (dmd && k == dmd_snapshots) {
-      k = 0;
-      for (int b = 0; b < B; ++b) {
-        if (done[b]) continue;
-        int r = 0;
-        double jr = 0;
-        const pcf_status sd = pcf_dmd_extrapolate(c, ring + (size_t)b * plen, (long long)B * plen, dmd_snapshots - 1,
-                                                  rank_tol, u + 2 * (size_t)c->state_off[b], &r, &jr);
-        if (sd == PCF_OK) ++jumps;
-        else if (sd != PCF_ENAN) return finish(sd);
+    if (!dmd) continue;
+    bool snap = false;
+    for (int b = 0; b < B; ++b) snap = snap || (!done[b] && phase[b] != GAP);
+    if (snap) {
+      const pcf_status st = pcf_snapshot(c, u, tmp);
+      if (st != PCF_OK) return finish(st);
+    }
+    for (int b = 0; b < B; ++b) {
+      if (done[b]) continue;
+      if (phase[b] == GAP) {
+        if (--wait[b] <= 0) phase[b] = COLLECT;
+        continue;
       }
+      // snapshot of instance b into its ring slot (a sliding window before the first jump)
+      double* slot = ring + ((size_t)next[b] * B + b) * plen;
+      if (cudaMemcpyAsync(slot, tmp + (size_t)b * plen, pbytes, cudaMemcpyDeviceToDevice, c->user) != cudaSuccess)
+        return finish(PCF_ECUDA);
+      next[b] = (next[b] + 1) % S;
+      filled[b] = std::min(filled[b] + 1, S);
+      if (filled[b] < S || (phase[b] == FIRST && !(J[b] < sc->j_start))) continue;
+      // the window in time order (oldest at slot next[b])
+      for (int k = 0; k < S; ++k)
+        if (cudaMemcpyAsync(ordered + (size_t)k * plen, ring + ((size_t)((next[b] + k) % S) * B + b) * plen, pbytes,
+                            cudaMemcpyDeviceToDevice, c->user) != cudaSuccess)
+          return finish(PCF_ECUDA);
+      int r = 0;
+      double jr = 0;
+      const pcf_status sd =
+          pcf_dmd_extrapolate(c, ordered, plen, S - 1, sc->rank_tol, u + 2 * (size_t)c->state_off[b], &r, &jr);
+      if (sd == PCF_OK) ++jumps;
+      else if (sd != PCF_ENAN) return finish(sd);
+      filled[b] = 0;
+      next[b] = 0;
+      phase[b] = gap_chunks > 0 ? GAP : COLLECT;
+      wait[b] = gap_chunks;
     }
   }
   for (int b = 0; b < B; ++b)
     if (done[b] == 2) return finish(PCF_ENAN);
   return finish(PCF_OK);
+}
+
+pcf_status pcf_run(pcf_ctx* c, double* u, double dtau, int max_steps, double tol, int dmd_period, int dmd_snapshots,
+                   double rank_tol, int* steps_out, double* j_out, int* dmd_jumps) {
+  if (dmd_period < 0) return PCF_EINVAL;
+  if (dmd_period == 0) return run_schedule(c, u, dtau, max_steps, tol, nullptr, steps_out, j_out, dmd_jumps);
+  if (dmd_snapshots < 3 || dmd_period % dmd_snapshots) return PCF_EINVAL;
+  pcf_dmd_schedule sc;
+  sc.snapshots = dmd_snapshots;
+  sc.spacing = dmd_period / dmd_snapshots;
+  sc.gap = 0;
+  sc.j_start = INFINITY;
+  sc.rank_tol = rank_tol;
+  return run_schedule(c, u, dtau, max_steps, tol, &sc, steps_out, j_out, dmd_jumps);
+}
+
+pcf_status pcf_run_schedule(pcf_ctx* c, double* u, double dtau, int max_steps, double tol,
+                            const pcf_dmd_schedule* schedule, int* steps_out, double* j_out, int* dmd_jumps) {
+  return run_schedule(c, u, dtau, max_steps, tol, schedule, steps_out, j_out, dmd_jumps);
 }
 
 pcf_status pcf_descent_step_host(pcf_ctx* c, double* u_host, double dtau, int nsteps, double* hist_host) {
@@ -1293,7 +1393,99 @@ pcf_status pcf_kernel_times(pcf_ctx* c, double* ms, long long* launches, int n) 
   return PCF_OK;
 }
 
-int pcf_launches_per_step(pcf_ctx* c) { return c ? (c->split ? (c->fused ? 7 : 11) : c->mixed ? 10 : 6) : 0; }
+int pcf_launches_per_step(pcf_ctx* c) {
+  if (!c) return 0;
+  const int base = c->split ? (c->fused ? 7 : 11) : c->mixed ? 10 : 6;
+  // symmetric subspace: the projection, plus a separate synthesis where the update kernel
+  // synthesises the state itself (fused and single per-mode kernels)
+  return base + (c->any_sym ? ((c->split && !c->fused) || c->mixed ? 1 : 2) : 0);
+}
+
+pcf_status pcf_norm(pcf_ctx* c, const double* u, double* out) {
+  if (!c || !u || !out) return PCF_EINVAL;
+  set_pointers(c, u, nullptr, nullptr);
+  PCF_TRY(enter(c));
+  PCF_TRY(push_descriptors(c));
+  PCF_TRY(launch_ysynth(c, 0));
+  PCF_TRY(launch_synth(c, 0, 3));
+  launch_norm_planes(c->plane_kind, c->cta_synth3, c->cs, li_of(c, c->pre_synth3), 0);
+  k_norm_final<<<1, 32, 0, c->cs>>>(li_of(c, c->pre_inst), out);
+  PCF_TRY(check_launch());
+  return leave(c);
+}
+
+pcf_status pcf_symmetrize(pcf_ctx* c, double* u, int mask) {
+  if (!c || !u || mask < 0 || mask > 3) return PCF_EINVAL;
+  if (mask == 0) return PCF_OK;
+  set_pointers(c, u, nullptr, nullptr);
+  PCF_TRY(enter(c));
+  PCF_TRY(push_descriptors(c));
+  PCF_TRY(launch_sym(c, mask));
+  PCF_TRY(check_launch());
+  return leave(c);
+}
+
+pcf_status pcf_dns(pcf_ctx* c, double* u, int nsteps, double* hist, double* guesses, int max_guesses,
+                   int* n_guesses) {
+  if (!c || !u || nsteps < 0 || max_guesses < 0 || (max_guesses > 0 && !guesses)) return PCF_EINVAL;
+  const int B = c->B;
+  if (!c->d_dns) {
+    if (ctx_alloc(c, &c->d_dns, (size_t)B) || ctx_alloc(c, &c->uprev, (size_t)c->total_state) ||
+        ctx_alloc(c, &c->dns_count, (size_t)B))
+      return PCF_ENOMEM;
+  }
+  set_pointers(c, u, (const double*)c->r_int, nullptr);
+  int* count = n_guesses ? n_guesses : c->dns_count;
+  std::vector<DnsInst> hd(B);
+  for (int b = 0; b < B; ++b) {
+    DnsInst& D = hd[b];
+    D.hist = hist ? hist + b : nullptr;
+    D.hist_stride = B;
+    D.uprev = c->uprev + c->state_off[b];
+    D.guess = guesses ? (double2*)guesses + c->state_off[b] : nullptr;
+    D.gstride = c->total_state;
+    D.gmax = max_guesses;
+    D.count = count + b;
+    D.step = 0;
+    D.slot = -1;
+    D.h1 = D.h2 = 0.0;
+  }
+  PCF_TRY(enter(c));
+  PCF_TRY(push_descriptors(c));
+  PCF_CUDA(cudaMemcpyAsync(c->d_dns, hd.data(), sizeof(DnsInst) * B, cudaMemcpyHostToDevice, c->cs));
+  PCF_CUDA(cudaMemsetAsync(count, 0, sizeof(int) * B, c->cs));
+  if (nsteps == 0) return leave(c);
+  if (c->any_sym) PCF_TRY(launch_sym(c, -1));
+  PCF_TRY(launch_ysynth(c, 0));
+  if (c->timing) {
+    for (int s = 0; s < nsteps; ++s) PCF_TRY(dns_body(c));
+    PCF_TRY(check_launch());
+    return leave(c);
+  }
+  // graphs of up to 64 steps (the step counter lives on the device, so one graph serves
+  // every chunk)
+  const int chunk = 64;
+  for (int done = 0; done < nsteps;) {
+    const int n = std::min(chunk, nsteps - done);
+    auto it = c->dns_graphs.find(n);
+    if (it == c->dns_graphs.end()) {
+      cudaGraph_t g;
+      PCF_CUDA(cudaStreamBeginCapture(c->cs, cudaStreamCaptureModeThreadLocal));
+      pcf_status st = PCF_OK;
+      for (int s = 0; s < n && st == PCF_OK; ++s) st = dns_body(c);
+      cudaError_t e = cudaStreamEndCapture(c->cs, &g);
+      if (st != PCF_OK) return st;
+      PCF_CUDA(e);
+      cudaGraphExec_t ex;
+      PCF_CUDA(cudaGraphInstantiate(&ex, g, 0));
+      cudaGraphDestroy(g);
+      it = c->dns_graphs.emplace(n, ex).first;
+    }
+    PCF_CUDA(cudaGraphLaunch(it->second, c->cs));
+    done += n;
+  }
+  return leave(c);
+}
 
 pcf_status pcf_probe_fp64_peak(void* stream, double* gflops) {
   if (!gflops) return PCF_EINVAL;

@@ -459,15 +459,16 @@ __global__ void __launch_bounds__(128) k_prod_t(LaunchInfo li) {
   }
 }
 
-// CTA = (instance, plane j, component c): sum over the plane of q_c^2 (slot 1, field c).
+// CTA = (instance, plane j, component c): sum over the plane of the squared velocity
+// component c of a slot (0: u, 1: q).
 template <class T>
-__global__ void __launch_bounds__(128) k_norm_planes_t(LaunchInfo li) {
+__global__ void __launch_bounds__(128) k_norm_planes_t(LaunchInfo li, int slot) {
   __shared__ double red[32];
   int local;
   const int b = find_inst(li, blockIdx.x, &local);
   const Inst& I = li.insts[b];
   const int c = local % 3, j = local / 3;
-  const T* q = fplane<T>(I, 1, c, j);
+  const T* q = fplane<T>(I, slot, c, j);
   typename Acc<T>::type sa = 0.0;
   for (int t = threadIdx.x; t < I.nx * I.nz; t += blockDim.x) acc_sq(&sa, q[t]);
   double sq = acc_value(sa);
@@ -500,10 +501,10 @@ void launch_prod(int kind, bool adj, int ctas, size_t smem, cudaStream_t s, Laun
     else k_prod_t<double, false><<<ctas, 128, smem, s>>>(li);
   }
 }
-void launch_norm_planes(int kind, int ctas, cudaStream_t s, LaunchInfo li) {
-  if (kind == 1) k_norm_planes_t<float><<<ctas, 128, 0, s>>>(li);
-  else if (kind == 2) k_norm_planes_t<ff><<<ctas, 128, 0, s>>>(li);
-  else k_norm_planes_t<double><<<ctas, 128, 0, s>>>(li);
+void launch_norm_planes(int kind, int ctas, cudaStream_t s, LaunchInfo li, int slot) {
+  if (kind == 1) k_norm_planes_t<float><<<ctas, 128, 0, s>>>(li, slot);
+  else if (kind == 2) k_norm_planes_t<ff><<<ctas, 128, 0, s>>>(li, slot);
+  else k_norm_planes_t<double><<<ctas, 128, 0, s>>>(li, slot);
 }
 template <class T>
 static cudaError_t set_plane_smem_t(size_t synth, size_t prod) {

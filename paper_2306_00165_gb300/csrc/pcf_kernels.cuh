@@ -39,6 +39,19 @@ __device__ __forceinline__ int find_inst(const LaunchInfo& li, int cta, int* loc
 
 __device__ __forceinline__ bool inst_active(const Inst& I) { return I.active == nullptr || *I.active != 0; }
 
+// Per-instance state of the DNS that produces guesses (pcf_dns), on the device.
+struct DnsInst {
+  double* hist;        // ||u_s|| history base (may be null), stride hist_stride
+  int hist_stride;
+  double2* uprev;      // the state before the current update
+  double2* guess;      // guess base (may be null); guess k at guess + k * gstride
+  long long gstride;
+  int gmax;
+  int* count;          // extrema found so far
+  int step, slot;      // steps taken in this call; guess slot of this step's capture (-1: none)
+  double h1, h2;       // ||u|| of the previous two steps
+};
+
 // J = sqrt(0.5 * sum_j w_j * mean_{x,z} |q|^2) from the plane sums (fixed order).
 __device__ __forceinline__ double norm_from_parts(const Inst& I) {
   double s = 0.0;
@@ -52,7 +65,7 @@ __device__ __forceinline__ double norm_from_parts(const Inst& I) {
 // kind: plane arithmetic, 0 FP64, 1 FP32 (mixed form), 2 float-float
 void launch_xzsynth(int kind, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int slot, int nf);
 void launch_prod(int kind, bool adj, int ctas, size_t smem, cudaStream_t s, LaunchInfo li);
-void launch_norm_planes(int kind, int ctas, cudaStream_t s, LaunchInfo li);
+void launch_norm_planes(int kind, int ctas, cudaStream_t s, LaunchInfo li, int slot);
 cudaError_t set_plane_smem(int kind, size_t synth, size_t prod);
 __global__ void k_mode(LaunchInfo li, int op, int sig, int mpc, int step_index);
 __global__ void k_norm_final(LaunchInfo li, double* out);
@@ -95,5 +108,13 @@ cudaError_t set_split_smem(size_t analysis, size_t solve, size_t synth);
 size_t smem_ystep(int N, int G);
 void launch_ystep(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op);
 cudaError_t set_ystep_smem(size_t smem);
+
+// Symmetric-subspace projection and the DNS helpers (pcf_sym_dns.cu).
+int symmetrize_ctas(const Inst& I);
+void launch_symmetrize(int ctas_x, int ninst, cudaStream_t s, const Inst* insts, int mask_override);
+int dns_ctas(const Inst& I);
+void launch_dns_norm(int ninst, cudaStream_t s, const Inst* insts, DnsInst* dns);
+void launch_dns_capture(int ctas_x, int ninst, cudaStream_t s, const Inst* insts, const DnsInst* dns);
+void launch_dns_update(int ctas_x, int ninst, cudaStream_t s, const Inst* insts, const DnsInst* dns);
 
 }  // namespace pcf

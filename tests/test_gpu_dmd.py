@@ -130,3 +130,38 @@ def test_run_with_dmd_period_matches_oracle(pcf):
     u = o.from_psi(psi_ref)
     u, _ = o.run(u, 0.01, 5)
     assert _rel(ud.cpu().numpy()[0], u) <= 1e-6
+
+
+def test_run_schedule_matches_oracle(pcf):
+    """§6.2's schedule with a threshold and a gap: a sliding window of 6 snapshots every 5
+    steps, the first jump once J falls below j_start (between the J of steps 39 and 44, so at
+    step 45), 10 steps of gap, then a fresh collection and a second jump at step 85."""
+    grid = (16, 17, 16)
+    o = PCFOracle(*grid)
+    u0 = gi.random_perturbation(*grid, 0.1, 7)
+    _, h = o.run(u0, 0.01, 45)
+    j_start = 0.5 * (h[39] + h[44])
+    cost = lambda p: o.residual(o.from_psi(p))[1]
+    ref, conv, Jref, jumps_ref = dmd.run_schedule(u0, lambda u, n: o.run(u, 0.01, n), o.to_psi, o.from_psi, cost,
+                                                  100, 1e-30, 6, 5, 10, j_start, 1e-8)
+    assert jumps_ref == [45, 85] and conv == -1
+    s = pcf.Solver(*grid, batch=1)
+    ud = torch.from_numpy(u0[None].copy()).cuda()
+    steps, J, jumps = s.run_schedule(ud, 0.01, 100, tol=1e-30, snapshots=6, spacing=5, gap=10, j_start=j_start,
+                                     rank_tol=1e-8)
+    assert jumps == 2 and steps == [-1]
+    assert _rel(ud.cpu().numpy()[0], ref) <= 1e-6
+    assert abs(J[0] - Jref) <= 1e-6 * Jref
+
+
+def test_run_schedule_without_dmd_and_bad_schedules(pcf):
+    grid = (16, 17, 16)
+    s = pcf.Solver(*grid, batch=2)
+    u = torch.from_numpy(gi.batch(gi.random_perturbation, range(2), *grid)).cuda()
+    u2 = u.clone()
+    steps, J, jumps = s.run_schedule(u, 0.01, 30, tol=1e-30, dmd=False)
+    s.descent_step(u2, 0.01, 30)
+    assert jumps == 0 and torch.equal(u, u2)
+    for bad in (dict(snapshots=2), dict(spacing=0), dict(gap=-1), dict(j_start=float("nan")), dict(rank_tol=0.0)):
+        with pytest.raises(pcf.PCFError):
+            s.run_schedule(u, 0.01, 10, **bad)

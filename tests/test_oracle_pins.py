@@ -569,3 +569,54 @@ def test_extrema_brute_force():
     h = [3.0, 2.0, 1.0, 2.0, 3.0, 2.0, 2.0, 1.0, 1.5]
     assert PCFOracle.extrema(h) == [2, 4, 7]
     assert PCFOracle.extrema([1.0, 2.0]) == []
+
+
+# ------------------------------------------------------------------ DMD schedule (§6.2)
+def _affine_system(n=60, mu=0.97, seed=3):
+    """psi_{t+1} = psi* + mu (psi_t - psi*), cost ||psi - psi*||: J_t = J_0 mu^t exactly, and
+    DMD of any window recovers psi* (one decaying mode plus the steady one)."""
+    rng = np.random.default_rng(seed)
+    star = rng.standard_normal(n)
+    d0 = rng.standard_normal(n)
+    cost = lambda p: float(np.linalg.norm(p - star))
+
+    def step(u, k):
+        hist = []
+        for _ in range(k):
+            hist.append(cost(u))
+            u = star + mu * (u - star)
+        return u, hist
+    return star + d0, star, step, cost, mu
+
+
+def test_dmd_schedule_jump_times_closed_form():
+    """J_t = J_0 mu^t: the first jump is at the first chunk end t = c spacing with a full window
+    (c >= snapshots) and J_{t-1} < j_start; it lands on psi*, so the run converges right
+    after it.  With a threshold never met there is no jump."""
+    u0, star, step, cost, mu = _affine_system()
+    J0 = cost(u0)
+    snapshots, spacing, j_start = 5, 7, 0.3 * J0
+    ident = lambda p: p
+    u, conv, J, jumps = dmd.run_schedule(u0, step, ident, ident, cost, 400, 1e-9, snapshots, spacing, 50,
+                                         j_start, 1e-12)
+    c = snapshots
+    while J0 * mu ** (c * spacing - 1) >= j_start:
+        c += 1
+    assert jumps == [c * spacing]
+    assert conv == c * spacing and J < 1e-9
+    u, conv, J, jumps = dmd.run_schedule(u0, step, ident, ident, cost, 300, 1e-30, snapshots, spacing, 50,
+                                         1e-30, 1e-12)
+    assert jumps == [] and conv == -1 and abs(J - J0 * mu ** 299) < 1e-12 * J0
+
+
+def test_dmd_schedule_gap_and_fixed_period():
+    """A cost that never converges (tol below rounding): jumps every snapshots * spacing steps
+    with no threshold and no gap (the fixed-period schedule), and every
+    gap + snapshots * spacing steps after the first with a gap (rounded up to whole chunks)."""
+    u0, star, step, cost, mu = _affine_system()
+    ident = lambda p: p
+    jitter = lambda p: p + 1e-3   # keeps the jump off psi*, so the descent goes on
+    _, _, _, jumps = dmd.run_schedule(u0, step, ident, jitter, cost, 200, 1e-300, 4, 10, 0, np.inf, 1e-12)
+    assert jumps == [40, 80, 120, 160, 200]
+    _, _, _, jumps = dmd.run_schedule(u0, step, ident, jitter, cost, 300, 1e-300, 4, 10, 25, np.inf, 1e-12)
+    assert jumps == [40, 40 + 30 + 40, 40 + 2 * 70, 40 + 3 * 70]
