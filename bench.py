@@ -81,41 +81,59 @@ def kernel_flops(grid, batch, split=True):
 
 
 class Clocks:
-    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    """Samples nvidia-smi clocks and throttle reasons every 20 ms; each sample is stamped when
+    it arrives, and only the samples taken inside the timed region (begin() .. end()) count."""
 
     def __init__(self):
         self.proc = None
-        self.path = None
+        self.rows = []
+        self.t0 = self.t1 = None
 
     def start(self):
-        fd, self.path = tempfile.mkstemp(suffix=".csv")
-        os.close(fd)
+        import threading
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return
+        first = threading.Event()
+
+        def read():
+            for line in self.proc.stdout:
+                self.rows.append((time.perf_counter(), line))
+                first.set()
+        threading.Thread(target=read, daemon=True).start()
+        first.wait(timeout=10.0)
+
+    def begin(self):
+        self.t0 = time.perf_counter()
+
+    def end(self):
+        self.t1 = time.perf_counter()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.05)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         rows = []
-        for line in open(self.path):
+        for t, line in list(self.rows):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
+            # a sample arrives within one interval of being taken
+            if len(parts) >= 9 and self.t0 is not None and self.t0 <= t <= self.t1 + 0.02:
                 rows.append(parts)
-        os.unlink(self.path)
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
 
         def num(x):
             try:
@@ -406,10 +424,11 @@ def run_ours(args):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = Clocks()
+    clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.begin()
     t_wall = time.perf_counter()
     hist = []
     for k in range(args.steps):
@@ -420,6 +439,7 @@ def run_ours(args):
         hist.append(H)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
+    clocks.end()
     if dist:
         dist.barrier()
     ck = clocks.stop()
