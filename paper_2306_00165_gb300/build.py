@@ -34,8 +34,12 @@ def _stale(obj, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False, extra_flags=()):
-    os.makedirs(OUT, exist_ok=True)
+def build(force=False, verbose=False, extra_flags=(), out=None):
+    """Compile every translation unit and link libpcfadj.so; returns its path.  ``out``: a
+    build folder other than the in-tree default (e.g. for a build with other flags)."""
+    OUT_ = out or OUT
+    LIB_ = os.path.join(OUT_, "libpcfadj.so")
+    os.makedirs(OUT_, exist_ok=True)
     nvcc = _nvcc()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(HERE, "..", "include", "pcfadj.h"))
@@ -43,7 +47,7 @@ def build(force=False, verbose=False, extra_flags=()):
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OUT, src.replace(".cu", ".o"))
+        o = os.path.join(OUT_, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
             jobs.append([nvcc, *ARCH, *FLAGS, *extra_flags, "-I", os.path.join(HERE, "..", "include"),
@@ -61,9 +65,9 @@ def build(force=False, verbose=False, extra_flags=()):
         for out in ex.map(run, jobs):
             if verbose and out.strip():
                 print(out)
-    if force or jobs or not os.path.exists(LIB):
-        run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs])
-    return LIB
+    if force or jobs or not os.path.exists(LIB_):
+        run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", LIB_, *objs])
+    return LIB_
 
 
 if __name__ == "__main__":

@@ -41,6 +41,10 @@ struct pcf_ctx {
   int* pre_yy = nullptr;
   int cta_ya = 0, cta_ys = 0, cta_yy = 0;
   int grid_ys = 0, buf_ys = 0, rows_ys = 0;  // persistent solve: CTAs, stage buffer, scratch rows
+  // the solve's own instance groups (its right-hand sides are per instance, so its grouping
+  // is independent of the analysis and synthesis kernels'); tuned separately
+  int sgrp_s = 0, ngroups_s = 0;
+  int2* d_groups_s = nullptr;
   bool fused = false;           // the step runs the fused per-mode kernel (k_ystep)
   int* pre_yf = nullptr;        // its CTA prefix over groups [B + 1]
   int cta_yf = 0;

@@ -424,13 +424,15 @@ pcf_status launch_tc_analysis(pcf_ctx* c) {
 }
 // split mode kernels of the FP64 descent step
 GroupLaunch gl_of(pcf_ctx* c, const int* pre) { return GroupLaunch{c->dinst, pre, c->d_groups, c->ngroups}; }
-pcf_status launch_split_analysis(pcf_ctx* c, int op) {
-  return timed(c, 7,
-               [&] { launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), op, c->plane_kind == 2, c->smt); });
+pcf_status launch_split_analysis(pcf_ctx* c, int op, int step_index = -1) {
+  return timed(c, 7, [&] {
+    launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), op, c->plane_kind == 2, c->smt, step_index);
+  });
 }
+GroupLaunch gl_solve(pcf_ctx* c) { return GroupLaunch{c->dinst, c->pre_ys, c->d_groups_s, c->ngroups_s}; }
 pcf_status launch_split_solve(pcf_ctx* c, int op) {
   return timed(c, op == MODE_PHI ? 3 : 6, [&] {
-    launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_of(c, c->pre_ys), op);
+    launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_solve(c), op);
   });
 }
 pcf_status launch_fused_step(pcf_ctx* c, int op) {
@@ -531,8 +533,7 @@ pcf_status step_body(pcf_ctx* c, int s) {
     PCF_TRY(launch_split_synth(c, 1, 1));
     PCF_TRY(launch_synth(c, 1, kFieldsSynth));
     PCF_TRY(launch_prodN(c));
-    PCF_TRY(launch_split_jnorm(c, s));
-    PCF_TRY(launch_split_analysis(c, MODE_PSI_UPDATE));
+    PCF_TRY(launch_split_analysis(c, MODE_PSI_UPDATE, s));  // with J, history and mask
     PCF_TRY(launch_split_solve(c, MODE_PSI_UPDATE));
     if (c->any_sym) PCF_TRY(launch_sym(c, -1));
     PCF_TRY(launch_split_synth(c, 0, 1));
@@ -734,11 +735,8 @@ static pcf_status set_mode_tiles(pcf_ctx* c, int want) {
 
 // Instance groups of the split mode kernels: runs of consecutive instances on the same grid,
 // at most G per group, and the derived launch geometry.
-static pcf_status set_split_groups(pcf_ctx* c, int G, int mt = 1) {
-  int Nmax = 0;
-  for (const Inst& I : c->hinst) Nmax = std::max(Nmax, I.N);
-  G = std::max(1, std::min(G, split_max_group(Nmax)));
-  while (G > 1 && smem_ysolve(Nmax, G) > 227 * 1024) --G;
+// Consecutive instances that share grid and tables, at most G per group.
+static std::vector<int2> make_groups(const pcf_ctx* c, int G) {
   std::vector<int2> groups;
   for (int b = 0; b < c->B; ++b) {
     const Inst& I = c->hinst[b];
@@ -749,29 +747,70 @@ static pcf_status set_split_groups(pcf_ctx* c, int G, int mt = 1) {
     }
     if (fresh) groups.push_back(make_int2(b, 1)); else groups.back().y += 1;
   }
+  return groups;
+}
+
+// Instance groups of the persistent Stokes solve (at most G instances each): items, prefix,
+// shared-memory layout and grid.
+static pcf_status set_solve_groups(pcf_ctx* c, int G) {
+  int Nmax = 0;
+  for (const Inst& I : c->hinst) Nmax = std::max(Nmax, I.N);
+  G = std::max(1, std::min(G, split_max_group(Nmax)));
+  while (G > 1 && smem_ysolve(Nmax, G) > 227 * 1024) --G;
+  const std::vector<int2> groups = make_groups(c, G);
+  const int ng = (int)groups.size();
+  int gmax = 1;
+  for (const int2& gq : groups) gmax = std::max(gmax, gq.y);
+  std::vector<int> ps(ng + 1, 0);
+  for (int q = 0; q < ng; ++q) ps[q + 1] = ps[q] + split_ctas_per_group(1, c->hinst[groups[q].x].nmodes, 1);
+  // the persistent solve lays out every item in buffers sized for the largest grid and group
+  const size_t ss = smem_ysolve(Nmax, gmax);
+  if (ss > 227 * 1024) return PCF_ENOTSUP;
+  if (!c->d_groups_s) {
+    if (ctx_alloc(c, &c->d_groups_s, (size_t)c->B) || ctx_alloc(c, &c->pre_ys, (size_t)c->B + 1)) return PCF_ENOMEM;
+  }
+  PCF_CUDA(cudaMemcpy(c->d_groups_s, groups.data(), sizeof(int2) * ng, cudaMemcpyHostToDevice));
+  PCF_CUDA(cudaMemcpy(c->pre_ys, ps.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
+  c->sgrp_s = G;
+  c->ngroups_s = ng;
+  c->cta_ys = ps[ng];
+  c->sm_ys = ss;
+  c->buf_ys = (int)ysolve_buffer(Nmax, gmax);
+  c->rows_ys = Nmax / 2 + 1;
+  PCF_CUDA(set_split_smem(c->sm_ya, ss, c->sm_yy));
+  int dev = 0, nsm = 0;
+  PCF_CUDA(cudaGetDevice(&dev));
+  PCF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int per_sm = std::max(1, ysolve_ctas_per_sm(ss));
+  c->grid_ys = std::min(c->cta_ys, nsm * per_sm);
+  return PCF_OK;
+}
+
+static pcf_status set_split_groups(pcf_ctx* c, int G, int mt = 1) {
+  int Nmax = 0;
+  for (const Inst& I : c->hinst) Nmax = std::max(Nmax, I.N);
+  G = std::max(1, std::min(G, split_max_group(Nmax)));
+  while (G > 1 && smem_ysolve(Nmax, G) > 227 * 1024) --G;
+  std::vector<int2> groups = make_groups(c, G);
   const int ng = (int)groups.size();
   int gmax = 1;
   for (const int2& gq : groups) gmax = std::max(gmax, gq.y);
   mt = std::max(1, mt);
   while (mt > 1 && split_col_pad(gmax) * mt > 32) mt >>= 1;
-  std::vector<int> pa(ng + 1, 0), ps(ng + 1, 0), py(ng + 1, 0), pf(ng + 1, 0);
+  std::vector<int> pa(ng + 1, 0), py(ng + 1, 0), pf(ng + 1, 0);
   size_t sa = 0, sy = 0;
   for (int q = 0; q < ng; ++q) {
     const Inst& I = c->hinst[groups[q].x];
     pf[q + 1] = pf[q] + I.nmodes;
     pa[q + 1] = pa[q] + split_ctas_per_group(0, I.nmodes, mt);
-    ps[q + 1] = ps[q] + split_ctas_per_group(1, I.nmodes, mt);
     py[q + 1] = py[q] + split_ctas_per_group(2, I.nmodes, mt);
     sa = std::max(sa, smem_yanalysis(I.N, groups[q].y, mt));
     sy = std::max(sy, smem_ysynth(I.N, groups[q].y, mt));
   }
-  // the persistent solve lays out every item in buffers sized for the largest grid and group
-  const size_t ss = smem_ysolve(Nmax, gmax);
-  if (std::max(sa, std::max(ss, sy)) > 227 * 1024) return PCF_ENOTSUP;
+  if (std::max(sa, sy) > 227 * 1024) return PCF_ENOTSUP;
   if (!c->d_groups) {
     if (ctx_alloc(c, &c->d_groups, (size_t)c->B) || ctx_alloc(c, &c->pre_ya, (size_t)c->B + 1) ||
-        ctx_alloc(c, &c->pre_ys, (size_t)c->B + 1) || ctx_alloc(c, &c->pre_yy, (size_t)c->B + 1) ||
-        ctx_alloc(c, &c->pre_yf, (size_t)c->B + 1))
+        ctx_alloc(c, &c->pre_yy, (size_t)c->B + 1) || ctx_alloc(c, &c->pre_yf, (size_t)c->B + 1))
       return PCF_ENOMEM;
   }
   PCF_CUDA(cudaMemcpy(c->pre_yf, pf.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
@@ -779,27 +818,17 @@ static pcf_status set_split_groups(pcf_ctx* c, int G, int mt = 1) {
   c->sm_yf = smem_ystep(Nmax, gmax);
   PCF_CUDA(cudaMemcpy(c->d_groups, groups.data(), sizeof(int2) * ng, cudaMemcpyHostToDevice));
   PCF_CUDA(cudaMemcpy(c->pre_ya, pa.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
-  PCF_CUDA(cudaMemcpy(c->pre_ys, ps.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
   PCF_CUDA(cudaMemcpy(c->pre_yy, py.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
   c->sgrp = G;
   c->smt = mt;
   c->ngroups = ng;
   c->cta_ya = pa[ng];
-  c->cta_ys = ps[ng];
   c->cta_yy = py[ng];
   c->sm_ya = sa;
-  c->sm_ys = ss;
   c->sm_yy = sy;
-  c->buf_ys = (int)ysolve_buffer(Nmax, gmax);
-  c->rows_ys = Nmax / 2 + 1;
-  PCF_CUDA(set_split_smem(sa, ss, sy));
   if (c->sm_yf <= 227 * 1024) PCF_CUDA(set_ystep_smem(c->sm_yf));
-  int dev = 0, nsm = 0;
-  PCF_CUDA(cudaGetDevice(&dev));
-  PCF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const int per_sm = std::max(1, ysolve_ctas_per_sm(ss));
-  c->grid_ys = std::min(c->cta_ys, nsm * per_sm);
-  return PCF_OK;
+  // the solve follows the same group size unless tuned on its own (autotune_split)
+  return set_solve_groups(c, G);
 }
 
 // Autotuner of the split mode kernels: time analysis + solve + synthesis of the NSE Stokes
@@ -828,8 +857,7 @@ static pcf_status autotune_split(pcf_ctx* c) {
             return;
           }
           launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), MODE_PHI, c->plane_kind == 2, c->smt);
-          launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_of(c, c->pre_ys),
-                        MODE_PHI);
+          launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_solve(c), MODE_PHI);
           launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), 1, 1, c->plane_kind == 2, c->smt);
         };
         seq();
@@ -848,11 +876,38 @@ static pcf_status autotune_split(pcf_ctx* c) {
       }
     }
   }
+  c->tuned_split_ms = best_ms / 3.0;
+  pcf_status st = set_split_groups(c, best, best_mt);
+  c->fused = st == PCF_OK && best_fused;
+  if (st == PCF_OK && !c->fused) {
+    // the solve alone over its own group sizes
+    int best_s = c->sgrp_s;
+    float best_s_ms = 1e30f;
+    last = 0;
+    for (int G0 : {1, 2, 4, 8}) {
+      const int G = std::min(G0, c->B);
+      if (G == last) continue;
+      last = G;
+      if (set_solve_groups(c, G) != PCF_OK || c->sgrp_s != G) continue;
+      auto seq = [&] {
+        launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_solve(c), MODE_PHI);
+      };
+      seq();
+      PCF_CUDA(cudaEventRecord(a, c->cs));
+      for (int r = 0; r < 5; ++r) seq();
+      PCF_CUDA(cudaEventRecord(b, c->cs));
+      PCF_CUDA(cudaEventSynchronize(b));
+      float ms = 0.f;
+      PCF_CUDA(cudaEventElapsedTime(&ms, a, b));
+      if (ms < best_s_ms) {
+        best_s_ms = ms;
+        best_s = G;
+      }
+    }
+    st = set_solve_groups(c, best_s);
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  c->tuned_split_ms = best_ms / 3.0;
-  const pcf_status st = set_split_groups(c, best, best_mt);
-  c->fused = st == PCF_OK && best_fused;
   return st;
 }
 
@@ -1395,7 +1450,7 @@ pcf_status pcf_kernel_times(pcf_ctx* c, double* ms, long long* launches, int n) 
 
 int pcf_launches_per_step(pcf_ctx* c) {
   if (!c) return 0;
-  const int base = c->split ? (c->fused ? 7 : 11) : c->mixed ? 10 : 6;
+  const int base = c->split ? (c->fused ? 7 : 10) : c->mixed ? 10 : 6;
   // symmetric subspace: the projection, plus a separate synthesis where the update kernel
   // synthesises the state itself (fused and single per-mode kernels)
   return base + (c->any_sym ? ((c->split && !c->fused) || c->mixed ? 1 : 2) : 0);

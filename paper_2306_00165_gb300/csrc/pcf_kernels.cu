@@ -258,8 +258,13 @@ size_t smem_prod(const Inst& I) { return smem_plane(I, sizeof(double2)); }
 __constant__ int c_src[kFieldsSynth] = {0, 1, 2, 0, 3, 0, 1, 1, 2, 4, 2};
 __constant__ int c_fac[kFieldsSynth] = {0, 0, 0, 1, 0, 2, 1, 2, 1, 0, 2};
 
+// Resident CTAs per SM the synthesis kernel is compiled for (register budget).
+#ifndef PCF_XZ_MINB
+#define PCF_XZ_MINB 8
+#endif
+
 template <class T>
-__global__ void __launch_bounds__(128) k_xzsynth_t(LaunchInfo li, int slot, int nfields) {
+__global__ void __launch_bounds__(128, PCF_XZ_MINB) k_xzsynth_t(LaunchInfo li, int slot, int nfields) {
   using C = typename Cx<T>::c;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
@@ -296,21 +301,24 @@ __global__ void __launch_bounds__(128) k_xzsynth_t(LaunchInfo li, int slot, int 
     const int nrc = min(pp.chunk, nr - r0);
     C* Z0 = Zb;
     C* Z1 = (pp.chunk == nr) ? G : Zb + pp.chunk * LZ;
+    // Row pair (x1, x2) -> one complex row whose inverse z transform gives row x1 in the
+    // real part and row x2 in the imaginary part: h_z = G_z[x1] + i G_z[x2] with
+    // G_{-p} = conj(G_p) (p = 0: real parts only; |p| > Kz: zero).  Written branch-free, so
+    // that a warp issues each multiply-add once for all its lanes: s = +-1 picks the
+    // conjugate, and the multiply-adds by +-1 and 0 are exact.
     for (int t = threadIdx.x; t < nrc * nz; t += blockDim.x) {
       const int r = t / nz, z = t - r * nz;
       const int x1 = 2 * (r0 + r), x2 = x1 + 1;
-      C h = Cx<T>::mk(0, 0);
-      if (z == 0) {
-        h = Cx<T>::mk(G[x1].x, G[x2].x);
-      } else if (z <= Kz) {
-        const C g1 = G[z * LX + x1], g2 = G[z * LX + x2];
-        h = Cx<T>::mk(g1.x - g2.y, g1.y + g2.x);
-      } else if (z >= nz - Kz) {
-        const int p = nz - z;
-        const C g1 = G[p * LX + x1], g2 = G[p * LX + x2];
-        h = Cx<T>::mk(g1.x + g2.y, g2.x - g1.y);
+      const bool lo = z <= Kz, hi = z >= nz - Kz;
+      const int p = lo ? z : nz - z;
+      C g1 = Cx<T>::mk(0, 0), g2 = g1;
+      if (lo || hi) {
+        g1 = G[p * LX + x1];
+        g2 = G[p * LX + x2];
       }
-      Z0[r * LZ + z] = h;
+      if (z == 0) g1.y = g2.y = T(0.0);
+      const T s = lo ? T(1.0) : T(-1.0);
+      Z0[r * LZ + z] = Cx<T>::mk(fma(-s, g2.y, g1.x), fma(s, g1.y, g2.x));
     }
     __syncthreads();
     C* Rz = fft_run<C>(Z0, Z1, nz, LZ, nrc, I.rz, I.nrz, twz, true);
@@ -386,8 +394,10 @@ __device__ __forceinline__ void product_rows(const Inst& I, const T* const* U, c
 // CTA = (instance, plane j, component c): product component c on the plane (M(u) or
 // N(q) with W = u_b + u = (U(y) + u, v, w)), forward FFT in z then x, 2/3 truncation.  ADJ also sums
 // q_c^2 over the plane (in FP64) for J.
+// Register budgets: eight resident CTAs per SM for M(u); six for N(q), which holds both
+// fields' plane pointers (at 8 x 32x33x32 its 792 CTAs then fit one wave of 152 SMs).
 template <class T, bool ADJ>
-__global__ void __launch_bounds__(128) k_prod_t(LaunchInfo li) {
+__global__ void __launch_bounds__(128, ADJ ? 6 : 8) k_prod_t(LaunchInfo li) {
   using C = typename Cx<T>::c;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);

@@ -96,7 +96,10 @@ size_t smem_ysolve(int N, int G);
 size_t smem_ysynth(int N, int G, int mt);
 // ff_arith: the Chebyshev dot products in float-float arithmetic (float-float form)
 // mt: consecutive modes per CTA of the analysis and synthesis kernels (col_pad(G) mt <= 32)
-void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith, int mt);
+// step_index >= 0: the dummy-dynamics analysis also computes J, its history entry and the
+// convergence mask (in place of launch_jnorm)
+void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith, int mt,
+                      int step_index = -1);
 void launch_ysolve(int ctas, int nitems, int bufsz, int scr_rows, size_t smem, cudaStream_t s, GroupLaunch gl,
                    int op);
 void launch_jnorm(int ninst, cudaStream_t s, const Inst* insts, int step_index);

@@ -104,9 +104,42 @@ __device__ __forceinline__ void group_flags(const GroupLaunch& gl, int first, in
   if (threadIdx.x < nI) live[threadIdx.x] = inst_active(gl.insts[first + threadIdx.x]) ? 1 : 0;
 }
 
+// J = ||r1|| from the plane sums of the adjoint product kernel, in the order of
+// norm_from_parts (one fma chain over j), so every kernel that computes it gets the same bits.
+__device__ __forceinline__ double jnorm_of(const Inst& I) {
+  const int ny = I.ny;
+  const double* P = I.normpart;
+  double s = 0.0;
+  for (int j = 0; j < ny; ++j) s = fma(I.ccw[j], P[j] + P[ny + j] + P[2 * ny + j], s);
+  return sqrt(0.5 * I.inv_nxnz * s);
+}
+
+// Live flags of the dummy-dynamics half-step with the norm folded in: every CTA of the group
+// computes J of its active instances (J < tol: the instance stops before this step's
+// update); the group's first CTA (lead) writes the history entry and clears the mask.  A CTA
+// that reads a mask the lead is clearing decides the same from its own J.
+__device__ __forceinline__ void group_flags_jnorm(const GroupLaunch& gl, int first, int nI, int* live, bool lead,
+                                                  int step_index) {
+  if (threadIdx.x < nI) {
+    const Inst& I = gl.insts[first + threadIdx.x];
+    int lv = inst_active(I) ? 1 : 0;
+    if (lv) {
+      const double J = jnorm_of(I);
+      if (lead && I.hist) I.hist[(size_t)step_index * I.hist_stride] = J;
+      if (I.tol > 0.0 && J < I.tol) {
+        lv = 0;
+        if (lead && I.active) *I.active = 0;
+      }
+    }
+    live[threadIdx.x] = lv;
+  }
+}
+
 // A: arithmetic of the Chebyshev dot products (double, or ff in the float-float form)
 template <class A>
-__global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int op, int mt) {
+// step_index >= 0 (dummy-dynamics half-step only): J, its history entry and the convergence
+// mask are computed here (group_flags_jnorm) instead of in k_jnorm.
+__global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int op, int mt, int step_index) {
   extern __shared__ double sm[];
   __shared__ int live[kMaxGroup];
   int local;
@@ -122,7 +155,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int
   A* Ao = Ae + H * H;                // [H][H] (rows < H-1 used)
   A* VP = Ao + H * H;                // [H][XS]    P_j = V_j + V_{N-j} (j < N/2), V_{N/2}
   A* VQ = VP + H * XS;               // [half][XS] Q_j = V_j - V_{N-j}
-  group_flags(gl, first, nI, live);
+  if (step_index >= 0) group_flags_jnorm(gl, first, nI, live, local == 0, step_index);
+  else group_flags(gl, first, nI, live);
   for (int t = threadIdx.x; t < 2 * H * H; t += blockDim.x) Ae[t] = cheb_at<A>(I0, CL.Ae() + t);
   for (int t = threadIdx.x; t < H * SPt / 2; t += blockDim.x) {
     const int pr = t % (SPt / 2), j = t / (SPt / 2), mm = pr / (SP / 2), i = pr - mm * (SP / 2);
@@ -316,103 +350,66 @@ __global__ void __launch_bounds__(kSolveThreads) k_ysolve(GroupLaunch gl, int op
       GG[j * XS + s] = gg;
       HH[j * XS + s] = hh;
     }
-    // outputs of this thread (assembly below): v rows, then u rows, then w rows per instance;
-    // their state values are loaded now and used after the products
     const int nV = mean ? (N - g) / 2 + 1 : McV;
     const int nU = mean ? nV : McP;
     const int nout = nV + 2 * nU;
-    constexpr int kOut = 4;  // outputs per thread (nI * nout <= kOut * kSolveThreads)
-    double2 sa[kOut], sb[kOut];
-#pragma unroll
-    for (int q = 0; q < kOut; ++q) {
-      const int t = threadIdx.x + q * kSolveThreads;
-      sa[q] = sb[q] = make_double2(0.0, 0.0);
-      if (t >= nI * nout) continue;
-      const int i = t / nout, kk = t - i * nout;
-      if (!live[i]) continue;
-      const int comp = kk < nV ? 1 : (kk < nV + nU ? 0 : 2);
-      const int row = kk < nV ? kk : kk - nV - (kk < nV + nU ? 0 : nU);
-      const int n = (kk < nV ? (mean ? g : pv) : (mean ? g : pP)) + 2 * row;
-      const Inst& I = gl.insts[first + i];
-      const size_t gidx = ((size_t)comp * nm + m) * ny + n;
-      sa[q] = op == MODE_PHI ? I.uhat[gidx] : I.rhat[gidx];
-      if (op != MODE_PHI) sb[q] = I.uhat[gidx];
-    }
     __syncthreads();
     // v = Av f_v + Ag g, xi = Xv f_v + Xg g (row list A: v rows, then xi rows), eta = Eh h
-    // (row list B); mean mode: u = Eh f_u, w = Eh f_w (list A), no list B.  A thread takes
-    // the rows r and r + h of a list (h = half the list, rounded up).
+    // (row list B); mean mode: u = Eh f_u, w = Eh f_w (list A), no list B.  A task is one
+    // row of list A (McV + McP terms) or two rows of list B (McP terms each), so the tasks
+    // carry about the same work; warps hold RW rows of one list.  Each row is one fma chain
+    // in increasing j (the order of the single per-mode kernel, so the bits agree).
     {
       const int Mc0 = (N - g) / 2 + 1;
       const int nA = mean ? 2 * Mc0 : McV + McP, nB = mean ? 0 : McP;
-      const int hA = (nA + 1) / 2, hB = (nB + 1) / 2;
-      const int PA = round_up(hA, RW), PB = round_up(hB, RW);
+      const int hB = (nB + 1) / 2;
+      const int PA = round_up(nA, RW), PB = round_up(hB, RW);
       for (int t = threadIdx.x; t < (PA + PB) * SP; t += blockDim.x) {
         const int sc = t % SP, rs = t / SP;
-        double a0 = 0.0, a1 = 0.0;
-        double *out0, *out1;
-        bool v0, v1;
         if (rs < PA) {
-          v0 = rs < hA;
-          v1 = v0 && rs + hA < nA;
-          const int r0 = v0 ? rs : 0, r1 = v1 ? rs + hA : 0;
+          if (rs >= nA) continue;
+          double a = 0.0;
+          double* out;
           if (mean) {
-            // r0 < Mc0 (u rows), r1 = r0 + Mc0 (w rows)
-            const double* col0 = D + 4 * MM + r0;
-            const double* col1 = D + 4 * MM + (v1 ? r1 - Mc0 : 0);
-            for (int j = 0; j < Mc0; ++j) {
-              a0 = fma(col0[j * Mh], FV[j * XS + sc], a0);
-              a1 = fma(col1[j * Mh], GG[j * XS + sc], a1);
-            }
-            out0 = OV + r0 * XS + sc;
-            out1 = OX + (v1 ? r1 - Mc0 : 0) * XS + sc;
+            // rows < Mc0: u from f_u; rows >= Mc0: w from f_w (both with Eh)
+            const bool isu = rs < Mc0;
+            const int r = isu ? rs : rs - Mc0;
+            const double* col = D + 4 * MM + r;
+            const double* X = (isu ? FV : GG) + sc;
+            for (int j = 0; j < Mc0; ++j) a = fma(col[j * Mh], X[j * XS], a);
+            out = (isu ? OV : OX) + r * XS + sc;
           } else {
-            const bool isv0 = r0 < McV, isv1 = r1 < McV;
-            const int rr0 = isv0 ? r0 : r0 - McV, rr1 = isv1 ? r1 : r1 - McV;
-            const double* cA0 = D + (isv0 ? 0 : 2) * MM + rr0;  // Av or Xv
-            const double* cA1 = D + (isv1 ? 0 : 2) * MM + rr1;
-            for (int j = 0; j < McV; ++j) {
-              const double x = FV[j * XS + sc];
-              a0 = fma(cA0[j * Mh], x, a0);
-              a1 = fma(cA1[j * Mh], x, a1);
-            }
-            const double* cG0 = cA0 + MM;                       // Ag or Xg
-            const double* cG1 = cA1 + MM;
-            for (int j = 0; j < McP; ++j) {
-              const double x = GG[j * XS + sc];
-              a0 = fma(cG0[j * Mh], x, a0);
-              a1 = fma(cG1[j * Mh], x, a1);
-            }
-            out0 = (isv0 ? OV : OX) + rr0 * XS + sc;
-            out1 = (isv1 ? OV : OX) + rr1 * XS + sc;
+            const bool isv = rs < McV;
+            const int rr = isv ? rs : rs - McV;
+            const double* cA = D + (isv ? 0 : 2) * MM + rr;  // Av or Xv
+            for (int j = 0; j < McV; ++j) a = fma(cA[j * Mh], FV[j * XS + sc], a);
+            const double* cG = cA + MM;                       // Ag or Xg
+            for (int j = 0; j < McP; ++j) a = fma(cG[j * Mh], GG[j * XS + sc], a);
+            out = (isv ? OV : OX) + rr * XS + sc;
           }
+          *out = a;
         } else {
           const int q = rs - PA;
-          v0 = q < hB;
-          v1 = v0 && q + hB < nB;
+          const bool v0 = q < hB, v1 = v0 && q + hB < nB;
           const int r0 = v0 ? q : 0, r1 = v1 ? q + hB : 0;
           const double* c0 = D + 4 * MM + r0;
           const double* c1 = D + 4 * MM + r1;
+          double a0 = 0.0, a1 = 0.0;
           for (int j = 0; j < McP; ++j) {
             const double x = HH[j * XS + sc];
             a0 = fma(c0[j * Mh], x, a0);
             a1 = fma(c1[j * Mh], x, a1);
           }
-          out0 = OE + r0 * XS + sc;
-          out1 = OE + r1 * XS + sc;
+          if (v0) OE[r0 * XS + sc] = a0;
+          if (v1) OE[r1 * XS + sc] = a1;
         }
-        if (v0) *out0 = a0;
-        if (v1) *out1 = a1;
       }
     }
     __syncthreads();
     // assembly and output: v (class g) and u, w (class 1-g); mean mode: u, v = 0, w (class g)
     const double inv_step = op == MODE_PHI ? I0.inv_dt : I0.inv_dtau_hat;
     const double ik2 = ik2_sh;
-#pragma unroll
-    for (int q = 0; q < kOut; ++q) {
-      const int t = threadIdx.x + q * kSolveThreads;
-      if (t >= nI * nout) continue;
+    for (int t = threadIdx.x; t < nI * nout; t += blockDim.x) {
       const int i = t / nout, kk = t - i * nout;
       if (!live[i]) continue;
       int comp, row, n;
@@ -447,11 +444,13 @@ __global__ void __launch_bounds__(kSolveThreads) k_ysolve(GroupLaunch gl, int op
       const Inst& I = gl.insts[first + i];
       const size_t gidx = ((size_t)comp * nm + m) * ny + n;
       if (op == MODE_PHI) {
-        I.rhat[gidx] = make_double2((vr - sa[q].x) * inv_step, (vi - sa[q].y) * inv_step);
+        const double2 u0 = I.uhat[gidx];
+        I.rhat[gidx] = make_double2((vr - u0.x) * inv_step, (vi - u0.y) * inv_step);
       } else {
-        const double fr = -(vr - sa[q].x) * inv_step;
-        const double fi = -(vi - sa[q].y) * inv_step;
-        I.uhat[gidx] = make_double2(fma(I.dtau, fr, sb[q].x), fma(I.dtau, fi, sb[q].y));
+        const double2 q0 = I.rhat[gidx], u0 = I.uhat[gidx];
+        const double fr = -(vr - q0.x) * inv_step;
+        const double fi = -(vi - q0.y) * inv_step;
+        I.uhat[gidx] = make_double2(fma(I.dtau, fr, u0.x), fma(I.dtau, fi, u0.y));
       }
     }
     __syncthreads();  // buffer and scratch are reused by the next item
@@ -901,9 +900,10 @@ size_t smem_ysynth(int N, int G, int mt) {
   const size_t H = N / 2 + 1, XS = col_pad_host(G) * mt + 1;
   return sizeof(double) * (2 * H * H + (2 * H) * XS);
 }
-void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith, int mt) {
-  if (ff_arith) k_yanalysis<ff><<<ctas, kSplitThreads, smem, s>>>(gl, op, mt);
-  else k_yanalysis<double><<<ctas, kSplitThreads, smem, s>>>(gl, op, mt);
+void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith, int mt,
+                      int step_index) {
+  if (ff_arith) k_yanalysis<ff><<<ctas, kSplitThreads, smem, s>>>(gl, op, mt, step_index);
+  else k_yanalysis<double><<<ctas, kSplitThreads, smem, s>>>(gl, op, mt, step_index);
 }
 void launch_ysolve(int ctas, int nitems, int bufsz, int scr_rows, size_t smem, cudaStream_t s, GroupLaunch gl,
                    int op) {

@@ -116,7 +116,7 @@ def test_kernel_organisations_give_the_same_bits(pcf, tile):
     the same operations per output, so the same bits."""
     us = _mixed_inputs()
     outs, hists = [], []
-    for kind, launches, variant in ((2, 6, 1), (3, 11, 2), (4, 7, 3), (0, None, None)):
+    for kind, launches, variant in ((2, 6, 1), (3, 10, 2), (4, 7, 3), (0, None, None)):
         s = pcf.Solver.batched(MIXED, solve_kind=kind, modes_per_block=tile)
         if launches is not None:
             assert s.launches_per_step() == launches and s.solve_variant() == variant
