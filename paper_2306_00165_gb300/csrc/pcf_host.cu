@@ -412,8 +412,10 @@ pcf_status launch_synth(pcf_ctx* c, int slot, int nf) {
 pcf_status launch_prodM(pcf_ctx* c) {
   return timed(c, 2, [&] { launch_prod(c->plane_kind, false, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod)); });
 }
-pcf_status launch_prodN(pcf_ctx* c) {
-  return timed(c, 5, [&] { launch_prod(c->plane_kind, true, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod)); });
+pcf_status launch_prodN(pcf_ctx* c, int step_index = -1) {
+  return timed(c, 5, [&] {
+    launch_prod(c->plane_kind, true, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod), step_index);
+  });
 }
 
 pcf_status launch_tc_synth(pcf_ctx* c, int slot) {
@@ -424,10 +426,9 @@ pcf_status launch_tc_analysis(pcf_ctx* c) {
 }
 // split mode kernels of the FP64 descent step
 GroupLaunch gl_of(pcf_ctx* c, const int* pre) { return GroupLaunch{c->dinst, pre, c->d_groups, c->ngroups}; }
-pcf_status launch_split_analysis(pcf_ctx* c, int op, int step_index = -1) {
-  return timed(c, 7, [&] {
-    launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), op, c->plane_kind == 2, c->smt, step_index);
-  });
+pcf_status launch_split_analysis(pcf_ctx* c, int op) {
+  return timed(c, 7,
+               [&] { launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), op, c->plane_kind == 2, c->smt); });
 }
 GroupLaunch gl_solve(pcf_ctx* c) { return GroupLaunch{c->dinst, c->pre_ys, c->d_groups_s, c->ngroups_s}; }
 pcf_status launch_split_solve(pcf_ctx* c, int op) {
@@ -532,8 +533,8 @@ pcf_status step_body(pcf_ctx* c, int s) {
     PCF_TRY(launch_split_solve(c, MODE_PHI));
     PCF_TRY(launch_split_synth(c, 1, 1));
     PCF_TRY(launch_synth(c, 1, kFieldsSynth));
-    PCF_TRY(launch_prodN(c));
-    PCF_TRY(launch_split_analysis(c, MODE_PSI_UPDATE, s));  // with J, history and mask
+    PCF_TRY(launch_prodN(c, s));  // with J, its history entry and the convergence mask
+    PCF_TRY(launch_split_analysis(c, MODE_PSI_UPDATE));
     PCF_TRY(launch_split_solve(c, MODE_PSI_UPDATE));
     if (c->any_sym) PCF_TRY(launch_sym(c, -1));
     PCF_TRY(launch_split_synth(c, 0, 1));
@@ -1064,8 +1065,11 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
   double *ph = nullptr, *np = nullptr, *fr = nullptr;
   float2 *yvf = nullptr, *xzf = nullptr, *xzc = nullptr;
   float* phf = nullptr;
-  if (ctx_alloc(c, &np, n_np) || ctx_alloc(c, &c->r_int, (size_t)c->total_state) || ctx_alloc(c, &c->active, (size_t)B))
+  int* jc = nullptr;
+  if (ctx_alloc(c, &np, n_np) || ctx_alloc(c, &c->r_int, (size_t)c->total_state) ||
+      ctx_alloc(c, &c->active, (size_t)B) || ctx_alloc(c, &jc, (size_t)B))
     return fail(PCF_ENOMEM);
+  if (cudaMemset(jc, 0, sizeof(int) * B) != cudaSuccess) return fail(PCF_ECUDA);
   if (c->mixed) {
     if (ctx_alloc(c, &yvf, n_yv) || ctx_alloc(c, &phf, n_ph) || ctx_alloc(c, &xzf, n_xz) || ctx_alloc(c, &xzc, n_xz))
       return fail(PCF_ENOMEM);
@@ -1099,6 +1103,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       I.dense[0] = g.dense0; I.dense[1] = g.dense1;
       I.sigma[0] = g.sig[0]; I.sigma[1] = g.sig[1];
       I.normpart = np + o_np;
+      I.jcount = jc + b;
       if (c->mixed) {
         I.yvf = yvf + o_yv; I.physf = phf + o_ph; I.xzf = xzf + o_xz; I.xzc = xzc + o_xz;
         I.twxf = g.twxf; I.twzf = g.twzf; I.tcA = g.tcA; I.mixed = 1;

@@ -120,6 +120,7 @@ struct Inst {
   int hist_stride;
   int* active;        // 1 = keep updating
   int sym;            // symmetry mask enforced on this instance (pcf_symmetry bits)
+  int* jcount;        // CTAs of the adjoint product kernel done with their plane sums (zero between launches)
 };
 
 // ------------------------------------------------------------------ quasi-tridiagonal tau solver

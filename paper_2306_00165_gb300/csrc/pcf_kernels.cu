@@ -397,7 +397,7 @@ __device__ __forceinline__ void product_rows(const Inst& I, const T* const* U, c
 // Register budgets: eight resident CTAs per SM for M(u); six for N(q), which holds both
 // fields' plane pointers (at 8 x 32x33x32 its 792 CTAs then fit one wave of 152 SMs).
 template <class T, bool ADJ>
-__global__ void __launch_bounds__(128, ADJ ? 6 : 8) k_prod_t(LaunchInfo li) {
+__global__ void __launch_bounds__(128, ADJ ? 6 : 8) k_prod_t(LaunchInfo li, int step_index) {
   using C = typename Cx<T>::c;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
@@ -467,6 +467,37 @@ __global__ void __launch_bounds__(128, ADJ ? 6 : 8) k_prod_t(LaunchInfo li) {
     const C v = Y[p * LX + xbin(i, Kx, Mx, nx)];
     dst[t] = store_c<T>(Cx<T>::mk(v.x * sc, v.y * sc));
   }
+  if (ADJ && step_index >= 0) {
+    // J = ||r1|| once all 3 ny plane sums of the instance are written: the CTA that counts
+    // last computes it (the chain of norm_from_parts, so the bits match the other paths),
+    // writes the history entry, clears the mask when J < tol (the instance stops before this
+    // step's update) and resets the counter for the next launch.
+    __shared__ int last;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      last = atomicAdd(I.jcount, 1) == 3 * I.ny - 1;
+    }
+    __syncthreads();
+    if (last) {  // uniform in the CTA
+      // the plane buffers are free now: stage the per-plane sums and the weights
+      const int ny = I.ny;
+      const double* P = I.normpart;
+      double* ps = reinterpret_cast<double*>(smraw);
+      for (int q = threadIdx.x; q < ny; q += blockDim.x) {
+        ps[q] = __ldcg(P + q) + __ldcg(P + ny + q) + __ldcg(P + 2 * ny + q);
+        ps[ny + q] = I.ccw[q];
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < ny; ++q) s = fma(ps[ny + q], ps[q], s);
+        const double J = sqrt(0.5 * I.inv_nxnz * s);
+        if (I.hist) I.hist[(size_t)step_index * I.hist_stride] = J;
+        if (I.tol > 0.0 && J < I.tol && I.active) *I.active = 0;
+        *I.jcount = 0;
+      }
+    }
+  }
 }
 
 // CTA = (instance, plane j, component c): sum over the plane of the squared velocity
@@ -499,16 +530,16 @@ void launch_xzsynth(int kind, int ctas, size_t smem, cudaStream_t s, LaunchInfo 
   else if (kind == 2) k_xzsynth_t<ff><<<ctas, 128, smem, s>>>(li, slot, nf);
   else k_xzsynth_t<double><<<ctas, 128, smem, s>>>(li, slot, nf);
 }
-void launch_prod(int kind, bool adj, int ctas, size_t smem, cudaStream_t s, LaunchInfo li) {
+void launch_prod(int kind, bool adj, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int step_index) {
   if (kind == 1) {
-    if (adj) k_prod_t<float, true><<<ctas, 128, smem, s>>>(li);
-    else k_prod_t<float, false><<<ctas, 128, smem, s>>>(li);
+    if (adj) k_prod_t<float, true><<<ctas, 128, smem, s>>>(li, step_index);
+    else k_prod_t<float, false><<<ctas, 128, smem, s>>>(li, -1);
   } else if (kind == 2) {
-    if (adj) k_prod_t<ff, true><<<ctas, 128, smem, s>>>(li);
-    else k_prod_t<ff, false><<<ctas, 128, smem, s>>>(li);
+    if (adj) k_prod_t<ff, true><<<ctas, 128, smem, s>>>(li, step_index);
+    else k_prod_t<ff, false><<<ctas, 128, smem, s>>>(li, -1);
   } else {
-    if (adj) k_prod_t<double, true><<<ctas, 128, smem, s>>>(li);
-    else k_prod_t<double, false><<<ctas, 128, smem, s>>>(li);
+    if (adj) k_prod_t<double, true><<<ctas, 128, smem, s>>>(li, step_index);
+    else k_prod_t<double, false><<<ctas, 128, smem, s>>>(li, -1);
   }
 }
 void launch_norm_planes(int kind, int ctas, cudaStream_t s, LaunchInfo li, int slot) {

@@ -64,7 +64,9 @@ __device__ __forceinline__ double norm_from_parts(const Inst& I) {
 
 // kind: plane arithmetic, 0 FP64, 1 FP32 (mixed form), 2 float-float
 void launch_xzsynth(int kind, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int slot, int nf);
-void launch_prod(int kind, bool adj, int ctas, size_t smem, cudaStream_t s, LaunchInfo li);
+// step_index >= 0 (adjoint product only): the last CTA of each instance also computes J from
+// the plane sums, its history entry and the convergence mask (in place of launch_jnorm)
+void launch_prod(int kind, bool adj, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int step_index = -1);
 void launch_norm_planes(int kind, int ctas, cudaStream_t s, LaunchInfo li, int slot);
 cudaError_t set_plane_smem(int kind, size_t synth, size_t prod);
 __global__ void k_mode(LaunchInfo li, int op, int sig, int mpc, int step_index);
@@ -96,10 +98,7 @@ size_t smem_ysolve(int N, int G);
 size_t smem_ysynth(int N, int G, int mt);
 // ff_arith: the Chebyshev dot products in float-float arithmetic (float-float form)
 // mt: consecutive modes per CTA of the analysis and synthesis kernels (col_pad(G) mt <= 32)
-// step_index >= 0: the dummy-dynamics analysis also computes J, its history entry and the
-// convergence mask (in place of launch_jnorm)
-void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith, int mt,
-                      int step_index = -1);
+void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith, int mt);
 void launch_ysolve(int ctas, int nitems, int bufsz, int scr_rows, size_t smem, cudaStream_t s, GroupLaunch gl,
                    int op);
 void launch_jnorm(int ninst, cudaStream_t s, const Inst* insts, int step_index);

@@ -104,42 +104,9 @@ __device__ __forceinline__ void group_flags(const GroupLaunch& gl, int first, in
   if (threadIdx.x < nI) live[threadIdx.x] = inst_active(gl.insts[first + threadIdx.x]) ? 1 : 0;
 }
 
-// J = ||r1|| from the plane sums of the adjoint product kernel, in the order of
-// norm_from_parts (one fma chain over j), so every kernel that computes it gets the same bits.
-__device__ __forceinline__ double jnorm_of(const Inst& I) {
-  const int ny = I.ny;
-  const double* P = I.normpart;
-  double s = 0.0;
-  for (int j = 0; j < ny; ++j) s = fma(I.ccw[j], P[j] + P[ny + j] + P[2 * ny + j], s);
-  return sqrt(0.5 * I.inv_nxnz * s);
-}
-
-// Live flags of the dummy-dynamics half-step with the norm folded in: every CTA of the group
-// computes J of its active instances (J < tol: the instance stops before this step's
-// update); the group's first CTA (lead) writes the history entry and clears the mask.  A CTA
-// that reads a mask the lead is clearing decides the same from its own J.
-__device__ __forceinline__ void group_flags_jnorm(const GroupLaunch& gl, int first, int nI, int* live, bool lead,
-                                                  int step_index) {
-  if (threadIdx.x < nI) {
-    const Inst& I = gl.insts[first + threadIdx.x];
-    int lv = inst_active(I) ? 1 : 0;
-    if (lv) {
-      const double J = jnorm_of(I);
-      if (lead && I.hist) I.hist[(size_t)step_index * I.hist_stride] = J;
-      if (I.tol > 0.0 && J < I.tol) {
-        lv = 0;
-        if (lead && I.active) *I.active = 0;
-      }
-    }
-    live[threadIdx.x] = lv;
-  }
-}
-
 // A: arithmetic of the Chebyshev dot products (double, or ff in the float-float form)
 template <class A>
-// step_index >= 0 (dummy-dynamics half-step only): J, its history entry and the convergence
-// mask are computed here (group_flags_jnorm) instead of in k_jnorm.
-__global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int op, int mt, int step_index) {
+__global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int op, int mt) {
   extern __shared__ double sm[];
   __shared__ int live[kMaxGroup];
   int local;
@@ -155,8 +122,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int
   A* Ao = Ae + H * H;                // [H][H] (rows < H-1 used)
   A* VP = Ao + H * H;                // [H][XS]    P_j = V_j + V_{N-j} (j < N/2), V_{N/2}
   A* VQ = VP + H * XS;               // [half][XS] Q_j = V_j - V_{N-j}
-  if (step_index >= 0) group_flags_jnorm(gl, first, nI, live, local == 0, step_index);
-  else group_flags(gl, first, nI, live);
+  group_flags(gl, first, nI, live);
   for (int t = threadIdx.x; t < 2 * H * H; t += blockDim.x) Ae[t] = cheb_at<A>(I0, CL.Ae() + t);
   for (int t = threadIdx.x; t < H * SPt / 2; t += blockDim.x) {
     const int pr = t % (SPt / 2), j = t / (SPt / 2), mm = pr / (SP / 2), i = pr - mm * (SP / 2);
@@ -900,10 +866,9 @@ size_t smem_ysynth(int N, int G, int mt) {
   const size_t H = N / 2 + 1, XS = col_pad_host(G) * mt + 1;
   return sizeof(double) * (2 * H * H + (2 * H) * XS);
 }
-void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith, int mt,
-                      int step_index) {
-  if (ff_arith) k_yanalysis<ff><<<ctas, kSplitThreads, smem, s>>>(gl, op, mt, step_index);
-  else k_yanalysis<double><<<ctas, kSplitThreads, smem, s>>>(gl, op, mt, step_index);
+void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith, int mt) {
+  if (ff_arith) k_yanalysis<ff><<<ctas, kSplitThreads, smem, s>>>(gl, op, mt);
+  else k_yanalysis<double><<<ctas, kSplitThreads, smem, s>>>(gl, op, mt);
 }
 void launch_ysolve(int ctas, int nitems, int bufsz, int scr_rows, size_t smem, cudaStream_t s, GroupLaunch gl,
                    int op) {
