@@ -530,7 +530,7 @@ def run_ours(args):
                            "dt": DT, "dtau_hat": DTAU_HAT, "dtau": DTAU,
                            "l2": "flushed (256 MB write) before every timed step",
                            "parallelism": f"replicas x{ws}"},
-                "e2e": e2e, "gpu_launches": (1 + s.launches_per_step()) * args.steps,
+                "e2e": e2e, "gpu_launches": s.launches_per_call(1) * args.steps,
                 "time_to_converge": ttc,
                 "roofline": roof, "clocks": ck, "wall_s": wall,
                 "J_after": [float(x) for x in J_last]}

@@ -355,9 +355,14 @@ pcf_status pcf_probe_fp64_peak(void* stream, double* gflops);
  * 9 computes J, its history and the convergence mask once per step; otherwise 3/6 hold
  * the whole per-mode kernel and 7, 8, 9 stay empty. */
 pcf_status pcf_set_kernel_timing(pcf_ctx* ctx, int enable);
+
+/* Kernel launches of one pcf_descent_step call of nsteps steps (the entry synthesis, and
+ * projection when a symmetry is enforced, plus the steps); -1 for a bad argument. */
+long long pcf_launches_per_call(pcf_ctx* ctx, int nsteps);
 pcf_status pcf_kernel_times(pcf_ctx* ctx, double* ms, long long* launches, int n);
 
-/* Number of kernel launches one descent step issues (for launch accounting). */
+/* Number of kernel launches one descent step issues inside a multi-step call (for launch
+ * accounting; pcf_launches_per_call counts a whole call). */
 int pcf_launches_per_step(pcf_ctx* ctx);
 
 #ifdef __cplusplus

@@ -92,6 +92,7 @@ def load_library(path=None):
         "pcf_set_kernel_timing": (I, [P, I]),
         "pcf_kernel_times": (I, [P, P, P, I]),
         "pcf_launches_per_step": (I, [P]),
+        "pcf_launches_per_call": (ctypes.c_longlong, [P, I]),
         "pcf_solve_variant": (I, [P]),
     }
     for name, (res, args) in sigs.items():
@@ -347,6 +348,10 @@ class Solver:
 
     def launches_per_step(self):
         return int(self.lib.pcf_launches_per_step(self._h))
+
+    def launches_per_call(self, nsteps=1):
+        """Kernel launches of one descent_step call of nsteps steps."""
+        return int(self.lib.pcf_launches_per_call(self._h, int(nsteps)))
 
 
 class FNO:

@@ -527,6 +527,9 @@ pcf_status step_body(pcf_ctx* c, int s) {
     return PCF_OK;
   }
   if (c->split) {
+    // the y-values of the state the previous step updated (the call's first step reads the
+    // synthesis done at the call's start)
+    if (s > 0) PCF_TRY(launch_split_synth(c, 0, 1));
     PCF_TRY(launch_synth(c, 0, kFieldsSynth));
     PCF_TRY(launch_prodM(c));
     PCF_TRY(launch_split_analysis(c, MODE_PHI));
@@ -537,7 +540,6 @@ pcf_status step_body(pcf_ctx* c, int s) {
     PCF_TRY(launch_split_analysis(c, MODE_PSI_UPDATE));
     PCF_TRY(launch_split_solve(c, MODE_PSI_UPDATE));
     if (c->any_sym) PCF_TRY(launch_sym(c, -1));
-    PCF_TRY(launch_split_synth(c, 0, 1));
     return PCF_OK;
   }
   PCF_TRY(launch_synth(c, 0, kFieldsSynth));
@@ -1472,6 +1474,15 @@ pcf_status pcf_norm(pcf_ctx* c, const double* u, double* out) {
   k_norm_final<<<1, 32, 0, c->cs>>>(li_of(c, c->pre_inst), out);
   PCF_TRY(check_launch());
   return leave(c);
+}
+
+long long pcf_launches_per_call(pcf_ctx* c, int nsteps) {
+  if (!c || nsteps < 0) return -1;
+  if (nsteps == 0) return 0;
+  // the entry projection and synthesis, then the steps; the split step synthesises the state
+  // at its start, which the first step takes from the entry synthesis
+  const long long entry = 1 + (c->any_sym ? 1 : 0);
+  return entry + (long long)nsteps * pcf_launches_per_step(c) - (c->split && !c->fused ? 1 : 0);
 }
 
 pcf_status pcf_symmetrize(pcf_ctx* c, double* u, int mask) {

@@ -120,6 +120,7 @@ def test_kernel_organisations_give_the_same_bits(pcf, tile):
         s = pcf.Solver.batched(MIXED, solve_kind=kind, modes_per_block=tile)
         if launches is not None:
             assert s.launches_per_step() == launches and s.solve_variant() == variant
+            assert s.launches_per_call(3) == 1 + 3 * launches - (1 if kind == 3 else 0)
         u = _flat(us)
         hists.append(s.descent_step(u, 0.01, 4).cpu().numpy())
         outs.append(u.cpu().numpy())
