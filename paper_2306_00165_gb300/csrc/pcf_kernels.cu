@@ -213,6 +213,84 @@ __device__ C* fft_run(C* a, C* b, int L, int LS, int nb, const int* radix, int n
   return a;
 }
 
+// The same pass with its inputs read through ld(b, i) (element i of batch b) and its outputs
+// written through st(b, i, v), so that a transform's first pass can read its input where it
+// lies (and build it on the fly) and its last pass can write the result where it is needed,
+// without shared-memory round trips and barriers of their own.  Same arithmetic as
+// stockham_pass.
+template <int R, class C, class LD, class ST>
+__device__ __forceinline__ void stockham_pass_io(int L, int nb, int Ns, const C* __restrict__ tw, bool inv,
+                                                 const LD& ld, const ST& st) {
+  const int nq = L / R;
+  const int total = nq * nb;
+  const int twstep = L / (Ns * R);
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int bi = t / nq;
+    const int j = t - bi * nq;
+    const int k = j % Ns;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = ld(bi, j + r * nq);
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C w = tw[r * k * twstep];
+        if (inv) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
+    }
+    butterfly<R, C>(v, inv);
+    const int idx = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) st(bi, idx + r * Ns, v[r]);
+  }
+}
+
+template <class C>
+struct SmemLd {
+  const C* p;
+  int LS;
+  __device__ __forceinline__ C operator()(int b, int i) const { return p[b * LS + i]; }
+};
+template <class C>
+struct SmemSt {
+  C* p;
+  int LS;
+  __device__ __forceinline__ void operator()(int b, int i, C v) const { p[b * LS + i] = v; }
+};
+
+template <class C, class LD, class ST>
+__device__ __forceinline__ void pass_r(int R, int L, int nb, int Ns, const C* tw, bool inv, const LD& ld, const ST& st) {
+  if (R == 4) stockham_pass_io<4, C>(L, nb, Ns, tw, inv, ld, st);
+  else if (R == 2) stockham_pass_io<2, C>(L, nb, Ns, tw, inv, ld, st);
+  else stockham_pass_io<3, C>(L, nb, Ns, tw, inv, ld, st);
+}
+
+// Full transform of nb batches whose first pass reads through ld.  The later passes
+// ping-pong between a and b (stride LS), the first pass writing a.  With OUT_ST the last
+// pass writes through st (returns null); otherwise the result stays in shared memory and
+// the buffer holding it is returned.  A barrier follows every pass but the last.
+template <bool OUT_ST, class C, class LD, class ST>
+__device__ C* fft_run_io(C* a, C* b, int L, int LS, int nb, const int* radix, int nr, const C* tw, bool inv,
+                         const LD& ld, const ST& st) {
+  int Ns = 1;
+  C* cur = nullptr;
+  C* out = a;
+  for (int s = 0; s < nr; ++s) {
+    const int R = radix[s];
+    const bool first = s == 0, last = s == nr - 1 && OUT_ST;
+    if (first && last) pass_r(R, L, nb, Ns, tw, inv, ld, st);
+    else if (first) pass_r(R, L, nb, Ns, tw, inv, ld, SmemSt<C>{out, LS});
+    else if (last) pass_r(R, L, nb, Ns, tw, inv, SmemLd<C>{cur, LS}, st);
+    else pass_r(R, L, nb, Ns, tw, inv, SmemLd<C>{cur, LS}, SmemSt<C>{out, LS});
+    Ns *= R;
+    if (s < nr - 1) __syncthreads();
+    cur = out;
+    out = (out == a) ? b : a;
+  }
+  return OUT_ST ? nullptr : cur;
+}
+
 template <class T>
 __device__ __forceinline__ void load_twiddles(const Inst& I, typename Cx<T>::c* twx, typename Cx<T>::c* twz) {
   const typename Sto<T>::c* sx = twx_of<T>(I);
@@ -279,21 +357,24 @@ __global__ void __launch_bounds__(128, PCF_XZ_MINB) k_xzsynth_t(LaunchInfo li, i
   C* B1 = sm + pp.PB;
   C* twx = sm + 2 * pp.PB;
   C* twz = twx + nx;
-  load_twiddles<T>(I, twx, twz);
+  load_twiddles<T>(I, twx, twz);  // first used after the first pass's barrier
   const int LX = pp.LX, LZ = pp.LZ;
-  for (int t = threadIdx.x; t < Mz * LX; t += blockDim.x) B0[t] = Cx<T>::mk(0, 0);
-  __syncthreads();
   const typename Sto<T>::c* src = yv_of<T>(I) + (((size_t)slot * kFieldsY + c_src[f]) * I.ny + j) * (size_t)I.nmodes;
   const int fac = c_fac[f];
-  for (int t = threadIdx.x; t < I.nmodes; t += blockDim.x) {
-    const int i = t / Mz, p = t - i * Mz;
-    C s = load_c<T>(src[t]);
-    if (fac == 1) { const T k = (T)I.kx[i]; s = Cx<T>::mk(-k * s.y, k * s.x); }
-    else if (fac == 2) { const T k = (T)I.kz[p]; s = Cx<T>::mk(-k * s.y, k * s.x); }
-    B0[p * LX + xbin(i, Kx, Mx, nx)] = s;
-  }
+  // x stage: batch p (retained z mode), element = x bin; the first pass reads the y-values
+  // (times i kx or i kz for the x and z derivatives); bins outside |m| <= Kx are zero
+  const auto ldx = [&](int p, int bin) -> C {
+    const int i = bin <= Kx ? bin : (bin >= nx - Kx ? Mx - (nx - bin) : -1);
+    C s = Cx<T>::mk(0, 0);
+    if (i >= 0) {
+      s = load_c<T>(src[i * Mz + p]);
+      if (fac == 1) { const T k = (T)I.kx[i]; s = Cx<T>::mk(-k * s.y, k * s.x); }
+      else if (fac == 2) { const T k = (T)I.kz[p]; s = Cx<T>::mk(-k * s.y, k * s.x); }
+    }
+    return s;
+  };
+  C* G = fft_run_io<false, C>(B0, B1, nx, LX, Mz, I.rx, I.nrx, twx, true, ldx, SmemSt<C>{nullptr, 0});
   __syncthreads();
-  C* G = fft_run<C>(B0, B1, nx, LX, Mz, I.rx, I.nrx, twx, true);
   C* Zb = (G == B0) ? B1 : B0;
   const int nr = nx / 2;
   T* out = phys_of<T>(I) + (((size_t)slot * kFieldsSynth + f) * I.ny + j) * (size_t)nx * nz;
@@ -303,11 +384,10 @@ __global__ void __launch_bounds__(128, PCF_XZ_MINB) k_xzsynth_t(LaunchInfo li, i
     C* Z1 = (pp.chunk == nr) ? G : Zb + pp.chunk * LZ;
     // Row pair (x1, x2) -> one complex row whose inverse z transform gives row x1 in the
     // real part and row x2 in the imaginary part: h_z = G_z[x1] + i G_z[x2] with
-    // G_{-p} = conj(G_p) (p = 0: real parts only; |p| > Kz: zero).  Written branch-free, so
-    // that a warp issues each multiply-add once for all its lanes: s = +-1 picks the
-    // conjugate, and the multiply-adds by +-1 and 0 are exact.
-    for (int t = threadIdx.x; t < nrc * nz; t += blockDim.x) {
-      const int r = t / nz, z = t - r * nz;
+    // G_{-p} = conj(G_p) (p = 0: real parts only; |p| > Kz: zero), built as the first z
+    // pass reads it.  Branch-free, so that a warp issues each multiply-add once for all its
+    // lanes: s = +-1 picks the conjugate, and the multiply-adds by +-1 and 0 are exact.
+    const auto ldz = [&](int r, int z) -> C {
       const int x1 = 2 * (r0 + r), x2 = x1 + 1;
       const bool lo = z <= Kz, hi = z >= nz - Kz;
       const int p = lo ? z : nz - z;
@@ -317,18 +397,16 @@ __global__ void __launch_bounds__(128, PCF_XZ_MINB) k_xzsynth_t(LaunchInfo li, i
         g2 = G[p * LX + x2];
       }
       if (z == 0) g1.y = g2.y = T(0.0);
-      const T s = lo ? T(1.0) : T(-1.0);
-      Z0[r * LZ + z] = Cx<T>::mk(fma(-s, g2.y, g1.x), fma(s, g1.y, g2.x));
-    }
-    __syncthreads();
-    C* Rz = fft_run<C>(Z0, Z1, nz, LZ, nrc, I.rz, I.nrz, twz, true);
-    for (int t = threadIdx.x; t < nrc * nz; t += blockDim.x) {
-      const int r = t / nz, z = t - r * nz;
-      const C h = Rz[r * LZ + z];
+      const T sg = lo ? T(1.0) : T(-1.0);
+      return Cx<T>::mk(fma(-sg, g2.y, g1.x), fma(sg, g1.y, g2.x));
+    };
+    // the last z pass writes rows x1 (real part) and x2 (imaginary part) of the plane
+    const auto stz = [&](int r, int z, C h) {
       out[(2 * (r0 + r)) * nz + z] = h.x;
       out[(2 * (r0 + r) + 1) * nz + z] = h.y;
-    }
-    __syncthreads();
+    };
+    fft_run_io<true, C>(Z0, Z1, nz, LZ, nrc, I.rz, I.nrz, twz, true, ldz, stz);
+    if (r0 + pp.chunk < nr) __syncthreads();  // the next chunk rewrites Z0
   }
 }
 
@@ -641,8 +719,7 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
   }
   __syncthreads();
 
-  const double step = sig == 0 ? I.dt : I.dtau_hat;
-  const double inv_step = sig == 0 ? I.inv_dt : I.inv_dtau_hat;  // = 1.0 / step
+  const double inv_step = sig == 0 ? I.inv_dt : I.inv_dtau_hat;  // 1 / the step size
   const double inv_nu = I.inv_nu;
   const int half = N / 2;
   if (solve) {
