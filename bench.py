@@ -517,7 +517,7 @@ def run_ours(args):
     roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_tf, 4), "unit": "TFLOP/s",
             "frac": round(achieved / peak_tf, 4), "traffic": TRAFFIC_BYTES.get(dom), "kernel": dom,
             "peak_source": "measured FP64 DFMA throughput (k_fp64_probe) on this GPU",
-            "kernel_share": round(kt[dom][0] / total_ms, 4), "mode_tile": s.mode_tile(),
+            "kernel_share": round(kt[dom][0] / total_ms, 4), "mode_tile": s.mode_tile(), "split_config": s.split_config(),
             "kernel_ms_per_launch": round(dom_ms, 5),
             "per_kernel_ms_per_step": {k: round(v[0] / nk, 5) for k, v in kt.items()}}
 

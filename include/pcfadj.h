@@ -356,6 +356,13 @@ pcf_status pcf_probe_fp64_peak(void* stream, double* gflops);
  * the whole per-mode kernel and 7, 8, 9 stay empty. */
 pcf_status pcf_set_kernel_timing(pcf_ctx* ctx, int enable);
 
+/* Organisation the autotuner chose for the split per-mode kernels (FP64 and float-float
+ * forms): cfg[0] instances per group of the analysis and synthesis kernels, cfg[1] and cfg[2]
+ * consecutive modes per CTA of the analysis and of the synthesis, cfg[3] instances per group
+ * of the Stokes solve.  Zeros where the context does not use those kernels (fused solve:
+ * cfg[3] = 0).  cfg: host int[4]. */
+pcf_status pcf_split_config(const pcf_ctx* ctx, int* cfg);
+
 /* Kernel launches of one pcf_descent_step call of nsteps steps (the entry synthesis, and
  * projection when a symmetry is enforced, plus the steps); -1 for a bad argument. */
 long long pcf_launches_per_call(pcf_ctx* ctx, int nsteps);

@@ -93,6 +93,7 @@ def load_library(path=None):
         "pcf_kernel_times": (I, [P, P, P, I]),
         "pcf_launches_per_step": (I, [P]),
         "pcf_launches_per_call": (ctypes.c_longlong, [P, I]),
+        "pcf_split_config": (I, [P, ctypes.POINTER(I)]),
         "pcf_solve_variant": (I, [P]),
     }
     for name, (res, args) in sigs.items():
@@ -348,6 +349,12 @@ class Solver:
 
     def launches_per_step(self):
         return int(self.lib.pcf_launches_per_step(self._h))
+
+    def split_config(self):
+        """Autotuned organisation of the split per-mode kernels: dict of group sizes and mode tiles."""
+        cfg = (ctypes.c_int * 4)()
+        _check(self.lib.pcf_split_config(self._h, cfg))
+        return {"group": cfg[0], "analysis_mode_tile": cfg[1], "synthesis_mode_tile": cfg[2], "solve_group": cfg[3]}
 
     def launches_per_call(self, nsteps=1):
         """Kernel launches of one descent_step call of nsteps steps."""

@@ -33,7 +33,8 @@ struct pcf_ctx {
   // split mode kernels (FP64 form with dense operators): instance groups and geometry
   bool split = false;
   int sgrp = 0;                 // largest instances per group
-  int smt = 1;                  // consecutive modes per CTA of the split analysis / synthesis
+  int smt = 1;                  // consecutive modes per CTA of the split analysis
+  int smt_y = 1;                // ... and of the split synthesis (tuned separately)
   int ngroups = 0;
   int2* d_groups = nullptr;     // [B] (first, count)
   int* pre_ya = nullptr;        // CTA prefixes over groups [B + 1]

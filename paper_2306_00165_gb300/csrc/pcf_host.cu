@@ -447,7 +447,7 @@ pcf_status launch_split_synth(pcf_ctx* c, int slot, int in_step) {
   return timed(c, in_step ? 8 : 0,
                [&] {
                  launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), slot, in_step,
-                                     c->plane_kind == 2, c->smt);
+                                     c->plane_kind == 2, c->smt_y);
                });
 }
 
@@ -789,7 +789,9 @@ static pcf_status set_solve_groups(pcf_ctx* c, int G) {
   return PCF_OK;
 }
 
-static pcf_status set_split_groups(pcf_ctx* c, int G, int mt = 1) {
+// Instance groups of the split analysis and synthesis (at most G instances each) with mt_a and
+// mt_y consecutive modes per CTA (mt_y < 1: the same as mt_a); also resets the solve's groups.
+static pcf_status set_split_groups(pcf_ctx* c, int G, int mt = 1, int mt_y = 0) {
   int Nmax = 0;
   for (const Inst& I : c->hinst) Nmax = std::max(Nmax, I.N);
   G = std::max(1, std::min(G, split_max_group(Nmax)));
@@ -800,15 +802,17 @@ static pcf_status set_split_groups(pcf_ctx* c, int G, int mt = 1) {
   for (const int2& gq : groups) gmax = std::max(gmax, gq.y);
   mt = std::max(1, mt);
   while (mt > 1 && split_col_pad(gmax) * mt > 32) mt >>= 1;
+  mt_y = mt_y < 1 ? mt : mt_y;
+  while (mt_y > 1 && split_col_pad(gmax) * mt_y > 32) mt_y >>= 1;
   std::vector<int> pa(ng + 1, 0), py(ng + 1, 0), pf(ng + 1, 0);
   size_t sa = 0, sy = 0;
   for (int q = 0; q < ng; ++q) {
     const Inst& I = c->hinst[groups[q].x];
     pf[q + 1] = pf[q] + I.nmodes;
     pa[q + 1] = pa[q] + split_ctas_per_group(0, I.nmodes, mt);
-    py[q + 1] = py[q] + split_ctas_per_group(2, I.nmodes, mt);
+    py[q + 1] = py[q] + split_ctas_per_group(2, I.nmodes, mt_y);
     sa = std::max(sa, smem_yanalysis(I.N, groups[q].y, mt));
-    sy = std::max(sy, smem_ysynth(I.N, groups[q].y, mt));
+    sy = std::max(sy, smem_ysynth(I.N, groups[q].y, mt_y));
   }
   if (std::max(sa, sy) > 227 * 1024) return PCF_ENOTSUP;
   if (!c->d_groups) {
@@ -824,6 +828,7 @@ static pcf_status set_split_groups(pcf_ctx* c, int G, int mt = 1) {
   PCF_CUDA(cudaMemcpy(c->pre_yy, py.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
   c->sgrp = G;
   c->smt = mt;
+  c->smt_y = mt_y;
   c->ngroups = ng;
   c->cta_ya = pa[ng];
   c->cta_yy = py[ng];
@@ -861,7 +866,7 @@ static pcf_status autotune_split(pcf_ctx* c) {
           }
           launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), MODE_PHI, c->plane_kind == 2, c->smt);
           launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_solve(c), MODE_PHI);
-          launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), 1, 1, c->plane_kind == 2, c->smt);
+          launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), 1, 1, c->plane_kind == 2, c->smt_y);
         };
         seq();
         PCF_CUDA(cudaEventRecord(a, c->cs));
@@ -882,6 +887,33 @@ static pcf_status autotune_split(pcf_ctx* c) {
   c->tuned_split_ms = best_ms / 3.0;
   pcf_status st = set_split_groups(c, best, best_mt);
   c->fused = st == PCF_OK && best_fused;
+  if (st == PCF_OK && !c->fused) {
+    // analysis and synthesis mode tiles, each timed alone
+    auto time5 = [&](auto&& launch, float* ms) -> pcf_status {
+      launch();
+      PCF_CUDA(cudaEventRecord(a, c->cs));
+      for (int r = 0; r < 5; ++r) launch();
+      PCF_CUDA(cudaEventRecord(b, c->cs));
+      PCF_CUDA(cudaEventSynchronize(b));
+      PCF_CUDA(cudaEventElapsedTime(ms, a, b));
+      return PCF_OK;
+    };
+    int mt_a = best_mt, mt_y = best_mt;
+    float ba = 1e30f, by = 1e30f;
+    for (int mt = 1; mt <= 16 && split_col_pad(best) * mt <= 32; mt *= 2) {
+      if (set_split_groups(c, best, mt, mt) != PCF_OK || c->smt != mt || c->smt_y != mt) continue;
+      float ms = 0.f;
+      PCF_TRY(time5([&] {
+        launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), MODE_PHI, c->plane_kind == 2, c->smt);
+      }, &ms));
+      if (ms < ba) { ba = ms; mt_a = mt; }
+      PCF_TRY(time5([&] {
+        launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), 1, 1, c->plane_kind == 2, c->smt_y);
+      }, &ms));
+      if (ms < by) { by = ms; mt_y = mt; }
+    }
+    st = set_split_groups(c, best, mt_a, mt_y);
+  }
   if (st == PCF_OK && !c->fused) {
     // the solve alone over its own group sizes
     int best_s = c->sgrp_s;
@@ -1474,6 +1506,15 @@ pcf_status pcf_norm(pcf_ctx* c, const double* u, double* out) {
   k_norm_final<<<1, 32, 0, c->cs>>>(li_of(c, c->pre_inst), out);
   PCF_TRY(check_launch());
   return leave(c);
+}
+
+pcf_status pcf_split_config(const pcf_ctx* c, int* cfg) {
+  if (!c || !cfg) return PCF_EINVAL;
+  cfg[0] = c->split ? c->sgrp : 0;
+  cfg[1] = c->split ? c->smt : 0;
+  cfg[2] = c->split ? c->smt_y : 0;
+  cfg[3] = c->split && !c->fused ? c->sgrp_s : 0;
+  return PCF_OK;
 }
 
 long long pcf_launches_per_call(pcf_ctx* c, int nsteps) {
