@@ -37,7 +37,9 @@ struct TabLayout {
 //   v  = Av f_v + Ag g,   xi = Xv f_v + Xg g,   eta = Eh h,
 // with f_v the v right-hand side (class g), g = Re/Im part of i(kx f_u + kz f_w) and
 // h = Re/Im part of i(kz f_u - kx f_w) (class 1-g).  For the mean mode, Eh of group g is
-// the inverse Dirichlet Helmholtz operator of class g (applied to f_u and f_w).
+// the inverse Dirichlet Helmholtz operator of class g (applied to f_u and f_w).  The
+// kernels take xi = -dv/dy from v by the derivative recurrence (xi_from_v), the step of the
+// banded sweeps, and read only Av, Ag and Eh; Xv and Xg remain in the tables.
 constexpr int kDenseMaxN = 128;
 struct DenseLayout {
   int Mh;
@@ -171,6 +173,20 @@ PCF_HD void class_deriv(int N, int q, const double* __restrict__ a, const double
     d[j] = acc;
   }
   if (p == 0) d[0] *= 0.5;
+}
+
+// xi = -dv/dy from the class array v (parity pv, stride vs) into the class array xi (parity
+// 1 - pv, stride xs): class_deriv's recurrence with its 2(n+1) factors formed in place (exact
+// integers, so the operations and their results are those of class_deriv followed by the sign).
+PCF_HD void xi_from_v(int N, int pv, const double* __restrict__ v, int vs, double* __restrict__ xi, int xs) {
+  const int p = 1 - pv;
+  const int Md = (N - p) / 2 + 1;
+  double acc = 0.0;
+  for (int j = Md - 1; j >= 0; --j) {
+    const int n = p + 2 * j;
+    if (n + 1 <= N) acc += (double)(2 * (n + 1)) * v[((n + 1 - pv) / 2) * vs];
+    xi[j * xs] = (p == 0 && j == 0) ? -(acc * 0.5) : -acc;
+  }
 }
 
 // One chain of the per-mode Stokes solve: group g (v parity g), real (rho = 0) or

@@ -822,13 +822,7 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
           for (int j = 0; j < McP; ++j) a = fma(__ldg(rg + j * Mh), sc[j], a);
           sc[2 * Mh + r] = a;
         } else if (which == 1) {
-          if (r >= McP) continue;
-          const double* ra = D + DL.at(g, 2, r, 0);
-          const double* rg = D + DL.at(g, 3, r, 0);
-          double a = 0.0;
-          for (int j = 0; j < McV; ++j) a = fma(__ldg(ra + j * Mh), fv[j], a);
-          for (int j = 0; j < McP; ++j) a = fma(__ldg(rg + j * Mh), sc[j], a);
-          sc[3 * Mh + r] = a;
+          continue;  // xi = -dv/dy follows from v below
         } else {
           if (r >= McP) continue;
           const double* re = D + DL.at(g, 4, r, 0);
@@ -836,6 +830,15 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
           for (int j = 0; j < McP; ++j) a = fma(__ldg(re + j * Mh), sc[Mh + j], a);
           sc[4 * Mh + r] = a;
         }
+      }
+      __syncthreads();
+      // xi = -dv/dy (class 1-g) of every (mode, group, part) chain but the mean mode's
+      for (int t = threadIdx.x; t < nmod * 4; t += blockDim.x) {
+        const int mm = t >> 2, g = (t >> 1) & 1, rho = t & 1;
+        const int m = m0 + mm, ix = m / Mz, p = m - ix * Mz;
+        if (I.kx[ix] == 0.0 && I.kz[p] == 0.0) continue;
+        double* sc = Ch + ((size_t)mm * 4 + g * 2 + rho) * 6 * Mh;
+        xi_from_v(N, g, sc + 2 * Mh, 1, sc + 3 * Mh, 1);
       }
     } else {
     // Stokes step: 4 chains per mode (group x part)

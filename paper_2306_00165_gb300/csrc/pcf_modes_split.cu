@@ -224,15 +224,20 @@ __device__ __forceinline__ SolveItem solve_item(const GroupLaunch& gl, int item)
   return SolveItem{grp.x, grp.y, local >> 1, local & 1};
 }
 
-// Stage the five operator blocks of (mode m, parity group g) and the class-split right-hand
-// sides of the group's instances at mode m (6 (N+2) doubles each) into buf.
+// Stage the operator blocks Av, Ag and Eh of (mode m, parity group g) at their places in the
+// five-block layout (xi comes from v by the derivative recurrence, so Xv and Xg are not
+// read) and the class-split right-hand sides of the group's instances at mode m (6 (N+2)
+// doubles each) into buf.
 __device__ __forceinline__ void solve_stage(const GroupLaunch& gl, const SolveItem& it, int sig, double* buf) {
   const Inst& I0 = gl.insts[it.first];
   const int N = I0.N, Mh = N / 2 + 1, per = 6 * (N + 2);
   const DenseLayout DL(N);
-  const int n5 = 5 * Mh * Mh, n5p = (n5 + 1) & ~1;
+  const int MM = Mh * Mh, n5 = 5 * MM, n5p = (n5 + 1) & ~1;
   const double* src = I0.dense[sig] + (size_t)it.m * DL.per_mode() + DL.block(it.g, 0);
-  for (int t = threadIdx.x; t < n5; t += blockDim.x) cp_async8(buf + t, src + t);
+  for (int t = threadIdx.x; t < 3 * MM; t += blockDim.x) {
+    const int o = t < 2 * MM ? t : t + 2 * MM;  // blocks 0, 1, then 4
+    cp_async8(buf + o, src + o);
+  }
   double* fr = buf + n5p;
   const int hp = per / 2;
   for (int t = threadIdx.x; t < it.nI * hp; t += blockDim.x) {
@@ -320,14 +325,14 @@ __global__ void __launch_bounds__(kSolveThreads) k_ysolve(GroupLaunch gl, int op
     const int nU = mean ? nV : McP;
     const int nout = nV + 2 * nU;
     __syncthreads();
-    // v = Av f_v + Ag g, xi = Xv f_v + Xg g (row list A: v rows, then xi rows), eta = Eh h
-    // (row list B); mean mode: u = Eh f_u, w = Eh f_w (list A), no list B.  A task is one
-    // row of list A (McV + McP terms) or two rows of list B (McP terms each), so the tasks
-    // carry about the same work; warps hold RW rows of one list.  Each row is one fma chain
-    // in increasing j (the order of the single per-mode kernel, so the bits agree).
+    // v = Av f_v + Ag g (row list A), eta = Eh h (row list B); mean mode: u = Eh f_u,
+    // w = Eh f_w (list A), no list B.  A task is one row of list A (McV + McP terms) or two
+    // rows of list B (McP terms each), so the tasks carry about the same work; warps hold RW
+    // rows of one list.  Each row is one fma chain in increasing j (the order of the single
+    // per-mode kernel, so the bits agree).  xi = -dv/dy follows from v below.
     {
       const int Mc0 = (N - g) / 2 + 1;
-      const int nA = mean ? 2 * Mc0 : McV + McP, nB = mean ? 0 : McP;
+      const int nA = mean ? 2 * Mc0 : McV, nB = mean ? 0 : McP;
       const int hB = (nB + 1) / 2;
       const int PA = round_up(nA, RW), PB = round_up(hB, RW);
       for (int t = threadIdx.x; t < (PA + PB) * SP; t += blockDim.x) {
@@ -345,13 +350,11 @@ __global__ void __launch_bounds__(kSolveThreads) k_ysolve(GroupLaunch gl, int op
             for (int j = 0; j < Mc0; ++j) a = fma(col[j * Mh], X[j * XS], a);
             out = (isu ? OV : OX) + r * XS + sc;
           } else {
-            const bool isv = rs < McV;
-            const int rr = isv ? rs : rs - McV;
-            const double* cA = D + (isv ? 0 : 2) * MM + rr;  // Av or Xv
+            const double* cA = D + rs;       // Av
             for (int j = 0; j < McV; ++j) a = fma(cA[j * Mh], FV[j * XS + sc], a);
-            const double* cG = cA + MM;                       // Ag or Xg
+            const double* cG = cA + MM;      // Ag
             for (int j = 0; j < McP; ++j) a = fma(cG[j * Mh], GG[j * XS + sc], a);
-            out = (isv ? OV : OX) + rr * XS + sc;
+            out = OV + rs * XS + sc;
           }
           *out = a;
         } else {
@@ -372,6 +375,10 @@ __global__ void __launch_bounds__(kSolveThreads) k_ysolve(GroupLaunch gl, int op
       }
     }
     __syncthreads();
+    if (!mean) {  // xi = -dv/dy (class 1-g), one column per thread
+      for (int s = threadIdx.x; s < SP; s += blockDim.x) xi_from_v(N, pv, OV + s, XS, OX + s, XS);
+      __syncthreads();
+    }
     // assembly and output: v (class g) and u, w (class 1-g); mean mode: u, v = 0, w (class g)
     const double inv_step = op == MODE_PHI ? I0.inv_dt : I0.inv_dtau_hat;
     const double ik2 = ik2_sh;
@@ -679,8 +686,9 @@ __global__ void __launch_bounds__(kStepThreads) k_ystep(GroupLaunch gl, int op) 
     }
     __syncthreads();
     {
+      // list A: v rows (Av f_v + Ag g; xi = -dv/dy follows below); mean mode: u and w rows
       const int Mc0 = (N - g) / 2 + 1;
-      const int nA = mean ? 2 * Mc0 : McV + McP, nB = mean ? 0 : McP;
+      const int nA = mean ? 2 * Mc0 : McV, nB = mean ? 0 : McP;
       const int hA = (nA + 1) / 2, hB = (nB + 1) / 2;
       const int PA = round_up(hA, RW), PB = round_up(hB, RW);
       for (int t = threadIdx.x; t < (PA + PB) * SP; t += blockDim.x) {
@@ -702,24 +710,22 @@ __global__ void __launch_bounds__(kStepThreads) k_ystep(GroupLaunch gl, int op) 
             out0 = OV + r0 * XS + sc;
             out1 = OX + (v1 ? r1 - Mc0 : 0) * XS + sc;
           } else {
-            const bool isv0 = r0 < McV, isv1 = r1 < McV;
-            const int rr0 = isv0 ? r0 : r0 - McV, rr1 = isv1 ? r1 : r1 - McV;
-            const double* cA0 = Dg + (isv0 ? 0 : 2) * MM + rr0;
-            const double* cA1 = Dg + (isv1 ? 0 : 2) * MM + rr1;
+            const double* cA0 = Dg + r0;  // Av
+            const double* cA1 = Dg + r1;
             for (int j = 0; j < McV; ++j) {
               const double x = FV[j * XS + sc];
               a0 = fma(cA0[j * Mh], x, a0);
               a1 = fma(cA1[j * Mh], x, a1);
             }
-            const double* cG0 = cA0 + MM;
+            const double* cG0 = cA0 + MM;  // Ag
             const double* cG1 = cA1 + MM;
             for (int j = 0; j < McP; ++j) {
               const double x = GG[j * XS + sc];
               a0 = fma(cG0[j * Mh], x, a0);
               a1 = fma(cG1[j * Mh], x, a1);
             }
-            out0 = (isv0 ? OV : OX) + rr0 * XS + sc;
-            out1 = (isv1 ? OV : OX) + rr1 * XS + sc;
+            out0 = OV + r0 * XS + sc;
+            out1 = OV + r1 * XS + sc;
           }
         } else {
           const int q = rs - PA;
@@ -741,6 +747,10 @@ __global__ void __launch_bounds__(kStepThreads) k_ystep(GroupLaunch gl, int op) 
       }
     }
     __syncthreads();
+    if (!mean) {  // xi = -dv/dy (class 1-g), one column per thread
+      for (int s = threadIdx.x; s < SP; s += blockDim.x) xi_from_v(N, pv, OV + s, XS, OX + s, XS);
+      __syncthreads();
+    }
     // assembly: v (class g) and u, w (class 1-g); mean mode: u, v = 0, w (class g)
     const int nV = mean ? (N - g) / 2 + 1 : McV;
     const int nU = mean ? nV : McP;
