@@ -224,21 +224,21 @@ __device__ __forceinline__ SolveItem solve_item(const GroupLaunch& gl, int item)
   return SolveItem{grp.x, grp.y, local >> 1, local & 1};
 }
 
-// Stage the operator blocks Av, Ag and Eh of (mode m, parity group g) at their places in the
-// five-block layout (xi comes from v by the derivative recurrence, so Xv and Xg are not
-// read) and the class-split right-hand sides of the group's instances at mode m (6 (N+2)
-// doubles each) into buf.
+// Stage the operator blocks Av, Ag and Eh of (mode m, parity group g), packed in that order
+// (xi comes from v by the derivative recurrence, so Xv and Xg are not read), and the
+// class-split right-hand sides of the group's instances at mode m (6 (N+2) doubles each)
+// into buf.
 __device__ __forceinline__ void solve_stage(const GroupLaunch& gl, const SolveItem& it, int sig, double* buf) {
   const Inst& I0 = gl.insts[it.first];
   const int N = I0.N, Mh = N / 2 + 1, per = 6 * (N + 2);
   const DenseLayout DL(N);
-  const int MM = Mh * Mh, n5 = 5 * MM, n5p = (n5 + 1) & ~1;
+  const int MM = Mh * Mh, n3p = (3 * MM + 1) & ~1;
   const double* src = I0.dense[sig] + (size_t)it.m * DL.per_mode() + DL.block(it.g, 0);
   for (int t = threadIdx.x; t < 3 * MM; t += blockDim.x) {
-    const int o = t < 2 * MM ? t : t + 2 * MM;  // blocks 0, 1, then 4
-    cp_async8(buf + o, src + o);
+    const int o = t < 2 * MM ? t : t + 2 * MM;  // blocks 0, 1, then 4 of the layout
+    cp_async8(buf + t, src + o);
   }
-  double* fr = buf + n5p;
+  double* fr = buf + n3p;
   const int hp = per / 2;
   for (int t = threadIdx.x; t < it.nI * hp; t += blockDim.x) {
     const int i = t / hp, k = t - i * hp;
@@ -285,8 +285,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_ysolve(GroupLaunch gl, int op
     const double kx = I0.kx[ix], kz = I0.kz[p];
     const bool mean = kx == 0.0 && kz == 0.0;
     const int MM = Mh * Mh, per = 6 * L2;
-    const double* D = buf;                          // [5][Mh][Mh] operator blocks of group g
-    const double* FR = buf + ((5 * MM + 1) & ~1);   // [nI][3][2][L2] right-hand sides
+    const double* D = buf;                          // [3][Mh][Mh] blocks Av, Ag, Eh of group g
+    const double* FR = buf + ((3 * MM + 1) & ~1);   // [nI][3][2][L2] right-hand sides
     double* FV = sm + 2 * (size_t)bufsz;            // [Mh][XS] f_v (class g); mean mode: f_u (class g)
     double* GG = FV + scr_rows * XS;                // [Mh][XS] g (class 1-g);   mean mode: f_w (class g)
     double* HH = GG + scr_rows * XS;                // [Mh][XS] h (class 1-g)
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_ysolve(GroupLaunch gl, int op
             // rows < Mc0: u from f_u; rows >= Mc0: w from f_w (both with Eh)
             const bool isu = rs < Mc0;
             const int r = isu ? rs : rs - Mc0;
-            const double* col = D + 4 * MM + r;
+            const double* col = D + 2 * MM + r;
             const double* X = (isu ? FV : GG) + sc;
             for (int j = 0; j < Mc0; ++j) a = fma(col[j * Mh], X[j * XS], a);
             out = (isu ? OV : OX) + r * XS + sc;
@@ -361,8 +361,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_ysolve(GroupLaunch gl, int op
           const int q = rs - PA;
           const bool v0 = q < hB, v1 = v0 && q + hB < nB;
           const int r0 = v0 ? q : 0, r1 = v1 ? q + hB : 0;
-          const double* c0 = D + 4 * MM + r0;
-          const double* c1 = D + 4 * MM + r1;
+          const double* c0 = D + 2 * MM + r0;
+          const double* c1 = D + 2 * MM + r1;
           double a0 = 0.0, a1 = 0.0;
           for (int j = 0; j < McP; ++j) {
             const double x = HH[j * XS + sc];
@@ -865,8 +865,8 @@ size_t smem_yanalysis(int N, int G, int mt) {
 }
 // Stage buffer of the persistent solve (doubles): operator blocks + right-hand sides of G instances.
 size_t ysolve_buffer(int N, int G) {
-  const size_t Mh = N / 2 + 1, n5p = (5 * Mh * Mh + 1) & ~(size_t)1;
-  return n5p + (size_t)G * 6 * (N + 2);
+  const size_t Mh = N / 2 + 1, n3p = (3 * Mh * Mh + 1) & ~(size_t)1;
+  return n3p + (size_t)G * 6 * (N + 2);
 }
 size_t smem_ysolve(int N, int G) {
   const size_t Mh = N / 2 + 1, XS = col_pad_host(G) + 1;
