@@ -158,6 +158,26 @@ def _dist():
     return None, 0, 1
 
 
+def rank_seeds(rank, batch=BATCH):
+    """Seeds of the guesses rank `rank` runs: disjoint across ranks (replicas, weak scaling)."""
+    return list(range(rank * batch, rank * batch + batch))
+
+
+def reduce_max(dist, x, dev):
+    """Maximum of x over the ranks (x itself without a process group)."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(batch, ws, steps, seconds):
+    """Whole-job gradient evaluations per second: every rank's instances over the slowest rank's time."""
+    return batch * ws * steps / seconds
+
+
 def _oracle_sample(seconds, out_path):
     """Runs in a fresh process: oracle descent steps on one streak/roll guess until `seconds`."""
     os.environ.setdefault("OMP_NUM_THREADS", "1")
@@ -411,7 +431,7 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    seeds = list(range(rank * BATCH, rank * BATCH + BATCH))
+    seeds = rank_seeds(rank)
     u0 = gi.batch(gi.streak_roll, seeds, *GRID)
     s = pcf.Solver(*GRID, batch=BATCH, Re=RE, dt=DT, dtau_hat=DTAU_HAT, modes_per_block=args.mode_tile)
     u = torch.from_numpy(u0).to(dev)
@@ -443,12 +463,8 @@ def run_ours(args):
     if dist:
         dist.barrier()
     ck = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = BATCH * ws * args.steps / (ms * 1e-3)
+    ms = reduce_max(dist, sum(a.elapsed_time(b) for a, b in zip(starts, ends)), dev)
+    value = aggregate_value(BATCH, ws, args.steps, ms * 1e-3)
     J_last = torch.cat(hist).cpu().numpy()[-1]
 
     # e2e: host buffers through the C ABI, copies inside the timed region
@@ -461,8 +477,8 @@ def run_ours(args):
     ne = max(10, args.steps)
     for _ in range(ne):
         s.descent_step_host(uh, DTAU, 1, hh)
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": BATCH * ws * ne / e2e_s, "unit": "gradient evals/s",
+    e2e_s = reduce_max(dist, time.perf_counter() - t0, dev)
+    e2e = {"value": aggregate_value(BATCH, ws, ne, e2e_s), "unit": "gradient evals/s",
            "h2d_bytes_per_step": uh.numel() * uh.element_size(),
            "d2h_bytes_per_step": uh.numel() * uh.element_size() + hh.numel() * hh.element_size()}
 
