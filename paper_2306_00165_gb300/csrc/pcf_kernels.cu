@@ -361,19 +361,24 @@ __global__ void __launch_bounds__(128, PCF_XZ_MINB) k_xzsynth_t(LaunchInfo li, i
   const int LX = pp.LX, LZ = pp.LZ;
   const typename Sto<T>::c* src = yv_of<T>(I) + (((size_t)slot * kFieldsY + c_src[f]) * I.ny + j) * (size_t)I.nmodes;
   const int fac = c_fac[f];
-  // x stage: batch p (retained z mode), element = x bin; the first pass reads the y-values
-  // (times i kx or i kz for the x and z derivatives); bins outside |m| <= Kx are zero
-  const auto ldx = [&](int p, int bin) -> C {
-    const int i = bin <= Kx ? bin : (bin >= nx - Kx ? Mx - (nx - bin) : -1);
-    C s = Cx<T>::mk(0, 0);
-    if (i >= 0) {
-      s = load_c<T>(src[i * Mz + p]);
-      if (fac == 1) { const T k = (T)I.kx[i]; s = Cx<T>::mk(-k * s.y, k * s.x); }
-      else if (fac == 2) { const T k = (T)I.kz[p]; s = Cx<T>::mk(-k * s.y, k * s.x); }
-    }
+  // x stage: batch p (retained z mode), element = x bin; the input is the y-values (times
+  // i kx or i kz for the x and z derivatives); bins outside |m| <= Kx are zero
+  const auto scaled = [&](C s, int i, int p) -> C {
+    if (fac == 1) { const T k = (T)I.kx[i]; s = Cx<T>::mk(-k * s.y, k * s.x); }
+    else if (fac == 2) { const T k = (T)I.kz[p]; s = Cx<T>::mk(-k * s.y, k * s.x); }
     return s;
   };
-  C* G = fft_run_io<false, C>(B0, B1, nx, LX, Mz, I.rx, I.nrx, twx, true, ldx, SmemSt<C>{nullptr, 0});
+  // the y-values, converted and scaled once per mode in a coalesced loop, at their bins in B0
+  // (the other bins are never read: the first pass returns zero for them)
+  for (int t = threadIdx.x; t < I.nmodes; t += blockDim.x) {
+    const int i = t / Mz, p = t - i * Mz;
+    B0[p * LX + xbin(i, Kx, Mx, nx)] = scaled(load_c<T>(src[t]), i, p);
+  }
+  __syncthreads();
+  const auto ldx = [&](int p, int bin) -> C {
+    return (bin <= Kx || bin >= nx - Kx) ? B0[p * LX + bin] : Cx<T>::mk(0, 0);
+  };
+  C* G = fft_run_io<false, C>(B1, B0, nx, LX, Mz, I.rx, I.nrx, twx, true, ldx, SmemSt<C>{nullptr, 0});
   __syncthreads();
   C* Zb = (G == B0) ? B1 : B0;
   const int nr = nx / 2;
