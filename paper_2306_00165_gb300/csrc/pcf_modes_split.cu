@@ -33,7 +33,15 @@
 
 namespace pcf {
 
-constexpr int kSplitThreads = 128;
+// Threads per CTA of the split synthesis and analysis kernels.
+#ifndef PCF_SPLIT_THREADS
+#define PCF_SPLIT_THREADS 128
+#endif
+#ifndef PCF_ANALYSIS_THREADS
+#define PCF_ANALYSIS_THREADS 256
+#endif
+constexpr int kSplitThreads = PCF_SPLIT_THREADS;
+constexpr int kAnalysisThreads = PCF_ANALYSIS_THREADS;
 constexpr int kSolveThreads = 256;
 constexpr int kMaxGroup = 8;  // instances per group (16 columns)
 
@@ -106,7 +114,7 @@ __device__ __forceinline__ void group_flags(const GroupLaunch& gl, int first, in
 
 // A: arithmetic of the Chebyshev dot products (double, or ff in the float-float form)
 template <class A>
-__global__ void __launch_bounds__(kSplitThreads) k_yanalysis(GroupLaunch gl, int op, int mt) {
+__global__ void __launch_bounds__(kAnalysisThreads) k_yanalysis(GroupLaunch gl, int op, int mt) {
   extern __shared__ double sm[];
   __shared__ int live[kMaxGroup];
   int local;
@@ -877,8 +885,8 @@ size_t smem_ysynth(int N, int G, int mt) {
   return sizeof(double) * (2 * H * H + (2 * H) * XS);
 }
 void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith, int mt) {
-  if (ff_arith) k_yanalysis<ff><<<ctas, kSplitThreads, smem, s>>>(gl, op, mt);
-  else k_yanalysis<double><<<ctas, kSplitThreads, smem, s>>>(gl, op, mt);
+  if (ff_arith) k_yanalysis<ff><<<ctas, kAnalysisThreads, smem, s>>>(gl, op, mt);
+  else k_yanalysis<double><<<ctas, kAnalysisThreads, smem, s>>>(gl, op, mt);
 }
 void launch_ysolve(int ctas, int nitems, int bufsz, int scr_rows, size_t smem, cudaStream_t s, GroupLaunch gl,
                    int op) {
