@@ -42,7 +42,10 @@ namespace pcf {
 #endif
 constexpr int kSplitThreads = PCF_SPLIT_THREADS;
 constexpr int kAnalysisThreads = PCF_ANALYSIS_THREADS;
-constexpr int kSolveThreads = 256;
+#ifndef PCF_SOLVE_THREADS
+#define PCF_SOLVE_THREADS 128
+#endif
+constexpr int kSolveThreads = PCF_SOLVE_THREADS;  // threads per CTA of the persistent solve
 constexpr int kMaxGroup = 8;  // instances per group (16 columns)
 
 // frg of one instance: [mode][3][2][L2] doubles, L2 = 2 (N/2 + 1); class-split (even n at
@@ -504,9 +507,9 @@ int split_ctas_per_group(int kind, int nmodes, int mt) {
   const int tiles = (nmodes + mt - 1) / mt;
   return kind == 0 ? 3 * tiles : kind == 1 ? 2 * nmodes : kFieldsY * tiles;
 }
-// Largest group on a grid: kMaxGroup, and the solve's four outputs per thread
-// (G (N/2 + 1) 3 <= 4 kSolveThreads).
-int split_max_group(int N) { return std::min(kMaxGroup, 4 * kSolveThreads / (3 * (N / 2 + 1))); }
+// Largest group on a grid: kMaxGroup (every loop of the split kernels strides over its
+// tasks; shared memory is checked where the groups are set).
+int split_max_group(int) { return kMaxGroup; }
 static size_t col_pad_host(int G) {
   size_t sp = 2;
   while (sp < 2 * (size_t)G) sp <<= 1;
