@@ -169,9 +169,9 @@ void launch_cheb_analysis_tc(int ctas, size_t smem, cudaStream_t s, LaunchInfo l
   k_cheb_analysis_tc<<<ctas, kTcThreads, smem, s>>>(li);
 }
 cudaError_t set_cheb_tc_smem(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_cheb_synth_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)k_cheb_synth_tc, smem);
   if (e) return e;
-  return cudaFuncSetAttribute(k_cheb_analysis_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return raise_smem_limit((const void*)k_cheb_analysis_tc, smem);
 }
 int cheb_tc_tiles(int nmodes) { return (2 * nmodes + kTcCols - 1) / kTcCols; }
 

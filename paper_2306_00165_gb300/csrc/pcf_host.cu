@@ -244,7 +244,7 @@ std::vector<double> make_dense_tables(int N, const std::vector<double>& kx, cons
             e[j] = 1.0;
             tau_solve(Mc, s, s + Mh, s + 2 * Mh, s + 3 * Mh, s[4 * Mh], rco.data() + RL.off(g, 0),
                       rco.data() + RL.off(g, 1), rco.data() + RL.off(g, 2), e.data(), 0.0, y.data());
-            for (int r = 0; r < Mc; ++r) d[DL.at(g, 4, r, j)] = y[r];
+            for (int r = 0; r < Mc; ++r) d[DL.at(g, DL.kEh, r, j)] = y[r];
           }
           continue;
         }
@@ -263,8 +263,7 @@ std::vector<double> make_dense_tables(int N, const std::vector<double>& kx, cons
             }
             std::fill(sc.begin(), sc.end(), 0.0);
             mode_chain(N, g, 0, kx[i], kz[p], sigma + k2, tab, rco.data(), Fr.data(), L2, sc.data());
-            for (int r = 0; r < McV; ++r) d[DL.at(g, src == 0 ? 0 : 1, r, j)] = sc[2 * Mh + r];
-            for (int r = 0; r < McP; ++r) d[DL.at(g, src == 0 ? 2 : 3, r, j)] = sc[3 * Mh + r];
+            for (int r = 0; r < McV; ++r) d[DL.at(g, src == 0 ? DL.kAv : DL.kAg, r, j)] = sc[2 * Mh + r];
           }
         }
         // eta: inverse Helmholtz of class pP
@@ -275,7 +274,7 @@ std::vector<double> make_dense_tables(int N, const std::vector<double>& kx, cons
           e[j] = 1.0;
           tau_solve(McP, s, s + Mh, s + 2 * Mh, s + 3 * Mh, s[4 * Mh], rco.data() + RL.off(pP, 0),
                     rco.data() + RL.off(pP, 1), rco.data() + RL.off(pP, 2), e.data(), 0.0, y.data());
-          for (int r = 0; r < McP; ++r) d[DL.at(g, 4, r, j)] = y[r];
+          for (int r = 0; r < McP; ++r) d[DL.at(g, DL.kEh, r, j)] = y[r];
         }
       }
     }
@@ -732,7 +731,7 @@ static pcf_status set_mode_tiles(pcf_ctx* c, int want) {
   c->mpc = want;
   c->sm_mode = sm;
   PCF_TRY(upload_prefix(c, per, &c->pre_mode, &c->cta_mode));
-  PCF_CUDA(cudaFuncSetAttribute(k_mode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->sm_mode));
+  PCF_CUDA(raise_smem_limit((const void*)k_mode, c->sm_mode));
   return PCF_OK;
 }
 
@@ -839,8 +838,9 @@ static pcf_status set_split_groups(pcf_ctx* c, int G, int mt = 1, int mt_y = 0) 
   return set_solve_groups(c, G);
 }
 
-// Autotuner of the split mode kernels: time analysis + solve + synthesis of the NSE Stokes
-// step on the batch for each candidate group size and keep the fastest.
+// Autotuner of the split mode kernels: time the per-mode work of a whole step (analysis,
+// solve and synthesis of both half-steps, or the fused kernel twice and the norm kernel) on
+// the batch for each candidate group size, mode tile and organisation, and keep the fastest.
 static pcf_status autotune_split(pcf_ctx* c) {
   const int cand[] = {1, 2, 4, 6, 8};
   cudaEvent_t a, b;
@@ -859,14 +859,21 @@ static pcf_status autotune_split(pcf_ctx* c) {
       for (int fuse = 0; fuse < 2; ++fuse) {
         if (fuse && (mt > 1 || c->sm_yf > 227 * 1024)) continue;  // the fused kernel has no mode tile
         if ((c->prm.solve_kind == 3 && fuse) || (c->prm.solve_kind == 4 && !fuse)) continue;
+        // the per-mode work of a whole step in each organisation (both half-steps; the fused
+        // path also launches the separate norm kernel)
         auto seq = [&] {
           if (fuse) {
             launch_ystep(c->cta_yf, c->sm_yf, c->cs, gl_of(c, c->pre_yf), MODE_PHI);
+            launch_jnorm(c->B, c->cs, c->dinst, 0);
+            launch_ystep(c->cta_yf, c->sm_yf, c->cs, gl_of(c, c->pre_yf), MODE_PSI_UPDATE);
             return;
           }
-          launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), MODE_PHI, c->plane_kind == 2, c->smt);
-          launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_solve(c), MODE_PHI);
-          launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), 1, 1, c->plane_kind == 2, c->smt_y);
+          for (int op : {(int)MODE_PHI, (int)MODE_PSI_UPDATE}) {
+            launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), op, c->plane_kind == 2, c->smt);
+            launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_solve(c), op);
+            launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), op == MODE_PHI ? 1 : 0, 1,
+                                c->plane_kind == 2, c->smt_y);
+          }
         };
         seq();
         PCF_CUDA(cudaEventRecord(a, c->cs));

@@ -32,21 +32,22 @@ struct TabLayout {
 };
 
 // Dense form of the same per-mode solve (used for N <= kDenseMaxN): for each parity group g
-// five Mh x Mh column-major blocks (element (r, j) at block + j Mh + r, so that threads
+// three Mh x Mh column-major blocks (element (r, j) at block + j Mh + r, so that threads
 // computing consecutive rows read consecutive addresses) mapping the group's inputs to its outputs,
-//   v  = Av f_v + Ag g,   xi = Xv f_v + Xg g,   eta = Eh h,
+//   v  = Av f_v + Ag g,   eta = Eh h,
 // with f_v the v right-hand side (class g), g = Re/Im part of i(kx f_u + kz f_w) and
 // h = Re/Im part of i(kz f_u - kx f_w) (class 1-g).  For the mean mode, Eh of group g is
-// the inverse Dirichlet Helmholtz operator of class g (applied to f_u and f_w).  The
-// kernels take xi = -dv/dy from v by the derivative recurrence (xi_from_v), the step of the
-// banded sweeps, and read only Av, Ag and Eh; Xv and Xg remain in the tables.
+// the inverse Dirichlet Helmholtz operator of class g (applied to f_u and f_w).
+// xi = -dv/dy follows from v by the derivative recurrence (xi_from_v), the step of the
+// banded sweeps.
 constexpr int kDenseMaxN = 128;
 struct DenseLayout {
   int Mh;
+  enum { kAv = 0, kAg = 1, kEh = 2 };
   PCF_HD DenseLayout(int N) : Mh(N / 2 + 1) {}
-  PCF_HD int block(int g, int k) const { return (g * 5 + k) * Mh * Mh; }  // k: 0 Av 1 Ag 2 Xv 3 Xg 4 Eh
+  PCF_HD int block(int g, int k) const { return (g * 3 + k) * Mh * Mh; }
   PCF_HD int at(int g, int k, int r, int j) const { return block(g, k) + j * Mh + r; }
-  PCF_HD int per_mode() const { return 10 * Mh * Mh; }
+  PCF_HD int per_mode() const { return 6 * Mh * Mh; }
 };
 
 // Shared (N-dependent) coefficient table, doubles, each array of length Mh:

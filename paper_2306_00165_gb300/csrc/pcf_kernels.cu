@@ -13,10 +13,28 @@
 // kernels on one y-plane of one field (or product component) per CTA.  All arithmetic is
 // FP64; the FP64 pipe is the bound on GB300, so the transforms are radix-4/2/3 Stockham
 // FFTs in shared memory (x, z) and parity-folded dense Chebyshev matrices (y).
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "pcf_ff.cuh"
 #include "pcf_kernels.cuh"
 
 namespace pcf {
+
+cudaError_t raise_smem_limit(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> limit;  // (kernel, device) -> bytes set
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limit[std::make_pair(func, dev)];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 
 // ------------------------------------------------------------------ helpers
 
@@ -633,9 +651,9 @@ void launch_norm_planes(int kind, int ctas, cudaStream_t s, LaunchInfo li, int s
 template <class T>
 static cudaError_t set_plane_smem_t(size_t synth, size_t prod) {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_xzsynth_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)synth))) return e;
-  if ((e = cudaFuncSetAttribute(k_prod_t<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prod))) return e;
-  return cudaFuncSetAttribute(k_prod_t<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prod);
+  if ((e = raise_smem_limit((const void*)k_xzsynth_t<T>, synth))) return e;
+  if ((e = raise_smem_limit((const void*)k_prod_t<T, false>, prod))) return e;
+  return raise_smem_limit((const void*)k_prod_t<T, true>, prod);
 }
 cudaError_t set_plane_smem(int kind, size_t synth, size_t prod) {
   if (kind == 1) return set_plane_smem_t<float>(synth, prod);
@@ -810,7 +828,7 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
           // mean mode: u (which 0) and w (which 1) of class g
           const int Mc = (N - g) / 2 + 1;
           if (which == 2 || r >= Mc) continue;
-          const double* col = D + DL.at(g, 4, r, 0);
+          const double* col = D + DL.at(g, DL.kEh, r, 0);
           const double* f = fr + ((which == 0 ? 0 : 2) * 2 + rho) * L2 + g * Mh;
           double a = 0.0;
           for (int j = 0; j < Mc; ++j) a = fma(__ldg(col + j * Mh), f[j], a);
@@ -820,8 +838,8 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
         const double* fv = fr + (1 * 2 + rho) * L2 + pv * Mh;
         if (which == 0) {
           if (r >= McV) continue;
-          const double* ra = D + DL.at(g, 0, r, 0);
-          const double* rg = D + DL.at(g, 1, r, 0);
+          const double* ra = D + DL.at(g, DL.kAv, r, 0);
+          const double* rg = D + DL.at(g, DL.kAg, r, 0);
           double a = 0.0;
           for (int j = 0; j < McV; ++j) a = fma(__ldg(ra + j * Mh), fv[j], a);
           for (int j = 0; j < McP; ++j) a = fma(__ldg(rg + j * Mh), sc[j], a);
@@ -830,7 +848,7 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
           continue;  // xi = -dv/dy follows from v below
         } else {
           if (r >= McP) continue;
-          const double* re = D + DL.at(g, 4, r, 0);
+          const double* re = D + DL.at(g, DL.kEh, r, 0);
           double a = 0.0;
           for (int j = 0; j < McP; ++j) a = fma(__ldg(re + j * Mh), sc[Mh + j], a);
           sc[4 * Mh + r] = a;

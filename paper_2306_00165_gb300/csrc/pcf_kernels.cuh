@@ -62,6 +62,11 @@ __device__ __forceinline__ double norm_from_parts(const Inst& I) {
   return sqrt(0.5 * I.inv_nxnz * s);
 }
 
+// Raise the maximum dynamic shared memory of kernel func on the current device to at least
+// bytes.  The attribute belongs to the function, not to a context, so it only ever grows: a
+// context that needs less must not lower the limit another context launches with.
+cudaError_t raise_smem_limit(const void* func, size_t bytes);
+
 // kind: plane arithmetic, 0 FP64, 1 FP32 (mixed form), 2 float-float
 void launch_xzsynth(int kind, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int slot, int nf);
 // step_index >= 0 (adjoint product only): the last CTA of each instance also computes J from

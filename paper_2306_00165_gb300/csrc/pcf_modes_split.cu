@@ -235,20 +235,15 @@ __device__ __forceinline__ SolveItem solve_item(const GroupLaunch& gl, int item)
   return SolveItem{grp.x, grp.y, local >> 1, local & 1};
 }
 
-// Stage the operator blocks Av, Ag and Eh of (mode m, parity group g), packed in that order
-// (xi comes from v by the derivative recurrence, so Xv and Xg are not read), and the
-// class-split right-hand sides of the group's instances at mode m (6 (N+2) doubles each)
-// into buf.
+// Stage the operator blocks Av, Ag and Eh of (mode m, parity group g) and the class-split
+// right-hand sides of the group's instances at mode m (6 (N+2) doubles each) into buf.
 __device__ __forceinline__ void solve_stage(const GroupLaunch& gl, const SolveItem& it, int sig, double* buf) {
   const Inst& I0 = gl.insts[it.first];
   const int N = I0.N, Mh = N / 2 + 1, per = 6 * (N + 2);
   const DenseLayout DL(N);
   const int MM = Mh * Mh, n3p = (3 * MM + 1) & ~1;
   const double* src = I0.dense[sig] + (size_t)it.m * DL.per_mode() + DL.block(it.g, 0);
-  for (int t = threadIdx.x; t < 3 * MM; t += blockDim.x) {
-    const int o = t < 2 * MM ? t : t + 2 * MM;  // blocks 0, 1, then 4 of the layout
-    cp_async8(buf + t, src + o);
-  }
+  for (int t = threadIdx.x; t < 3 * MM; t += blockDim.x) cp_async8(buf + t, src + t);
   double* fr = buf + n3p;
   const int hp = per / 2;
   for (int t = threadIdx.x; t < it.nI * hp; t += blockDim.x) {
@@ -534,7 +529,7 @@ __host__ __device__ inline StepLayout step_layout(int N, int SP) {
   StepLayout L;
   L.cheb = 0;
   L.dense = L.cheb + ((6 * H * H + 1) & ~1);
-  L.v = L.dense + ((10 * H * H + 1) & ~1);
+  L.v = L.dense + ((6 * H * H + 1) & ~1);
   L.fr = L.v + 3 * 2 * H * XS;
   L.st = L.fr + (SP / 2) * 6 * L2;
   L.uh = L.st + 3 * ny * XS;
@@ -560,7 +555,7 @@ __global__ void __launch_bounds__(kStepThreads) k_ystep(GroupLaunch gl, int op) 
   const ChebLayout CL(N);
   const StepLayout SL = step_layout(N, SP);
   double* CH = sm + SL.cheb;   // Chebyshev tables (Ce Co De Do Ae Ao)
-  double* D = sm + SL.dense;   // the 10 operator blocks of mode m
+  double* D = sm + SL.dense;   // the 6 operator blocks of mode m (3 per parity group)
   double* V = sm + SL.v;       // [3][2H][XS] folded product values: P rows 0..H-1, Q rows H..H+N/2-1
   double* FR = sm + SL.fr;     // [SP/2][3][2][L2] right-hand sides (class-split)
   double* ST = sm + SL.st;     // [3][ny][XS] state of the step (uhat for PHI, rhat = r1 for PSI)
@@ -570,7 +565,7 @@ __global__ void __launch_bounds__(kStepThreads) k_ystep(GroupLaunch gl, int op) 
   // read-only tables, asynchronously
   {
     const double* src = I0.dense[sig] + (size_t)m * DL.per_mode();
-    for (int t = threadIdx.x; t < 10 * Mh * Mh; t += blockDim.x) cp_async8(D + t, src + t);
+    for (int t = threadIdx.x; t < DL.per_mode(); t += blockDim.x) cp_async8(D + t, src + t);
     for (int t = threadIdx.x; t < CL.total(); t += blockDim.x) cp_async8(CH + t, I0.cheb + t);
     cp_commit();
   }
@@ -712,8 +707,8 @@ __global__ void __launch_bounds__(kStepThreads) k_ystep(GroupLaunch gl, int op) 
           v1 = v0 && rs + hA < nA;
           const int r0 = v0 ? rs : 0, r1 = v1 ? rs + hA : 0;
           if (mean) {
-            const double* col0 = Dg + 4 * MM + r0;
-            const double* col1 = Dg + 4 * MM + (v1 ? r1 - Mc0 : 0);
+            const double* col0 = Dg + 2 * MM + r0;  // Eh
+            const double* col1 = Dg + 2 * MM + (v1 ? r1 - Mc0 : 0);
             for (int j = 0; j < Mc0; ++j) {
               a0 = fma(col0[j * Mh], FV[j * XS + sc], a0);
               a1 = fma(col1[j * Mh], GG[j * XS + sc], a1);
@@ -743,8 +738,8 @@ __global__ void __launch_bounds__(kStepThreads) k_ystep(GroupLaunch gl, int op) 
           v0 = q < hB;
           v1 = v0 && q + hB < nB;
           const int r0 = v0 ? q : 0, r1 = v1 ? q + hB : 0;
-          const double* c0 = Dg + 4 * MM + r0;
-          const double* c1 = Dg + 4 * MM + r1;
+          const double* c0 = Dg + 2 * MM + r0;  // Eh
+          const double* c1 = Dg + 2 * MM + r1;
           for (int j = 0; j < McP; ++j) {
             const double x = HV[j * XS + sc];
             a0 = fma(c0[j * Mh], x, a0);
@@ -867,7 +862,7 @@ void launch_ystep(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op)
   k_ystep<<<ctas, kStepThreads, smem, s>>>(gl, op);
 }
 cudaError_t set_ystep_smem(size_t smem) {
-  return cudaFuncSetAttribute(k_ystep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return raise_smem_limit((const void*)k_ystep, smem);
 }
 
 size_t smem_yanalysis(int N, int G, int mt) {
@@ -910,12 +905,11 @@ void launch_ysynth_split(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, 
 }
 cudaError_t set_split_smem(size_t analysis, size_t solve, size_t synth) {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_yanalysis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)analysis)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_yanalysis<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)analysis))) return e;
-  if ((e = cudaFuncSetAttribute(k_ysolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve))) return e;
-  if ((e = cudaFuncSetAttribute(k_ysynth<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)synth))) return e;
-  return cudaFuncSetAttribute(k_ysynth<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)synth);
+  if ((e = raise_smem_limit((const void*)k_yanalysis<double>, analysis))) return e;
+  if ((e = raise_smem_limit((const void*)k_yanalysis<ff>, analysis))) return e;
+  if ((e = raise_smem_limit((const void*)k_ysolve, solve))) return e;
+  if ((e = raise_smem_limit((const void*)k_ysynth<double>, synth))) return e;
+  return raise_smem_limit((const void*)k_ysynth<ff>, synth);
 }
 
 }  // namespace pcf

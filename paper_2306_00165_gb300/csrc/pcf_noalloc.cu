@@ -245,11 +245,9 @@ extern "C" pcf_status pcf_influence_matrix_solve_noalloc(const pcf_params* prm, 
   while (mpc > 1 && smem_mode(I, mpc) > 110 * 1024) --mpc;
   const size_t smem = smem_mode(I, mpc);
   if (smem > 227 * 1024) return PCF_EINVAL;
-  // a limit, not an allocation; set on every call because a context created in between
-  // may have lowered it to its own size
-  if (cudaFuncSetAttribute(k_mode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess &&
-      cudaFuncSetAttribute(k_mode, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
-    return PCF_ECUDA;
+  // a limit, not an allocation; it only ever grows, so this call cannot lower the limit a
+  // context launches the same kernel with
+  if (raise_smem_limit((const void*)k_mode, smem) != cudaSuccess) return PCF_ECUDA;
   k_noalloc_setup_shared<<<1, 256, 0, s>>>(I, base, L, prm->Lx, prm->Lz);
   k_noalloc_setup_modes<<<(nm + 127) / 128, 128, 0, s>>>(base, L, N, Mx, Mz, I.sigma[0]);
   const int ctas = (nm + mpc - 1) / mpc;

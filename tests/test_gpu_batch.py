@@ -127,3 +127,25 @@ def test_kernel_organisations_give_the_same_bits(pcf, tile):
     for k in (1, 2, 3):   # 3: whatever group size, mode tile and organisation the autotuner picked
         assert np.array_equal(outs[0], outs[k])
         assert np.array_equal(hists[0], hists[k])
+
+
+def test_contexts_of_different_sizes_coexist(pcf):
+    """A kernel's shared-memory limit belongs to the kernel, not to a context: creating a
+    smaller context later must not break an earlier, larger one (its captured graph and a new
+    capture give the same bits as before)."""
+    big = pcf.Solver(48, 49, 48, batch=2)
+    ub = torch.from_numpy(gi.batch(gi.streak_roll, range(2), 48, 49, 48)).cuda()
+    u1 = ub.clone()
+    H1 = big.descent_step(u1, 0.01, 2)
+    for kind in (0, 4):
+        small = pcf.Solver(16, 17, 16, batch=1, solve_kind=kind)
+        us = torch.from_numpy(gi.batch(gi.streak_roll, range(1), 16, 17, 16)).cuda()
+        small.descent_step(us, 0.01, 2)
+        small.close()
+    u2 = ub.clone()
+    H2 = big.descent_step(u2, 0.01, 2)
+    assert torch.equal(u1, u2) and torch.equal(H1, H2)
+    u3 = ub.clone()
+    big.descent_step(u3, 0.01, 1)
+    big.descent_step(u3, 0.01, 1)
+    assert torch.equal(u3, u1)
