@@ -109,6 +109,24 @@ __device__ __forceinline__ void dot2(const A* r0, const A* r1, const A* x, int s
   }
 }
 
+// One chain in index order: a += r[j] x[j s] for j < len (dot2's chain for a row without a
+// partner).
+template <class A>
+__device__ __forceinline__ void dot1(const A* r, const A* x, int s, int len, A& a) {
+  for (int j = 0; j < len; ++j) a = fma(r[j], x[j * s], a);
+}
+// The two chains of one synthesis row side by side, each in index order: e over len terms of
+// the even-class row re and column xe, o over len - 1 terms of the odd-class row ro and xo.
+template <class A>
+__device__ __forceinline__ void dot_eo(const A* re, const A* ro, const A* xe, const A* xo, int s, int len, A& e,
+                                       A& o) {
+  for (int j = 0; j + 1 < len; ++j) {
+    e = fma(re[j], xe[j * s], e);
+    o = fma(ro[j], xo[j * s], o);
+  }
+  e = fma(re[len - 1], xe[(len - 1) * s], e);
+}
+
 // Per-instance flags of a group in shared memory: live[i] = instance takes part in this
 // launch (active; in the dummy-dynamics step the mask already holds this step's J < tol).
 __device__ __forceinline__ void group_flags(const GroupLaunch& gl, int first, int nI, int* live) {
@@ -159,15 +177,23 @@ __global__ void __launch_bounds__(kAnalysisThreads) k_yanalysis(GroupLaunch gl, 
   __syncthreads();
   const double inv_step = op == MODE_PHI ? I0.inv_dt : I0.inv_dtau_hat, inv_nu = I0.inv_nu;
   // row pairs (k, k + hE) of the even coefficients n = 2k (k < H, from P), then pairs
-  // (k, k + hO) of the odd coefficients n = 2k+1 (k < N/2, from Q)
+  // (k, k + hO) of the odd coefficients n = 2k+1 (k < N/2, from Q).  In FP64 a class with an
+  // odd number of rows leaves its middle row unpaired: that row takes one single-chain task
+  // per column, in whole warps after the pairs (at most one class has one: H = N/2 + 1).
+  // Float-float pairs it with a dead row.
   const int hE = (H + 1) / 2, hO = (half + 1) / 2;
-  const int ER = round_up(hE, RW), OR = round_up(hO, RW);
-  for (int t = threadIdx.x; t < (ER + OR) * SPt; t += blockDim.x) {
-    const int sc = t % SPt, rs = t / SPt, mm = sc / SP, m = m0 + mm;
-    const bool even = rs < ER;
-    const int nrow = even ? H : half, hh = even ? hE : hO;
-    const int k0 = even ? rs : rs - ER, k1 = k0 + hh;
-    const bool v0 = k0 < hh, v1 = v0 && k1 < nrow;
+  const bool dbl = std::is_same<A, double>::value;
+  const bool loneE = dbl && (H & 1), loneO = dbl && (half & 1);
+  const int pE = hE - (loneE ? 1 : 0), pO = hO - (loneO ? 1 : 0);
+  const int ER = round_up(pE, RW), OR = round_up(pO, RW), PT = (ER + OR) * SPt;
+  const int ntask = PT + (loneE || loneO ? SPt : 0);
+  auto task = [&](int t, auto single_c) {
+    constexpr bool single = decltype(single_c)::value;
+    const int sc = single ? t - PT : t % SPt, rs = t / SPt, mm = sc / SP, m = m0 + mm;
+    const bool even = single ? loneE : rs < ER;
+    const int nrow = even ? H : half, hh = even ? hE : hO, pp = even ? pE : pO;
+    const int k0 = single ? hh - 1 : (even ? rs : rs - ER), k1 = k0 + hh;
+    const bool v0 = single || k0 < pp, v1 = !single && v0 && k1 < nrow;
     const int i = (sc - mm * SP) >> 1, part = sc & 1;
     const bool out = i < nI && m < nm && live[i];
     const double* st = nullptr;
@@ -183,11 +209,16 @@ __global__ void __launch_bounds__(kAnalysisThreads) k_yanalysis(GroupLaunch gl, 
     const A* v = (even ? VP : VQ) + sc;
     const int len = even ? H : half;  // P_j for j < H, Q_j for j < N/2
     A a0 = A(0.0), a1 = A(0.0);
-    dot2(row0, row1, v, XS, len, a0, a1);
-    if (!out) continue;
+    if constexpr (single) dot1(row0, v, XS, len, a0);
+    else dot2(row0, row1, v, XS, len, a0, a1);
+    if (!out) return;
     double* fr = gl.insts[first + i].frg + ((size_t)m * 3 + c) * 2 * L2 + part * L2;
     if (v0) fr[even ? k0 : Mh + k0] = fma(u0a, inv_step, to_double(a0)) * inv_nu;
     if (v1) fr[even ? k1 : Mh + k1] = fma(u0b, inv_step, to_double(a1)) * inv_nu;
+  };
+  for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
+    if (t < PT) task(t, std::false_type());
+    else task(t, std::true_type());
   }
 }
 
@@ -473,11 +504,28 @@ __global__ void __launch_bounds__(kSplitThreads) k_ysynth(GroupLaunch gl, int sl
     d[1] = A(v.y);
   }
   __syncthreads();
-  // rows j and j + hJ of the output (hJ = H/2 rounded up), values at y_j and y_{N-j}
-  const int hJ = (H + 1) / 2, JR = round_up(hJ, RW);
-  for (int t = threadIdx.x; t < JR * SPt; t += blockDim.x) {
+  // rows j and j + hJ of the output (hJ = H/2 rounded up), values at y_j and y_{N-j}.  In FP64
+  // an odd H leaves the middle row hJ - 1 unpaired: each of its columns takes one thread that
+  // runs the row's even and odd chains side by side (half the work of a pair), in whole warps
+  // after the pairs.  Float-float pairs it with a dead row.
+  const int hJ = (H + 1) / 2;
+  const bool lone = std::is_same<A, double>::value && (H & 1);
+  const int np = hJ - (lone ? 1 : 0), PT = round_up(np, RW) * SPt;
+  const int ntask = PT + (lone ? SPt : 0);
+  for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
+    if (t >= PT) {
+      const int sc = t - PT, j = hJ - 1, mm = sc / SP, m = m0 + mm;
+      A e = A(0.0), o = A(0.0);
+      dot_eo(ME + j * H, MO + j * H, AE + sc, AO + sc, XS, H, e, o);
+      const int i = (sc - mm * SP) >> 1, part = sc & 1;
+      if (i >= nI || m >= nm || !live[i]) continue;
+      double* dst = reinterpret_cast<double*>(gl.insts[first + i].yv + ((size_t)slot * kFieldsY + qf) * ny * nm + m) + part;
+      dst[(size_t)j * nm * 2] = to_double(e + o);
+      if (j < half) dst[(size_t)(N - j) * nm * 2] = to_double(deriv ? o - e : e - o);
+      continue;
+    }
     const int sc = t % SPt, j0 = t / SPt, j1 = j0 + hJ, mm = sc / SP, m = m0 + mm;
-    const bool v0 = j0 < hJ, v1 = v0 && j1 < H;
+    const bool v0 = j0 < np, v1 = v0 && j1 < H;
     const A* re0 = ME + (v0 ? j0 : 0) * H;
     const A* ro0 = MO + (v0 ? j0 : 0) * H;
     const A* re1 = ME + (v1 ? j1 : 0) * H;

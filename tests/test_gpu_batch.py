@@ -30,11 +30,14 @@ def _flat(states):
 
 
 MIXED = [(16, 17, 16, 2), (32, 33, 32, 2), (48, 49, 48, 1)]
+# The paper's 32 x 31 x 32 grid: N = ny - 1 = 2 mod 4, so an even number of even-class
+# Chebyshev rows and an odd number of odd-class rows (the other way round from MIXED)
+PAPER_GRID = [(32, 31, 32, 3)]
 
 
-def _mixed_inputs():
+def _mixed_inputs(grids=MIXED):
     us, seeds = [], iter(range(100))
-    for (nx, ny, nz, cnt) in MIXED:
+    for (nx, ny, nz, cnt) in grids:
         for _ in range(cnt):
             us.append(gi.random_perturbation(nx, ny, nz, 0.1, next(seeds)))
     return us
@@ -109,15 +112,15 @@ def test_uneven_64_instance_batch(pcf):
         assert _rel(got, ref) <= TOL
 
 
-@pytest.mark.parametrize("tile", [0, 3])
-def test_kernel_organisations_give_the_same_bits(pcf, tile):
+@pytest.mark.parametrize("grids,tile", [(MIXED, 0), (MIXED, 3), (PAPER_GRID, 0)])
+def test_kernel_organisations_give_the_same_bits(pcf, grids, tile):
     """The per-mode work of a step as one per-mode kernel (solve_kind 2), as analysis, solve
     and synthesis kernels (3), or as one fused half-step kernel over instance groups (4):
     the same operations per output, so the same bits."""
-    us = _mixed_inputs()
+    us = _mixed_inputs(grids)
     outs, hists = [], []
     for kind, launches, variant in ((2, 6, 1), (3, 10, 2), (4, 7, 3), (0, None, None)):
-        s = pcf.Solver.batched(MIXED, solve_kind=kind, modes_per_block=tile)
+        s = pcf.Solver.batched(grids, solve_kind=kind, modes_per_block=tile)
         if launches is not None:
             assert s.launches_per_step() == launches and s.solve_variant() == variant
             assert s.launches_per_call(3) == 1 + 3 * launches - (1 if kind == 3 else 0)
