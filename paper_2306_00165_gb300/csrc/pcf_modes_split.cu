@@ -133,9 +133,11 @@ __device__ __forceinline__ void group_flags(const GroupLaunch& gl, int first, in
   if (threadIdx.x < nI) live[threadIdx.x] = inst_active(gl.insts[first + threadIdx.x]) ? 1 : 0;
 }
 
-// A: arithmetic of the Chebyshev dot products (double, or ff in the float-float form)
+// A: arithmetic of the Chebyshev dot products (double, or ff in the float-float form).
+// Five resident CTAs per SM (48 registers): with one mode per CTA a 32x33x32 batch of 8 has
+// 7.5 CTAs per SM, one and a half waves at five and two at four.
 template <class A>
-__global__ void __launch_bounds__(kAnalysisThreads) k_yanalysis(GroupLaunch gl, int op, int mt) {
+__global__ void __launch_bounds__(kAnalysisThreads, 5) k_yanalysis(GroupLaunch gl, int op, int mt) {
   extern __shared__ double sm[];
   __shared__ int live[kMaxGroup];
   int local;
