@@ -179,13 +179,14 @@ __global__ void __launch_bounds__(kAnalysisThreads, 5) k_yanalysis(GroupLaunch g
   __syncthreads();
   const double inv_step = op == MODE_PHI ? I0.inv_dt : I0.inv_dtau_hat, inv_nu = I0.inv_nu;
   // row pairs (k, k + hE) of the even coefficients n = 2k (k < H, from P), then pairs
-  // (k, k + hO) of the odd coefficients n = 2k+1 (k < N/2, from Q).  In FP64 a class with an
-  // odd number of rows leaves its middle row unpaired: that row takes one single-chain task
-  // per column, in whole warps after the pairs (at most one class has one: H = N/2 + 1).
-  // Float-float pairs it with a dead row.
+  // (k, k + hO) of the odd coefficients n = 2k+1 (k < N/2, from Q).  A class with an odd
+  // number of rows leaves its middle row with a dead partner.  In FP64, when that pair would
+  // start a warp of its own ((h - 1) a multiple of the pairs per warp), the row instead takes
+  // one single-chain task per column, in whole warps after the pairs: half a pair warp's
+  // work.  At most one class has an odd count (H = N/2 + 1).
   const int hE = (H + 1) / 2, hO = (half + 1) / 2;
   const bool dbl = std::is_same<A, double>::value;
-  const bool loneE = dbl && (H & 1), loneO = dbl && (half & 1);
+  const bool loneE = dbl && (H & 1) && (hE - 1) % RW == 0, loneO = dbl && (half & 1) && (hO - 1) % RW == 0;
   const int pE = hE - (loneE ? 1 : 0), pO = hO - (loneO ? 1 : 0);
   const int ER = round_up(pE, RW), OR = round_up(pO, RW), PT = (ER + OR) * SPt;
   const int ntask = PT + (loneE || loneO ? SPt : 0);
@@ -470,9 +471,10 @@ __global__ void __launch_bounds__(kSolveThreads) k_ysolve(GroupLaunch gl, int op
   }
 }
 
-// slot 0: synthesis of uhat, slot 1: of rhat.  q = 0..4: V_u V_v V_w W_u W_w.
+// slot 0: synthesis of uhat, slot 1: of rhat.  q = 0..4: V_u V_v V_w W_u W_w.  Ten resident
+// CTAs per SM (48 registers): one mode per CTA gives a 32x33x32 batch of 8 12.5 CTAs per SM.
 template <class A>
-__global__ void __launch_bounds__(kSplitThreads) k_ysynth(GroupLaunch gl, int slot, int check_active, int mt) {
+__global__ void __launch_bounds__(kSplitThreads, 10) k_ysynth(GroupLaunch gl, int slot, int check_active, int mt) {
   extern __shared__ double sm[];
   __shared__ int live[kMaxGroup];
   int local;
@@ -506,12 +508,12 @@ __global__ void __launch_bounds__(kSplitThreads) k_ysynth(GroupLaunch gl, int sl
     d[1] = A(v.y);
   }
   __syncthreads();
-  // rows j and j + hJ of the output (hJ = H/2 rounded up), values at y_j and y_{N-j}.  In FP64
-  // an odd H leaves the middle row hJ - 1 unpaired: each of its columns takes one thread that
-  // runs the row's even and odd chains side by side (half the work of a pair), in whole warps
-  // after the pairs.  Float-float pairs it with a dead row.
+  // rows j and j + hJ of the output (hJ = H/2 rounded up), values at y_j and y_{N-j}.  An odd
+  // H leaves the middle row hJ - 1 with a dead partner.  In FP64, when that pair would start a
+  // warp of its own, each of the row's columns instead takes one thread that runs the row's
+  // even and odd chains side by side, in whole warps after the pairs: half a pair warp's work.
   const int hJ = (H + 1) / 2;
-  const bool lone = std::is_same<A, double>::value && (H & 1);
+  const bool lone = std::is_same<A, double>::value && (H & 1) && (hJ - 1) % RW == 0;
   const int np = hJ - (lone ? 1 : 0), PT = round_up(np, RW) * SPt;
   const int ntask = PT + (lone ? SPt : 0);
   for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
