@@ -181,9 +181,9 @@ __global__ void __launch_bounds__(kAnalysisThreads, 5) k_yanalysis(GroupLaunch g
   // row pairs (k, k + hE) of the even coefficients n = 2k (k < H, from P), then pairs
   // (k, k + hO) of the odd coefficients n = 2k+1 (k < N/2, from Q).  A class with an odd
   // number of rows leaves its middle row with a dead partner.  In FP64, when that pair would
-  // start a warp of its own ((h - 1) a multiple of the pairs per warp), the row instead takes
-  // one single-chain task per column, in whole warps after the pairs: half a pair warp's
-  // work.  At most one class has an odd count (H = N/2 + 1).
+  // start a warp of its own (hE - 1 or hO - 1 a multiple of RW, the pairs per warp), the row
+  // instead takes one single-chain task per column, in whole warps after the pairs: half a
+  // pair warp's work.  At most one class has an odd count (H = N/2 + 1).
   const int hE = (H + 1) / 2, hO = (half + 1) / 2;
   const bool dbl = std::is_same<A, double>::value;
   const bool loneE = dbl && (H & 1) && (hE - 1) % RW == 0, loneO = dbl && (half & 1) && (hO - 1) % RW == 0;
