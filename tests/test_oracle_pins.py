@@ -168,6 +168,72 @@ def test_r1_and_f_admissible(o16):
             assert np.max(np.abs(wv)) <= 1e-14 * scale * 100
 
 
+def _d2(a):
+    """Second y-derivative of Chebyshev coefficients (numpy's Chebyshev module), same length."""
+    return np.pad(npC.chebder(a, m=2, axis=-1), [(0, 0)] * (a.ndim - 1) + [(0, 2)])
+
+
+def _step_equation_gap(o, u):
+    """Largest relative residual of (I - dt nu Lap) r1 = M(u) + nu Lap u on the Chebyshev rows
+    0..N-2, for the wall-normal vorticity i kz r_x - i kx r_z of every mode (no pressure) and
+    for r_x, r_z of the mean mode (no mean pressure gradient).  M is the unmodified oracle's,
+    so a mistake planted in the residual path shows."""
+    r1, _, (uval, ugrad) = o.residual(u, return_fields=True)
+    M = PCFOracle.M_hat(o, uval, ugrad)
+    k2 = o.KX ** 2 + o.KZ ** 2
+    rows = slice(0, o.N - 1)
+
+    def lap(a):
+        return _d2(a) - k2 * a
+
+    def eta(a):
+        return 1j * o.KZ * a[0] - 1j * o.KX * a[2]
+
+    lhs = eta(r1) - o.dt * o.nu * lap(eta(r1))
+    rhs = eta(M) + o.nu * lap(eta(u))
+    gap = np.abs(lhs - rhs)[..., rows].max() / np.abs(rhs[..., rows]).max()
+    for c in (0, 2):
+        lm = r1[c, 0, 0] - o.dt * o.nu * _d2(r1[c, 0, 0])
+        rm = M[c, 0, 0] + o.nu * _d2(u[c, 0, 0])
+        gap = max(gap, np.abs(lm - rm)[rows].max() / np.abs(rm[rows]).max())
+    return gap
+
+
+@pytest.mark.parametrize("dt", [0.05, 0.25, 1.0])
+def test_r1_solves_the_step_equation_for_every_dt(dt):
+    """§4 steps 1-2: u^dt = u + dt r1 solves (1/dt - nu Lap) u^dt + grad p = u/dt + M(u), so
+    (I - dt nu Lap) r1 + grad p = M(u) + nu Lap u.  The right-hand side does not depend on dt:
+    r1 = 0 exactly where u is an equilibrium of the discrete equations, whatever the step
+    (§4).  Checked where pressure drops out, on the rows where the momentum equations hold
+    (the last two rows of each field carry the no-slip conditions instead)."""
+    u = gi.random_perturbation(16, 17, 16, 0.1, 3)
+    assert _step_equation_gap(PCFOracle(16, 17, 16, dt=dt), u) <= 1e-12
+
+
+class _ViscosityDropped(PCFOracle):
+    def stokes_step(self, rhs, step):       # shift 1/step instead of 1/(nu step)
+        return self.stokes(rhs / self.nu, 1.0 / step)
+
+
+class _QuotientWithoutDt(PCFOracle):
+    def residual(self, uhat, return_fields=False):
+        r1, J, f = PCFOracle.residual(self, uhat, return_fields=True)
+        return (r1 * self.dt, J, f) if return_fields else (r1 * self.dt, J)
+
+
+class _ProductSignFlipped(PCFOracle):
+    def M_hat(self, uval, ugrad):
+        return -PCFOracle.M_hat(self, uval, ugrad)
+
+
+@pytest.mark.parametrize("bad", [_ViscosityDropped, _QuotientWithoutDt, _ProductSignFlipped])
+def test_step_equation_catches_planted_mistakes(bad):
+    """A wrong implicit shift, a missing 1/dt in the quotient or a flipped explicit term
+    breaks the step equation by many orders of magnitude."""
+    u = gi.random_perturbation(16, 17, 16, 0.1, 3)
+    assert _step_equation_gap(bad(16, 17, 16, dt=0.25), u) > 1e-4
+
+
 def test_descent_monotone(o16):
     """J decreases monotonically along the descent for a small step (§2, §3.4)."""
     u = gi.random_perturbation(16, 17, 16, 0.1, 1)
