@@ -234,6 +234,71 @@ def test_step_equation_catches_planted_mistakes(bad):
     assert _step_equation_gap(bad(16, 17, 16, dt=0.25), u) > 1e-4
 
 
+def _adjoint_step_gap(o, u):
+    """Largest relative residual of (I - dtau_hat nu Lap) f = -(N(r1) + nu Lap r1) (up to a
+    gradient) on the momentum rows, for the wall-normal vorticity and the mean mode's x, z
+    components.  N is the unmodified oracle's."""
+    r1, _, uf = PCFOracle.residual(o, u, return_fields=True)
+    f = o.adjoint_direction(u, r1, uf)
+    qval, qgrad = PCFOracle.fields(o, r1)
+    Nh = PCFOracle.N_hat(o, qval, qgrad, *uf)
+    k2 = o.KX ** 2 + o.KZ ** 2
+    rows, h = slice(0, o.N - 1), o.dtau_hat * o.nu
+
+    def lap(a):
+        return _d2(a) - k2 * a
+
+    def eta(a):
+        return 1j * o.KZ * a[0] - 1j * o.KX * a[2]
+
+    lhs = eta(f) - h * lap(eta(f))
+    rhs = -(eta(Nh) + o.nu * lap(eta(r1)))
+    gap = np.abs(lhs - rhs)[..., rows].max() / np.abs(rhs[..., rows]).max()
+    for c in (0, 2):
+        lm = f[c, 0, 0] - h * _d2(f[c, 0, 0])
+        rm = -(Nh[c, 0, 0] + o.nu * _d2(r1[c, 0, 0]))
+        gap = max(gap, np.abs(lm - rm)[rows].max() / np.abs(rm[rows]).max())
+    return gap
+
+
+@pytest.mark.parametrize("dtau_hat", [0.02, 0.1, 0.5])
+def test_f_solves_the_dummy_step_equation(dtau_hat):
+    """§4 steps 3-4: r1^+ solves (1/dtau_hat - nu Lap) r1^+ + grad phi = r1/dtau_hat + N(r1)
+    and f = -(r1^+ - r1)/dtau_hat, so (I - dtau_hat nu Lap) f = -(N(r1) + nu Lap r1) up to a
+    gradient.  As dtau_hat -> 0 this is the adjoint evolution of §3 (Eq.
+    adjoint_evolution_divergence_free) with the sign reading of step 4.  dt = 0.25 differs
+    from every dtau_hat here, so the two step sizes cannot be swapped unnoticed."""
+    u = gi.random_perturbation(16, 17, 16, 0.1, 5)
+    assert _adjoint_step_gap(PCFOracle(16, 17, 16, dt=0.25, dtau_hat=dtau_hat), u) <= 1e-12
+
+
+class _DirectionSignFlipped(PCFOracle):
+    def adjoint_direction(self, uhat, r1, ufields=None):
+        return -PCFOracle.adjoint_direction(self, uhat, r1, ufields)
+
+
+class _DummyStepTakesDt(PCFOracle):
+    def adjoint_direction(self, uhat, r1, ufields=None):
+        uval, ugrad = ufields if ufields is not None else self.fields(uhat)
+        qval, qgrad = self.fields(r1)
+        Nh = self.N_hat(qval, qgrad, uval, ugrad)
+        r1_plus = self.stokes_step(r1 / self.dtau_hat + Nh, self.dt)    # dt for dtau_hat
+        return -(r1_plus - r1) / self.dtau_hat
+
+
+class _AdjointTermFlipped(PCFOracle):
+    def N_hat(self, qval, qgrad, uval, ugrad):
+        return -PCFOracle.N_hat(self, qval, qgrad, uval, ugrad)
+
+
+@pytest.mark.parametrize("bad", [_DirectionSignFlipped, _DummyStepTakesDt, _AdjointTermFlipped])
+def test_dummy_step_equation_catches_planted_mistakes(bad):
+    """A flipped descent direction, the NSE step size in the dummy step or a flipped adjoint
+    term breaks the equation by many orders of magnitude."""
+    u = gi.random_perturbation(16, 17, 16, 0.1, 5)
+    assert _adjoint_step_gap(bad(16, 17, 16, dt=0.25, dtau_hat=0.1), u) > 1e-4
+
+
 def test_descent_monotone(o16):
     """J decreases monotonically along the descent for a small step (§2, §3.4)."""
     u = gi.random_perturbation(16, 17, 16, 0.1, 1)
