@@ -751,3 +751,83 @@ def test_dmd_schedule_gap_and_fixed_period():
     assert jumps == [40, 80, 120, 160, 200]
     _, _, _, jumps = dmd.run_schedule(u0, step, ident, jitter, cost, 300, 1e-300, 4, 10, 25, np.inf, 1e-12)
     assert jumps == [40, 40 + 30 + 40, 40 + 2 * 70, 40 + 3 * 70]
+
+
+# ------------------------------------------------------------------ the norm of J
+def _mode_field(o, comp, m, p, g):
+    """Coefficients of the real field cos(2 pi (m x/Lx + p z/Lz)) g(y) e_comp (g: Chebyshev
+    coefficients), written directly in the storage layout: the p = 0 plane holds the two
+    halves at +-m, a p > 0 mode holds half (its conjugate at -p is implied)."""
+    a = np.zeros((3, o.Mx, o.Mz, o.N + 1), np.complex128)
+    gc = np.zeros(o.N + 1)
+    gc[: len(g)] = g
+    if m == 0 and p == 0:
+        a[comp, 0, 0] = gc
+    elif p == 0:
+        a[comp, m % o.Mx, 0] += 0.5 * gc
+        a[comp, (-m) % o.Mx, 0] += 0.5 * gc
+    else:
+        a[comp, m % o.Mx, p] = 0.5 * gc
+    return a
+
+
+# (1 - y^2) = T0/2 - T2/2; (1 - y^2)^2 = 3/8 T0 - T2/2 + T4/8; T2 itself
+_ONE_MINUS_Y2 = [0.5, 0.0, -0.5]
+_ONE_MINUS_Y2_SQ = [0.375, 0.0, -0.5, 0.0, 0.125]
+_T2 = [0.0, 0.0, 1.0]
+
+# Squared norms (1/(2 Lx Lz)) int |u|^2 in closed form: the mean over x, z of cos^2 is 1/2
+# for a non-zero wavenumber and 1 for the mean mode; int (1-y^2)^2 = 16/15,
+# int (1-y^2)^4 = 256/315, int T2^2 = 14/15.
+_NORM_CASES = [
+    ((0, 0, 0, _ONE_MINUS_Y2), 0.5 * 16.0 / 15.0),          # mean streamwise profile: 8/15
+    ((0, 1, 0, _ONE_MINUS_Y2), 0.5 * 0.5 * 16.0 / 15.0),    # one x-mode: 4/15
+    ((2, 0, 1, _ONE_MINUS_Y2), 0.5 * 0.5 * 16.0 / 15.0),    # one z-mode (p > 0, Hermitian half): 4/15
+    ((1, -1, 2, _ONE_MINUS_Y2_SQ), 0.5 * 0.5 * 256.0 / 315.0),  # oblique mode: 64/315
+    ((2, 0, 0, _T2), 0.5 * 14.0 / 15.0),                    # pure Chebyshev mean field: 7/15
+]
+
+
+def _norm_closed_form_gap(o):
+    """Largest relative error of o.norm()^2 against the closed forms, one case at a time
+    and for their sum (distinct modes or components are orthogonal, so squares add)."""
+    gaps = []
+    total, want_total = 0, 0.0
+    for (comp, m, p, g), want in _NORM_CASES:
+        a = _mode_field(o, comp, m, p, g)
+        gaps.append(abs(o.norm(a) ** 2 - want) / want)
+        total = total + a
+        want_total += want
+    gaps.append(abs(o.norm(total) ** 2 - want_total) / want_total)
+    return max(gaps)
+
+
+@pytest.mark.parametrize("grid", [(16, 17, 16), (32, 33, 48), (48, 25, 32)])
+def test_norm_closed_forms(grid):
+    """||u||^2 = (1/(2 Lx Lz)) int |u|^2 (the norm of J = ||r1||): exact values of single
+    mean, x, z and oblique modes and of a pure Chebyshev profile."""
+    assert _norm_closed_form_gap(PCFOracle(*grid)) < 1e-14
+
+
+class _NormWithoutHalf(PCFOracle):
+    def norm_phys(self, val):
+        return math.sqrt(2.0) * PCFOracle.norm_phys(self, val)
+
+
+class _NormSumOverXZ(PCFOracle):
+    def norm_phys(self, val):
+        s = (val ** 2).sum(axis=0).sum(axis=(-2, -1))
+        return math.sqrt(0.5 * float((self.w_cc * s).sum()))
+
+
+class _NormUniformInY(PCFOracle):
+    def norm_phys(self, val):
+        s = (val ** 2).sum(axis=0).mean(axis=(-2, -1))
+        return math.sqrt(0.5 * float(s.sum() * 2.0 / len(s)))
+
+
+@pytest.mark.parametrize("bad", [_NormWithoutHalf, _NormSumOverXZ, _NormUniformInY])
+def test_norm_closed_forms_catch_planted_mistakes(bad):
+    """A dropped 1/2, a sum in place of the mean over x, z, or uniform weights in y miss the
+    closed forms by far more than rounding."""
+    assert _norm_closed_form_gap(bad(16, 17, 16)) > 1e-2
