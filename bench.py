@@ -32,9 +32,9 @@ DTAU = 0.01
 WORKLOAD = "PCF Re=400 box 2pi/1.14 x 2 x 2pi/2.5, 32x33x32, 8 streak/roll guesses, plain FP64 descent step"
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel classes
-# from the ncu capture in profiles/fp64_step_32x33x32_b8_launches_and_top_kernels.md; reset
-# an entry to None when that kernel changes.
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel classes,
+# read from one ncu capture of the current kernels on this workload; reset an entry to None
+# when that kernel changes.
 TRAFFIC_BYTES = {"xzsynth_u": 4.09e6, "xzsynth_q": 4.09e6}
 
 

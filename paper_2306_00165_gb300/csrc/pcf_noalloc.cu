@@ -190,7 +190,7 @@ __global__ void k_noalloc_setup_modes(double* base, NoAllocLayout L, int N, int 
 }
 
 bool noalloc_grid_ok(int nx, int ny, int nz) {
-  if (nx < 16 || nz < 16 || (nx % 2) || (nz % 2) || ny < 9 || !(ny % 2)) return false;
+  if (nx < 16 || nz < 16 || nx > 64 || nz > 64 || (nx % 2) || (nz % 2) || ny < 9 || !(ny % 2)) return false;
   const int Kx = nx / 3 - 1, Kz = nz / 3 - 1;
   const int Mh = (ny - 1) / 2 + 1;
   return Mh <= kNoAllocMaxMh && (2 * Kx + 1) * (Kz + 1) <= kNoAllocMaxModes;
