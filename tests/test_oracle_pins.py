@@ -831,3 +831,55 @@ def test_norm_closed_forms_catch_planted_mistakes(bad):
     """A dropped 1/2, a sum in place of the mean over x, z, or uniform weights in y miss the
     closed forms by far more than rounding."""
     assert _norm_closed_form_gap(bad(16, 17, 16)) > 1e-2
+
+
+# ------------------------------------------------------------------ equilibria: shifts, alignment, dissipation
+from oracle import equilibria as eqm  # noqa: E402
+
+
+def test_shift_by_grid_points_is_a_roll(o16):
+    """A shift by whole grid spacings moves the physical values by whole points."""
+    a = gi.random_perturbation(16, 17, 16, 0.1, 5)
+    for i, j in [(1, 0), (0, 3), (5, 7), (15, 15)]:
+        b = eqm.shift(o16, a, i * LX / 16, j * LZ / 16)
+        want = np.roll(o16.to_phys(a), (i, j), axis=(-2, -1))
+        assert np.max(np.abs(o16.to_phys(b) - want)) < 1e-14
+
+
+def test_shift_of_a_single_mode(o16):
+    """Any shift of one (m, p, n) mode equals the closed form 2 Re(c T_n e^{i(kx (x - lx) + kz (z - lz))})."""
+    x = np.arange(16) * LX / 16
+    z = np.arange(16) * LZ / 16
+    a = np.zeros((3, o16.Mx, o16.Mz, o16.N + 1), np.complex128)
+    c = 0.3 - 0.7j
+    a[1, 2, 3, 4] = c
+    lx, lz = 0.37 * LX, 0.81 * LZ
+    got = o16.to_phys(eqm.shift(o16, a, lx, lz))[1]
+    E = np.exp(1j * (o16.kx[2] * (x[:, None] - lx) + o16.kz[3] * (z[None, :] - lz)))
+    want = 2 * np.real(c * E)[None] * np.cos(4 * np.arccos(o16.y))[:, None, None]
+    assert np.max(np.abs(got - want)) < 1e-14
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_align_recovers_a_shift(o16, seed):
+    """A field and a shifted copy: alignment finds the inverse shift and distance zero."""
+    rng = np.random.default_rng(seed)
+    a = gi.random_perturbation(16, 17, 16, 0.1, 10 + seed)
+    lx0, lz0 = rng.uniform(0, LX), rng.uniform(0, LZ)
+    b = eqm.shift(o16, a, lx0, lz0)
+    lx, lz, bs, dist = eqm.align(o16, a, b)
+    assert dist < 1e-12
+    assert abs(((lx + lx0 + LX / 2) % LX) - LX / 2) < 1e-8
+    assert abs(((lz + lz0 + LZ / 2) % LZ) - LZ / 2) < 1e-8
+
+
+def test_dissipation_closed_forms(o16):
+    """D/D_lam = 1 for the laminar flow, 7/3 for u = (1 - y^2) e_x, and
+    1 + (kx^2 16/15 + 8/3)/4 for u = cos(kx x)(1 - y^2) e_x."""
+    zero = np.zeros((3, o16.Mx, o16.Mz, o16.N + 1), np.complex128)
+    assert abs(eqm.dissipation(o16, zero) - 1.0) < 1e-15
+    a = _mode_field(o16, 0, 0, 0, _ONE_MINUS_Y2)
+    assert abs(eqm.dissipation(o16, a) - 7.0 / 3.0) < 1e-14
+    b = _mode_field(o16, 0, 1, 0, _ONE_MINUS_Y2)
+    kx = o16.kx[1]
+    assert abs(eqm.dissipation(o16, b) - (1.0 + 0.25 * (kx * kx * 16.0 / 15.0 + 8.0 / 3.0))) < 1e-14
