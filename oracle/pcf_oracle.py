@@ -185,6 +185,15 @@ class PCFOracle:
         key = float(sigma)
         if key in self._lu:
             return self._lu[key]
+        table = {}
+        for ij, (A, scale) in self.stokes_systems(sigma).items():
+            table[ij] = sla.lu_factor(A) if scale is None else (sla.lu_factor(A * scale[:, None]), scale)
+        self._lu[key] = table
+        return table
+
+    def stokes_systems(self, sigma):
+        """The dense tau system of every mode: {(i, j): (A, row scale)}; the mean mode's
+        real Dirichlet Helmholtz matrix has no scale (None)."""
         N, n1 = self.N, self.N + 1
         I = np.eye(n1)
         D = self.Dmat
@@ -200,7 +209,7 @@ class PCFOracle:
                     A[: N - 1] = (sigma * I - D2)[: N - 1]
                     A[N - 1] = 1.0
                     A[N] = alt
-                    table[(i, j)] = sla.lu_factor(A)
+                    table[(i, j)] = (A, None)
                     continue
                 H = (sigma + k2) * I - D2
                 grads = [1j * kx * I, D, 1j * kz * I]
@@ -220,8 +229,7 @@ class PCFOracle:
                         A[r, c * n1:(c + 1) * n1] = grads[c][row]
                     r += 1
                 scale = 1.0 / np.abs(A).max(axis=1)
-                table[(i, j)] = (sla.lu_factor(A * scale[:, None]), scale)
-        self._lu[key] = table
+                table[(i, j)] = (A, scale)
         return table
 
     def stokes(self, F, sigma):
