@@ -348,14 +348,17 @@ pcf_status pcf_probe_fp64_peak(void* stream, double* gflops);
  * subsequent eager (non-graph) calls; pcf_kernel_times returns the accumulated
  * milliseconds and launch counts per kernel class (host arrays of length n).
  * Kernel classes: 0 ysynth, 1 xzsynth_u, 2 prod_M, 3 mode_phi, 4 xzsynth_q,
- * 5 prod_N, 6 mode_psi, 7 yanalysis, 8 ysynth_step, 9 jnorm, 10 symmetrize, 11 dns_aux.
+ * 5 prod_N, 6 mode_psi, 7 yanalysis, 8 ysynth_step, 9 jnorm, 10 symmetrize, 11 dns_aux,
+ * 12 cheb_synth_tc, 13 cheb_analysis_tc.
  * In the FP64 form with dense per-mode operators (ny <= 97) the per-mode work of a step
  * runs as three kernels: 7 (Chebyshev analysis + right-hand side, twice per step), 3/6
  * (Stokes solve and update of the NSE / dummy step), 8 (Chebyshev synthesis of r1 and of
  * the new u).  J, its history and the convergence mask come from the last CTA of each
  * instance in 5, except with the fused half-step kernel, where 9 computes them; without
  * dense operators 3/6 hold the whole per-mode kernel and 7, 8, 9 stay empty.  10 is the
- * projection onto the symmetric subspace, 11 the small kernels around pcf_dns. */
+ * projection onto the symmetric subspace, 11 the small kernels around pcf_dns; 12 and 13 are the
+ * mixed form's tensor-core Chebyshev synthesis and analysis (its mode kernel, 3/6, then holds
+ * only the Stokes solve). */
 pcf_status pcf_set_kernel_timing(pcf_ctx* ctx, int enable);
 
 /* Organisation the autotuner chose for the split per-mode kernels (FP64 and float-float

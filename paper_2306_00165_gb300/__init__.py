@@ -143,7 +143,8 @@ class Solver:
     states are one flat complex128 tensor (``flat_len`` values, instance views via ``view``)."""
 
     KERNEL_CLASSES = ["ysynth", "xzsynth_u", "prod_M", "mode_phi", "xzsynth_q", "prod_N", "mode_psi",
-                      "yanalysis", "ysynth_step", "jnorm", "symmetrize", "dns_aux"]
+                      "yanalysis", "ysynth_step", "jnorm", "symmetrize", "dns_aux", "cheb_synth_tc",
+                      "cheb_analysis_tc"]
 
     def __init__(self, nx, ny, nz, batch=1, Lx=LX_PAPER, Lz=LZ_PAPER, Re=400.0, dt=0.25, dtau_hat=0.25,
                  precision=0, modes_per_block=0, solve_kind=0, base_flow=COUETTE, symmetry=0):

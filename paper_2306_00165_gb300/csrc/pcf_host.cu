@@ -418,10 +418,10 @@ pcf_status launch_prodN(pcf_ctx* c, int step_index = -1) {
 }
 
 pcf_status launch_tc_synth(pcf_ctx* c, int slot) {
-  return timed(c, 0, [&] { launch_cheb_synth_tc(c->cta_tcs, c->sm_tc, c->cs, li_of(c, c->pre_tcs), slot); });
+  return timed(c, 12, [&] { launch_cheb_synth_tc(c->cta_tcs, c->sm_tc, c->cs, li_of(c, c->pre_tcs), slot); });
 }
 pcf_status launch_tc_analysis(pcf_ctx* c) {
-  return timed(c, 0, [&] { launch_cheb_analysis_tc(c->cta_tca, c->sm_tc, c->cs, li_of(c, c->pre_tca)); });
+  return timed(c, 13, [&] { launch_cheb_analysis_tc(c->cta_tca, c->sm_tc, c->cs, li_of(c, c->pre_tca)); });
 }
 // split mode kernels of the FP64 descent step
 GroupLaunch gl_of(pcf_ctx* c, const int* pre) { return GroupLaunch{c->dinst, pre, c->d_groups, c->ngroups}; }

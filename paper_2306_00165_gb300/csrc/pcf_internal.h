@@ -12,7 +12,7 @@ namespace pcf {
 constexpr int kMaxRadix = 8;     // max number of FFT stages
 constexpr int kFieldsSynth = 11; // u v w u_x u_y u_z v_x v_z w_x w_y w_z (v_y = -u_x - w_z)
 constexpr int kFieldsY = 5;      // y-values V_u V_v V_w and y-derivative values W_u W_w
-constexpr int kNumKernelClasses = 12;
+constexpr int kNumKernelClasses = 14;
 
 // ------------------------------------------------------------------ table layout
 // Chebyshev index n runs 0..N (N = ny - 1, even).  A parity class par holds the
