@@ -273,6 +273,115 @@ def run_robustness(pcf, gi, dev, args):
             "norm_u_end": [round(r[3], 4) for r in res]}
 
 
+def _form_roofline(s, u, flush, grids, args, nk=5):
+    """Per-kernel CUDA-event times of a form's step (eager launches) and the FP64 roofline of
+    its dominant kernel: algorithmic flops of every grid's instances per launch (kernel_flops)
+    over the kernel's average launch time."""
+    import torch
+    s.set_kernel_timing(True)
+    for _ in range(nk):
+        flush.fill_(1.0)
+        s.descent_step(u, DTAU, 1, hist=False)
+    torch.cuda.synchronize()
+    kt = s.kernel_times()
+    s.set_kernel_timing(False)
+    split = kt["yanalysis"][1] > 0
+    flops = {}
+    for grid, count in grids:
+        for k, v in kernel_flops(grid, count, split=split).items():
+            flops[k] = flops.get(k, 0.0) + v
+    dom = max((k for k in kt if kt[k][1]), key=lambda k: kt[k][0])
+    dom_ms = kt[dom][0] / kt[dom][1]
+    peak_tf = args.fp64_peak_gflops / 1e3
+    achieved = flops.get(dom, 0.0) / (dom_ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak_tf, 4),
+            "unit": "TFLOP/s", "frac": round(achieved / peak_tf, 4), "traffic": None,
+            "peak_source": "measured FP64 DFMA throughput (k_fp64_probe) on this GPU",
+            "kernel_ms_per_launch": round(dom_ms, 5),
+            "per_kernel_ms_per_step": {k: round(v[0] / nk, 5) for k, v in kt.items() if v[1]}}
+
+
+# Time to J < 1e-10 on perturbed-laminar guesses (random divergence-free perturbations of
+# norm 0.1, seeds 0-7, 16x17x16, Re 400): descent with Stokes-preconditioned steps
+# dt = dtau_hat = 64 and dtau = 3, the DMD schedule of §6 with 41 snapshots every 1000 steps;
+# J is measured with the paper's dt = dtau_hat = 0.25 every TTC_CHUNK steps (the stopping test).
+TTC_GRID = (16, 17, 16)
+TTC_DT, TTC_DTAU = 64.0, 3.0
+TTC_SNAPSHOTS, TTC_SPACING = 41, 1000
+TTC_CHUNK = 100000
+
+
+def _ttc_run(pcf, u0, dev, precision, max_steps, seeds):
+    """Chunks of run_schedule until every instance has J(dt 0.25) < 1e-10 or max_steps; returns
+    per instance the steps to convergence (-1: not converged), the final J, the wall time
+    and the history [(steps, wall_s, J per instance)]."""
+    import numpy as np
+    import torch
+    B = u0.shape[0]
+    ref = pcf.Solver(*TTC_GRID, batch=B, Re=RE, dt=DT, dtau_hat=DTAU_HAT, precision=precision)
+    s = pcf.Solver(*TTC_GRID, batch=B, Re=RE, dt=TTC_DT, dtau_hat=TTC_DT, precision=precision)
+    u = torch.from_numpy(u0.copy()).to(dev)
+    conv = [-1] * B
+    hist = []
+    n = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while n < max_steps:
+        s.run_schedule(u, TTC_DTAU, TTC_CHUNK, tol=1e-300, snapshots=TTC_SNAPSHOTS, spacing=TTC_SPACING, gap=0)
+        n += TTC_CHUNK
+        J = ref.residual(u)[1].cpu().numpy()
+        for b in range(B):
+            if conv[b] < 0 and J[b] < 1e-10:
+                conv[b] = n
+        hist.append((n, time.perf_counter() - t0, [float(x) for x in J]))
+        if all(c >= 0 for c in conv) or not np.all(np.isfinite(J)):
+            break
+    wall = time.perf_counter() - t0
+    norms = s.norm(u).cpu().numpy()
+    s.close()
+    ref.close()
+    return {"seeds": list(seeds), "steps_to_converge": conv, "J_final": hist[-1][2], "wall_s": round(wall, 3),
+            "norm_u_final": [float(x) for x in norms], "steps_run": n,
+            "history": [{"steps": h[0], "wall_s": round(h[1], 3), "J": h[2]} for h in hist]}
+
+
+def run_time_to_converge(pcf, gi, dev, args):
+    """Time to J < 1e-10: the batched form (all guesses in one context) in FP64 and in
+    float-float, and the plain method on one guess at a time (the guesses the batched FP64
+    run converged, each alone, for exactly its steps)."""
+    import numpy as np
+    import torch
+    seeds = list(range(8))
+    u0 = gi.batch(gi.random_perturbation, seeds, *TTC_GRID, 0.1)
+    out = {"config": f"8 perturbed-laminar guesses (random divergence-free, norm 0.1, seeds 0-7), "
+                     f"{TTC_GRID[0]}x{TTC_GRID[1]}x{TTC_GRID[2]}, Re 400; descent dt = dtau_hat = {TTC_DT:g}, "
+                     f"dtau = {TTC_DTAU:g}; DMD {TTC_SNAPSHOTS} snapshots every {TTC_SPACING} steps; "
+                     f"tol 1e-10 on J at dt = dtau_hat = 0.25, tested every {TTC_CHUNK} steps",
+           "max_steps": args.ttc_long_steps}
+    out["batched_fp64"] = _ttc_run(pcf, u0, dev, pcf.FP64, args.ttc_long_steps, seeds)
+    done = [b for b, c in enumerate(out["batched_fp64"]["steps_to_converge"]) if c >= 0]
+    last = max([out["batched_fp64"]["steps_to_converge"][b] for b in done], default=args.ttc_long_steps)
+    out["batched_float_float"] = _ttc_run(pcf, u0, dev, pcf.FLOAT_FLOAT, last, seeds)
+    # the plain method on one guess at a time, for the steps the batched run needed
+    plain = []
+    for b in done:
+        steps = out["batched_fp64"]["steps_to_converge"][b]
+        r = _ttc_run(pcf, u0[b:b + 1], dev, pcf.FP64, steps, [seeds[b]])
+        plain.append({"seed": seeds[b], "steps_to_converge": r["steps_to_converge"][0], "wall_s": r["wall_s"],
+                      "J_final": r["J_final"][0]})
+    out["plain_fp64_one_guess_at_a_time"] = plain
+    if done:
+        tb = out["batched_fp64"]["history"]
+        t_batched = next(h["wall_s"] for h in tb if h["steps"] >= last)
+        out["summary"] = {
+            "converged_batched_fp64": len(done), "of": len(seeds),
+            "wall_s_batched_fp64_all_converged": t_batched,
+            "wall_s_plain_fp64_same_guesses_sequential": round(sum(p["wall_s"] for p in plain), 3),
+            "wall_s_batched_float_float": out["batched_float_float"]["wall_s"],
+            "converged_float_float": sum(1 for c in out["batched_float_float"]["steps_to_converge"] if c >= 0)}
+    return out
+
+
 def run_forms(pcf, gi, flush, stream, dev, args):
     """The batched, mixed-precision and learned forms of the method, each next to the plain
     FP64 method on the same work."""
@@ -292,7 +401,9 @@ def run_forms(pcf, gi, flush, stream, dev, args):
     ms = _timed_steps(sb, ub, DTAU, 10, flush, stream)
     out["batched"] = {"config": "64 guesses: 24x32x33x32 + 24x48x49x48 + 16x64x65x64, Re 400, FP64",
                       "gradient_evals_per_s": 64 * 10 / (ms * 1e-3), "ms_per_step": ms / 10,
-                      "mode_tile_autotuned": sb.mode_tile(), "points": int(24 * 33792 + 24 * 112896 + 16 * 266240)}
+                      "mode_tile_autotuned": sb.mode_tile(), "points": int(24 * 33792 + 24 * 112896 + 16 * 266240),
+                      "launches_per_step": sb.launches_per_step()}
+    out["batched"]["roofline"] = _form_roofline(sb, ub, flush, [(g[:3], g[3]) for g in grids], args)
     sb.close()
     # plane Poiseuille base flow u_b = (1 - y^2, 0, 0): the same step on the bench workload's shape
     sq = pcf.Solver(*GRID, batch=BATCH, Re=RE, dt=DT, dtau_hat=DTAU_HAT, base_flow=pcf.POISEUILLE)
@@ -339,11 +450,13 @@ def run_forms(pcf, gi, flush, stream, dev, args):
     g4 = (128, 97, 128)
     u4 = gi.random_perturbation(*g4, 0.1, 0)[None]
     res = {}
+    # dtau 0.001: at Re 1000 on this grid the explicit descent step is stable only below
+    # about 2e-3 (high-kx advection); the time per step does not depend on dtau
     for name, prec in (("fp64", 0), ("mixed", 1)):
         s4 = pcf.Solver(*g4, batch=1, Re=1000.0, precision=prec)
         u = torch.from_numpy(u4).to(dev)
-        s4.descent_step(u, DTAU, 2)
-        ms = _timed_steps(s4, u, DTAU, 5, flush, stream)
+        s4.descent_step(u, 0.001, 2)
+        ms = _timed_steps(s4, u, 0.001, 5, flush, stream)
         r, J = s4.residual(torch.from_numpy(u4).to(dev))
         res[name] = (ms / 5, r.cpu().numpy()[0], float(J[0]))
         s4.close()
@@ -394,28 +507,44 @@ def run_forms(pcf, gi, flush, stream, dev, args):
     sl = pcf.Solver(*g5, batch=64)
     up = torch.from_numpy(fresh).to(dev)
     ul = torch.from_numpy(fresh).to(dev)
-    taken = 0
-    t2 = time.perf_counter()
     rounds = args.learn_steps // 500
+    # plain branch: the same descent steps without proposals (520 per round)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
     for _ in range(rounds):
-        sp.descent_step(up, DTAU, 500, hist=False)
+        sp.descent_step(up, DTAU, 520, hist=False)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t2
+    Jp = sp.residual(up)[1].cpu().numpy()
+    # learned branch: 500 steps, then a proposal judged after 20 relaxation steps on both
+    # branches (features, network, rebuild of the state and the second relaxation priced in)
+    taken = 0
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    for _ in range(rounds):
         sl.descent_step(ul, DTAU, 500, hist=False)
         acc, _, _ = net.propose(sl, ul, sc, relax_steps=20, dtau=DTAU)
-        sp.descent_step(up, DTAU, 20, hist=False)
         taken += sum(acc)
     torch.cuda.synchronize()
-    t_inf = time.perf_counter() - t2
-    Jp = sp.residual(up)[1].cpu().numpy()
+    t_learn = time.perf_counter() - t3
     Jl = sl.residual(ul)[1].cpu().numpy()
+    # the plain branch continued for the learned branch's extra wall time
+    extra = max(0, int(round((t_learn - t_plain) / (t_plain / (rounds * 520)))))
+    if extra:
+        sp.descent_step(up, DTAU, extra, hist=False)
+    Jp_eq = sp.residual(up)[1].cpu().numpy()
     out["learned"] = {"config": f"FNO ({net.num_params()} params, width 32, 4 layers, GELU) trained on {n} "
                                 f"(state, state + {args.learn_lag * DTAU:g} tau) pairs from 64 streak/roll descent "
                                 "trajectories at 32x33x32 Re 400; judged on 64 fresh guesses (seeds 2000-2063)",
                       "pairs": n, "train_iters": args.learn_iters, "loss_first": losses[0],
                       "loss_last": float(np.mean(losses[-20:])), "data_s": t_data, "train_s": t_train,
                       "proposals_taken": taken, "proposals": 64 * rounds,
-                      "descent_steps_each": rounds * 520, "inference_s": t_inf,
-                      "J_plain_over_J_learned_geomean": float(np.exp(np.mean(np.log(Jp / Jl)))),
-                      "J_plain_median": float(np.median(Jp)), "J_learned_median": float(np.median(Jl))}
+                      "descent_steps_each": rounds * 520, "plain_branch_s": t_plain, "learned_branch_s": t_learn,
+                      "J_plain_over_J_learned_geomean_equal_steps": float(np.exp(np.mean(np.log(Jp / Jl)))),
+                      "plain_extra_steps_for_equal_wall_time": extra,
+                      "J_plain_over_J_learned_geomean_equal_wall_time": float(np.exp(np.mean(np.log(Jp_eq / Jl)))),
+                      "J_plain_median": float(np.median(Jp)), "J_learned_median": float(np.median(Jl)),
+                      "J_plain_equal_wall_time_median": float(np.median(Jp_eq))}
     net.close()
     return out
 
@@ -514,6 +643,9 @@ def run_ours(args):
             "J_final": [float(x) for x in J], "dmd_jumps": jumps,
             "J_reduction_geomean": float(np.exp(np.mean(np.log(np.array(J) / np.array(J0)))))}
 
+    if not args.no_ttc and ws == 1 and args.ttc_long_steps > 0:
+        ttc["perturbed_laminar_16"] = run_time_to_converge(pcf, gi, dev, args)
+
     # per-kernel CUDA-event timing (eager launches, same steps, same stream) for the roofline
     s.set_kernel_timing(True)
     nk = max(5, min(args.steps, 50))
@@ -551,6 +683,7 @@ def run_ours(args):
                 "roofline": roof, "clocks": ck, "wall_s": wall,
                 "J_after": [float(x) for x in J_last]}
         if ws == 1 and not args.no_forms:
+            args.fp64_peak_gflops = fp64
             line["forms"] = run_forms(pcf, gi, flush, stream, dev, args)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(15.0)
@@ -574,6 +707,8 @@ def main():
                     help="tile of the per-mode kernels (instances per group of the split kernels); 0 = autotune")
     ap.add_argument("--no-ttc", action="store_true", help="skip the time-to-converge runs")
     ap.add_argument("--ttc-steps", type=int, default=20000)
+    ap.add_argument("--ttc-long-steps", type=int, default=1000000,
+                    help="step budget of the time-to-converge runs on perturbed-laminar guesses (0: skip)")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched/mixed/learned forms")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal form")
     ap.add_argument("--no-robust", action="store_true", help="skip the DNS-guess robustness experiment")

@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define PCF_ABI_VERSION 1
+#define PCF_ABI_VERSION 2
 
 typedef enum {
   PCF_OK = 0,
@@ -87,6 +87,11 @@ typedef struct pcf_params {
   int symmetry;         /* pcf_symmetry mask enforced along the descent and the DNS (0: none).
                            s1 requires PCF_COUETTE (it maps the Poiseuille profile to its
                            negative); PCF_EINVAL otherwise. */
+  int plane_kernel;     /* x-z plane kernels of the mixed form (FP32): 0 = transforms in warp
+                           registers when every instance has nx, nz in {32, 64, 96, 128}, else
+                           the shared-memory Stockham kernels; 1 = always the Stockham kernels.
+                           The FP64 and float-float forms always use the Stockham kernels.
+                           pcf_plane_variant reports the choice. */
 } pcf_params;
 
 /* Base flows (§3.1 derives the method for a general laminar base flow u_b; §7 names plane
@@ -160,6 +165,10 @@ int pcf_mode_tile(const pcf_ctx* ctx);
  * the FP64 form times 2 against 3 and the mixed-precision form 0 against 1 at creation,
  * and each keeps the faster.  -1 for a NULL context. */
 int pcf_solve_variant(const pcf_ctx* ctx);
+
+/* x-z plane kernels the context launches: 0 shared-memory Stockham passes, 1 transforms in
+ * warp registers (FP32 form, see pcf_params.plane_kernel); -1 for a NULL context. */
+int pcf_plane_variant(const pcf_ctx* ctx);
 
 /* Release a context (waits for its stream).  NULL is ignored. */
 void pcf_destroy(pcf_ctx* ctx);

@@ -35,7 +35,8 @@ class _Params(ctypes.Structure):
                 ("Lx", ctypes.c_double), ("Lz", ctypes.c_double), ("Re", ctypes.c_double),
                 ("dt", ctypes.c_double), ("dtau_hat", ctypes.c_double),
                 ("precision", ctypes.c_int), ("modes_per_block", ctypes.c_int),
-                ("solve_kind", ctypes.c_int), ("base_flow", ctypes.c_int), ("symmetry", ctypes.c_int)]
+                ("solve_kind", ctypes.c_int), ("base_flow", ctypes.c_int), ("symmetry", ctypes.c_int),
+                ("plane_kernel", ctypes.c_int)]
 
 COUETTE, POISEUILLE = 0, 1   # laminar base flows u_b = (y,0,0) and (1-y^2,0,0)
 SYM_S1, SYM_S2 = 1, 2        # symmetries of §5.1 (bit mask): shift-and-rotate, shift-and-reflect
@@ -95,6 +96,7 @@ def load_library(path=None):
         "pcf_launches_per_call": (ctypes.c_longlong, [P, I]),
         "pcf_split_config": (I, [P, ctypes.POINTER(I)]),
         "pcf_solve_variant": (I, [P]),
+        "pcf_plane_variant": (I, [P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -147,14 +149,14 @@ class Solver:
                       "cheb_analysis_tc"]
 
     def __init__(self, nx, ny, nz, batch=1, Lx=LX_PAPER, Lz=LZ_PAPER, Re=400.0, dt=0.25, dtau_hat=0.25,
-                 precision=0, modes_per_block=0, solve_kind=0, base_flow=COUETTE, symmetry=0):
+                 precision=0, modes_per_block=0, solve_kind=0, base_flow=COUETTE, symmetry=0, plane_kernel=0):
         import torch
         self.lib = load_library()
         self.shape = state_shape(nx, ny, nz, batch)
         self.nx, self.ny, self.nz, self.batch = nx, ny, nz, batch
         self.dt, self.dtau_hat = dt, dtau_hat
         p = _Params(nx, ny, nz, batch, Lx, Lz, Re, dt, dtau_hat, precision, modes_per_block, solve_kind, base_flow,
-                    symmetry)
+                    symmetry, plane_kernel)
         h = ctypes.c_void_p()
         _check(self.lib.pcf_create(ctypes.byref(p), _stream(), ctypes.byref(h)))
         self._h = h
@@ -343,6 +345,10 @@ class Solver:
         cnt = (ctypes.c_longlong * n)()
         _check(self.lib.pcf_kernel_times(self._h, ms, cnt, n))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(self.KERNEL_CLASSES)}
+
+    def plane_variant(self):
+        """0 shared-memory Stockham plane kernels, 1 transforms in warp registers (FP32 form)."""
+        return int(self.lib.pcf_plane_variant(self._h))
 
     def solve_variant(self):
         """0 banded sweeps, 1 dense operators (single per-mode kernel), 2 dense split kernels."""

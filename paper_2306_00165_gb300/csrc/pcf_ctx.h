@@ -14,6 +14,7 @@ struct pcf_ctx {
   bool uniform = true;   // every instance on the same problem
   bool mixed = false;    // mixed-precision form (FP32 planes, split-BF16 Chebyshev, FP64 solves)
   int plane_kind = 0;    // arithmetic of the x-z plane kernels: 0 FP64, 1 FP32, 2 float-float
+  bool plane_warp = false;  // FP32 plane kernels with the transforms in warp registers
   double tuned_ms = 0.0; // autotuner: time of the chosen mode-kernel launch
   cudaStream_t user = nullptr, cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -29,7 +30,7 @@ struct pcf_ctx {
   int* pre_tcs = nullptr;   // tensor-core synthesis (mixed form)
   int* pre_tca = nullptr;   // tensor-core analysis (mixed form)
   int cta_synth11 = 0, cta_synth3 = 0, cta_prod = 0, cta_mode = 0, cta_tcs = 0, cta_tca = 0;
-  size_t sm_synth = 0, sm_prod = 0, sm_mode = 0, sm_tc = 0;
+  size_t sm_synth = 0, sm_prod = 0, sm_mode = 0, sm_tc = 0, sm_warp = 0;
   // split mode kernels (FP64 form with dense operators): instance groups and geometry
   bool split = false;
   int sgrp = 0;                 // largest instances per group

@@ -405,15 +405,21 @@ pcf_status launch_mode(pcf_ctx* c, int op, int sig, int step_index) {
 pcf_status launch_synth(pcf_ctx* c, int slot, int nf) {
   const int* pre = nf == kFieldsSynth ? c->pre_synth11 : c->pre_synth3;
   const int ctas = nf == kFieldsSynth ? c->cta_synth11 : c->cta_synth3;
-  return timed(c, slot == 0 ? 1 : 4,
-               [&] { launch_xzsynth(c->plane_kind, ctas, c->sm_synth, c->cs, li_of(c, pre), slot, nf); });
+  return timed(c, slot == 0 ? 1 : 4, [&] {
+    if (c->plane_warp) launch_xzsynth_warp(ctas, c->sm_synth, c->cs, li_of(c, pre), slot, nf);
+    else launch_xzsynth(c->plane_kind, ctas, c->sm_synth, c->cs, li_of(c, pre), slot, nf);
+  });
 }
 pcf_status launch_prodM(pcf_ctx* c) {
-  return timed(c, 2, [&] { launch_prod(c->plane_kind, false, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod)); });
+  return timed(c, 2, [&] {
+    if (c->plane_warp) launch_prod_warp(false, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod), -1);
+    else launch_prod(c->plane_kind, false, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod));
+  });
 }
 pcf_status launch_prodN(pcf_ctx* c, int step_index = -1) {
   return timed(c, 5, [&] {
-    launch_prod(c->plane_kind, true, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod), step_index);
+    if (c->plane_warp) launch_prod_warp(true, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod), step_index);
+    else launch_prod(c->plane_kind, true, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod), step_index);
   });
 }
 
@@ -619,7 +625,7 @@ static bool params_ok(const pcf_params* prm) {
   return grid_ok(prm->nx, prm->ny, prm->nz) && prm->batch >= 1 && prm->Re > 0 && prm->dt > 0 &&
          prm->dtau_hat > 0 && prm->Lx > 0 && prm->Lz > 0 && prm->solve_kind >= 0 && prm->solve_kind <= 4 &&
          prm->modes_per_block >= 0 && (prm->base_flow == PCF_COUETTE || prm->base_flow == PCF_POISEUILLE) &&
-         prm->symmetry >= 0 && prm->symmetry <= 3 &&
+         prm->symmetry >= 0 && prm->symmetry <= 3 && prm->plane_kernel >= 0 && prm->plane_kernel <= 1 &&
          !((prm->symmetry & PCF_SYM_S1) && prm->base_flow != PCF_COUETTE);
 }
 
@@ -1122,6 +1128,9 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
   std::vector<int> per11(B), per3(B), per1(B, 1), per_tcs(B), per_tca(B);
   size_t o_yv = 0, o_ph = 0, o_xz = 0, o_np = 0, o_fr = 0;
   c->split = !c->mixed;
+  // the FP32 form's plane kernels keep their transforms in warp registers wherever every
+  // instance's nx and nz allow it (unless the caller asks for the shared-memory kernels)
+  c->plane_warp = c->mixed && list[0].plane_kernel != 1;
   int b = 0;
   for (int k = 0; k < nlist; ++k)
     for (int r = 0; r < list[k].batch; ++r, ++b) {
@@ -1167,8 +1176,10 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       per_tcs[b] = kFieldsY * cheb_tc_tiles(I.nmodes);
       per_tca[b] = 3 * cheb_tc_tiles(I.nmodes);
       const int elem = c->mixed ? (int)sizeof(float2) : (int)sizeof(double2);
+      if (!plane_warp_ok(I)) c->plane_warp = false;
       c->sm_synth = std::max(c->sm_synth, smem_plane(I, elem));
       c->sm_prod = std::max(c->sm_prod, smem_plane(I, elem));
+      c->sm_warp = std::max(c->sm_warp, smem_plane_warp(I, elem));
       if (c->mixed) c->sm_tc = std::max(c->sm_tc, smem_cheb_tc(p.ny));
     }
   if (ctx_alloc(c, &c->dinst, (size_t)B)) return fail(PCF_ENOMEM);
@@ -1182,8 +1193,12 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       (st = upload_prefix(c, per_tca, &c->pre_tca, &c->cta_tca)) != PCF_OK)
     return fail(st);
   if (c->mixed && set_cheb_tc_smem(c->sm_tc)) return fail(PCF_ECUDA);
-  if (set_plane_smem(c->plane_kind, c->sm_synth, c->sm_prod))
+  if (c->plane_warp) {
+    c->sm_synth = c->sm_prod = c->sm_warp;
+    if (set_plane_warp_smem(c->sm_synth, c->sm_prod)) return fail(PCF_ECUDA);
+  } else if (set_plane_smem(c->plane_kind, c->sm_synth, c->sm_prod)) {
     return fail(PCF_ECUDA);
+  }
   const int want = list[0].modes_per_block;
   st = want > 0 ? set_mode_tiles(c, want) : autotune_tiles(c);
   if (st == PCF_OK && want > 0 && c->split) {
@@ -1211,6 +1226,8 @@ long long pcf_state_offset(const pcf_ctx* c, int instance) {
 }
 
 int pcf_mode_tile(const pcf_ctx* c) { return c ? (c->split ? c->sgrp : c->mpc) : 0; }
+
+int pcf_plane_variant(const pcf_ctx* c) { return c ? (c->plane_warp ? 1 : 0) : -1; }
 
 int pcf_solve_variant(const pcf_ctx* c) {
   if (!c) return -1;

@@ -74,6 +74,13 @@ void launch_xzsynth(int kind, int ctas, size_t smem, cudaStream_t s, LaunchInfo 
 void launch_prod(int kind, bool adj, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int step_index = -1);
 void launch_norm_planes(int kind, int ctas, cudaStream_t s, LaunchInfo li, int slot);
 cudaError_t set_plane_smem(int kind, size_t synth, size_t prod);
+// Plane kernels of the FP32 form with the x, z transforms in warp registers
+// (pcf_planes_warp.cu): nx, nz in {32, 64, 96, 128}.
+bool plane_warp_ok(const Inst& I);
+size_t smem_plane_warp(const Inst& I, int elem_bytes);
+void launch_xzsynth_warp(int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int slot, int nf);
+void launch_prod_warp(bool adj, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int step_index);
+cudaError_t set_plane_warp_smem(size_t synth, size_t prod);
 __global__ void k_mode(LaunchInfo li, int op, int sig, int mpc, int step_index);
 __global__ void k_norm_final(LaunchInfo li, double* out);
 __global__ void k_fp64_probe(double* out, int iters);

@@ -40,7 +40,7 @@ def test_host_only_queries(lib):
     lib.pcf_state_len.restype = ctypes.c_longlong
     lib.pcf_psi_len.restype = ctypes.c_longlong
     lib.pcf_status_str.restype = ctypes.c_char_p
-    assert lib.pcf_abi_version() == 1
+    assert lib.pcf_abi_version() == 2
     assert lib.pcf_state_len(32, 33, 32) == 3 * 19 * 10 * 33
     assert lib.pcf_state_len(30, 33, 32) == 0          # 30 = 2*3*5 has a radix-5 factor
     assert lib.pcf_state_len(32, 32, 32) == 0          # even ny rejected
