@@ -92,6 +92,10 @@ typedef struct pcf_params {
                            the shared-memory Stockham kernels; 1 = always the Stockham kernels.
                            The FP64 and float-float forms always use the Stockham kernels.
                            pcf_plane_variant reports the choice. */
+  int contraction_kernel; /* Chebyshev transforms of the mixed form (split-BF16, FP32
+                           accumulation): 0 = tcgen05 MMAs with the accumulator in tensor
+                           memory; 1 = warp-level mma.sync.  pcf_contraction_variant reports
+                           the choice.  Ignored by the other forms. */
 } pcf_params;
 
 /* Base flows (§3.1 derives the method for a general laminar base flow u_b; §7 names plane
@@ -169,6 +173,10 @@ int pcf_solve_variant(const pcf_ctx* ctx);
 /* x-z plane kernels the context launches: 0 shared-memory Stockham passes, 1 transforms in
  * warp registers (FP32 form, see pcf_params.plane_kernel); -1 for a NULL context. */
 int pcf_plane_variant(const pcf_ctx* ctx);
+
+/* Tensor-core instructions of the mixed form's Chebyshev transforms: 1 tcgen05 (tensor
+ * memory accumulator), 0 mma.sync, -1 for a NULL context (see pcf_params.contraction_kernel). */
+int pcf_contraction_variant(const pcf_ctx* ctx);
 
 /* Release a context (waits for its stream).  NULL is ignored. */
 void pcf_destroy(pcf_ctx* ctx);

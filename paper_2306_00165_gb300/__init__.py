@@ -36,7 +36,7 @@ class _Params(ctypes.Structure):
                 ("dt", ctypes.c_double), ("dtau_hat", ctypes.c_double),
                 ("precision", ctypes.c_int), ("modes_per_block", ctypes.c_int),
                 ("solve_kind", ctypes.c_int), ("base_flow", ctypes.c_int), ("symmetry", ctypes.c_int),
-                ("plane_kernel", ctypes.c_int)]
+                ("plane_kernel", ctypes.c_int), ("contraction_kernel", ctypes.c_int)]
 
 COUETTE, POISEUILLE = 0, 1   # laminar base flows u_b = (y,0,0) and (1-y^2,0,0)
 SYM_S1, SYM_S2 = 1, 2        # symmetries of §5.1 (bit mask): shift-and-rotate, shift-and-reflect
@@ -97,6 +97,7 @@ def load_library(path=None):
         "pcf_split_config": (I, [P, ctypes.POINTER(I)]),
         "pcf_solve_variant": (I, [P]),
         "pcf_plane_variant": (I, [P]),
+        "pcf_contraction_variant": (I, [P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -149,14 +150,15 @@ class Solver:
                       "cheb_analysis_tc"]
 
     def __init__(self, nx, ny, nz, batch=1, Lx=LX_PAPER, Lz=LZ_PAPER, Re=400.0, dt=0.25, dtau_hat=0.25,
-                 precision=0, modes_per_block=0, solve_kind=0, base_flow=COUETTE, symmetry=0, plane_kernel=0):
+                 precision=0, modes_per_block=0, solve_kind=0, base_flow=COUETTE, symmetry=0, plane_kernel=0,
+                 contraction_kernel=0):
         import torch
         self.lib = load_library()
         self.shape = state_shape(nx, ny, nz, batch)
         self.nx, self.ny, self.nz, self.batch = nx, ny, nz, batch
         self.dt, self.dtau_hat = dt, dtau_hat
         p = _Params(nx, ny, nz, batch, Lx, Lz, Re, dt, dtau_hat, precision, modes_per_block, solve_kind, base_flow,
-                    symmetry, plane_kernel)
+                    symmetry, plane_kernel, contraction_kernel)
         h = ctypes.c_void_p()
         _check(self.lib.pcf_create(ctypes.byref(p), _stream(), ctypes.byref(h)))
         self._h = h
@@ -349,6 +351,10 @@ class Solver:
     def plane_variant(self):
         """0 shared-memory Stockham plane kernels, 1 transforms in warp registers (FP32 form)."""
         return int(self.lib.pcf_plane_variant(self._h))
+
+    def contraction_variant(self):
+        """1 tcgen05 (tensor-memory accumulator), 0 mma.sync: the mixed form's Chebyshev transforms."""
+        return int(self.lib.pcf_contraction_variant(self._h))
 
     def solve_variant(self):
         """0 banded sweeps, 1 dense operators (single per-mode kernel), 2 dense split kernels."""

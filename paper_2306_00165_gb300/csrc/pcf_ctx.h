@@ -15,6 +15,7 @@ struct pcf_ctx {
   bool mixed = false;    // mixed-precision form (FP32 planes, split-BF16 Chebyshev, FP64 solves)
   int plane_kind = 0;    // arithmetic of the x-z plane kernels: 0 FP64, 1 FP32, 2 float-float
   bool plane_warp = false;  // FP32 plane kernels with the transforms in warp registers
+  bool tc05 = false;        // Chebyshev contractions of the mixed form on tcgen05 (else mma.sync)
   double tuned_ms = 0.0; // autotuner: time of the chosen mode-kernel launch
   cudaStream_t user = nullptr, cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;

@@ -424,10 +424,16 @@ pcf_status launch_prodN(pcf_ctx* c, int step_index = -1) {
 }
 
 pcf_status launch_tc_synth(pcf_ctx* c, int slot) {
-  return timed(c, 12, [&] { launch_cheb_synth_tc(c->cta_tcs, c->sm_tc, c->cs, li_of(c, c->pre_tcs), slot); });
+  return timed(c, 12, [&] {
+    if (c->tc05) launch_cheb_synth_tc05(c->cta_tcs, c->sm_tc, c->cs, li_of(c, c->pre_tcs), slot);
+    else launch_cheb_synth_tc(c->cta_tcs, c->sm_tc, c->cs, li_of(c, c->pre_tcs), slot);
+  });
 }
 pcf_status launch_tc_analysis(pcf_ctx* c) {
-  return timed(c, 13, [&] { launch_cheb_analysis_tc(c->cta_tca, c->sm_tc, c->cs, li_of(c, c->pre_tca)); });
+  return timed(c, 13, [&] {
+    if (c->tc05) launch_cheb_analysis_tc05(c->cta_tca, c->sm_tc, c->cs, li_of(c, c->pre_tca));
+    else launch_cheb_analysis_tc(c->cta_tca, c->sm_tc, c->cs, li_of(c, c->pre_tca));
+  });
 }
 // split mode kernels of the FP64 descent step
 GroupLaunch gl_of(pcf_ctx* c, const int* pre) { return GroupLaunch{c->dinst, pre, c->d_groups, c->ngroups}; }
@@ -626,6 +632,7 @@ static bool params_ok(const pcf_params* prm) {
          prm->dtau_hat > 0 && prm->Lx > 0 && prm->Lz > 0 && prm->solve_kind >= 0 && prm->solve_kind <= 4 &&
          prm->modes_per_block >= 0 && (prm->base_flow == PCF_COUETTE || prm->base_flow == PCF_POISEUILLE) &&
          prm->symmetry >= 0 && prm->symmetry <= 3 && prm->plane_kernel >= 0 && prm->plane_kernel <= 1 &&
+         prm->contraction_kernel >= 0 && prm->contraction_kernel <= 1 &&
          !((prm->symmetry & PCF_SYM_S1) && prm->base_flow != PCF_COUETTE);
 }
 
@@ -1131,6 +1138,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
   // the FP32 form's plane kernels keep their transforms in warp registers wherever every
   // instance's nx and nz allow it (unless the caller asks for the shared-memory kernels)
   c->plane_warp = c->mixed && list[0].plane_kernel != 1;
+  c->tc05 = c->mixed && list[0].contraction_kernel != 1;
   int b = 0;
   for (int k = 0; k < nlist; ++k)
     for (int r = 0; r < list[k].batch; ++r, ++b) {
@@ -1180,7 +1188,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       c->sm_synth = std::max(c->sm_synth, smem_plane(I, elem));
       c->sm_prod = std::max(c->sm_prod, smem_plane(I, elem));
       c->sm_warp = std::max(c->sm_warp, smem_plane_warp(I, elem));
-      if (c->mixed) c->sm_tc = std::max(c->sm_tc, smem_cheb_tc(p.ny));
+      if (c->mixed) c->sm_tc = std::max(c->sm_tc, c->tc05 ? smem_cheb_tc05(p.ny) : smem_cheb_tc(p.ny));
     }
   if (ctx_alloc(c, &c->dinst, (size_t)B)) return fail(PCF_ENOMEM);
   int dummy;
@@ -1192,7 +1200,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       (st = upload_prefix(c, per_tcs, &c->pre_tcs, &c->cta_tcs)) != PCF_OK ||
       (st = upload_prefix(c, per_tca, &c->pre_tca, &c->cta_tca)) != PCF_OK)
     return fail(st);
-  if (c->mixed && set_cheb_tc_smem(c->sm_tc)) return fail(PCF_ECUDA);
+  if (c->mixed && (c->tc05 ? set_cheb_tc05_smem(c->sm_tc) : set_cheb_tc_smem(c->sm_tc))) return fail(PCF_ECUDA);
   if (c->plane_warp) {
     c->sm_synth = c->sm_prod = c->sm_warp;
     if (set_plane_warp_smem(c->sm_synth, c->sm_prod)) return fail(PCF_ECUDA);
@@ -1228,6 +1236,8 @@ long long pcf_state_offset(const pcf_ctx* c, int instance) {
 int pcf_mode_tile(const pcf_ctx* c) { return c ? (c->split ? c->sgrp : c->mpc) : 0; }
 
 int pcf_plane_variant(const pcf_ctx* c) { return c ? (c->plane_warp ? 1 : 0) : -1; }
+
+int pcf_contraction_variant(const pcf_ctx* c) { return c ? (c->tc05 ? 1 : 0) : -1; }
 
 int pcf_solve_variant(const pcf_ctx* c) {
   if (!c) return -1;

@@ -93,6 +93,12 @@ size_t smem_cheb_tc(int ny);
 void launch_cheb_synth_tc(int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int slot);
 void launch_cheb_analysis_tc(int ctas, size_t smem, cudaStream_t s, LaunchInfo li);
 cudaError_t set_cheb_tc_smem(size_t smem);
+// The same contractions on the 5th-generation tensor cores (tcgen05, TMEM accumulator;
+// pcf_cheb_tc05.cu), same CTA map.
+size_t smem_cheb_tc05(int ny);
+void launch_cheb_synth_tc05(int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int slot);
+void launch_cheb_analysis_tc05(int ctas, size_t smem, cudaStream_t s, LaunchInfo li);
+cudaError_t set_cheb_tc05_smem(size_t smem);
 int cheb_tc_tiles(int nmodes);
 
 // Split mode kernels of the FP64 descent step (Chebyshev analysis, dense Stokes solve,

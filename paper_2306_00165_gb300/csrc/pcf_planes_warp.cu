@@ -152,6 +152,27 @@ __device__ __forceinline__ void store_seg(float* p, int E, const float* v) {
   }
 }
 
+// Two adjacent complex values as one 16-byte shared-memory access (float2 pairs; p is
+// 16-byte aligned), else two accesses.
+__device__ __forceinline__ void st_pair(float2* p, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = make_float2(v.x, v.y);
+  b = make_float2(v.z, v.w);
+}
+template <class C>
+__device__ __forceinline__ void st_pair(C* p, C a, C b) {
+  p[0] = a;
+  p[1] = b;
+}
+template <class C>
+__device__ __forceinline__ void ld_pair(const C* p, C& a, C& b) {
+  a = p[0];
+  b = p[1];
+}
+
 // Shared-memory plan: staged spectral values S[Mx][SP] (SP = Mz rounded up to odd), x-stage
 // rows G[Mz][LG] (LG = nx + 2: 16-byte aligned rows and conflict-free 16-byte column
 // walks), then the twiddles of x and z and a reduction scratch.
@@ -164,7 +185,7 @@ __host__ __device__ inline WarpPlan warp_plan(const Inst& I, int elem) {
   w.SP = I.Mz | 1;
   w.LG = I.nx + 2;
   w.S = 0;
-  w.G = w.S + (size_t)I.Mx * w.SP;
+  w.G = (w.S + (size_t)I.Mx * w.SP + 1) & ~(size_t)1;  // even: 16-byte aligned pairs of float2
   w.twx = w.G + (size_t)I.Mz * w.LG;
   w.twz = w.twx + I.nx;
   w.red = w.twz + I.nz;
@@ -240,9 +261,16 @@ __global__ void __launch_bounds__(kWarpPlaneThreads, 3) k_xzsynth_w(LaunchInfo l
       }
     fft_dif(x, EX, twx, w32, true, lane);
     C* g = G + (size_t)p * LG + EX * lane;
+    if (EX == 4) {
+      st_pair(g, x[0], x[1]);
+      st_pair(g + 2, x[2], x[3]);
+    } else if (EX == 2) {
+      st_pair(g, x[0], x[1]);
+    } else {
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
-      if (s < EX) g[s] = x[s];
+      for (int s = 0; s < 3; ++s)
+        if (s < EX) g[s] = x[s];
+    }
   }
   __syncthreads();
   // z stage: row pair (x1, x2) -> one complex row h_z = G_z[x1] + i G_z[x2] with
@@ -260,9 +288,7 @@ __global__ void __launch_bounds__(kWarpPlaneThreads, 3) k_xzsynth_w(LaunchInfo l
         const int p = lo ? z : nz - z;
         C g1 = Cx<T>::mk(0, 0), g2 = g1;
         if (lo || hi) {
-          const C* gp = G + (size_t)p * LG + x1;
-          g1 = gp[0];
-          g2 = gp[1];
+          ld_pair(G + (size_t)p * LG + x1, g1, g2);
         }
         if (z == 0) g1.y = g2.y = T(0.0);
         const T sg = lo ? T(1.0) : T(-1.0);
@@ -405,9 +431,8 @@ __device__ __forceinline__ void prod_row_pair(const Inst& I, const T* U, const T
       const int p = lane + 32 * s;
       if (p <= Kz) {
         const C hp = h[s];
-        C* d = X + (size_t)p * LG + x1;
-        d[0] = Cx<T>::mk(half * (hp.x + hm.x), half * (hp.y - hm.y));
-        d[1] = Cx<T>::mk(half * (hp.y + hm.y), -half * (hp.x - hm.x));
+        st_pair(X + (size_t)p * LG + x1, Cx<T>::mk(half * (hp.x + hm.x), half * (hp.y - hm.y)),
+                Cx<T>::mk(half * (hp.y + hm.y), -half * (hp.x - hm.x)));
       }
     }
 }

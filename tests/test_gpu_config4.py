@@ -62,12 +62,14 @@ def ref():
 @pytest.mark.parametrize("precision,plane_kernel,tol,jtol", [(0, 0, TOL, TOL), (1, 0, MIXED_TOL, 1e-5),
                                                               (1, 1, MIXED_TOL, 1e-5)])
 def test_residual_and_gradient_against_the_oracle(pcf, ref, precision, plane_kernel, tol, jtol):
-    """plane_kernel 0 in the mixed form: the x-z transforms in warp registers; 1: the
-    shared-memory Stockham kernels."""
+    """plane_kernel 0 in the mixed form: the x-z transforms in warp registers and the
+    Chebyshev transforms on tcgen05; 1: the shared-memory Stockham kernels and mma.sync."""
     o, u, r_ref, J_ref, f_ref = ref
-    s = pcf.Solver(*GRID, batch=1, Re=RE, precision=precision, plane_kernel=plane_kernel)
+    s = pcf.Solver(*GRID, batch=1, Re=RE, precision=precision, plane_kernel=plane_kernel,
+                   contraction_kernel=plane_kernel)
     if precision == 1:
         assert s.plane_variant() == 1 - plane_kernel
+        assert s.contraction_variant() == 1 - plane_kernel
     ud = torch.from_numpy(u[None]).cuda()
     r, J = s.residual(ud)
     f = s.adjoint_gradient(ud, r)

@@ -30,17 +30,21 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-@pytest.mark.parametrize("grid,plane_kernel", [((16, 17, 16), 0), ((32, 33, 32), 0), ((32, 33, 32), 1),
-                                               ((48, 49, 48), 0), ((64, 49, 32), 0), ((64, 49, 32), 1),
-                                               ((96, 33, 64), 0)])
-def test_mixed_residual_and_gradient_per_field(pcf, grid, plane_kernel):
+@pytest.mark.parametrize("grid,plane_kernel,contraction_kernel",
+                         [((16, 17, 16), 0, 0), ((16, 17, 16), 0, 1), ((32, 33, 32), 0, 0), ((32, 33, 32), 1, 1),
+                          ((48, 49, 48), 0, 0), ((64, 49, 32), 0, 0), ((64, 49, 32), 1, 1), ((96, 33, 64), 0, 0),
+                          ((32, 113, 32), 0, 0)])
+def test_mixed_residual_and_gradient_per_field(pcf, grid, plane_kernel, contraction_kernel):
     """Both FP32 plane-kernel variants (transforms in warp registers where nx, nz allow it;
-    shared-memory Stockham passes otherwise or on request) against the oracle."""
+    shared-memory Stockham passes otherwise or on request) and both tensor-core paths of the
+    Chebyshev transforms (tcgen05 with a tensor-memory accumulator, or mma.sync) against the
+    oracle; ny = 113 fills the 128-row MMA tile."""
     o = PCFOracle(*grid)
     u = gi.batch(gi.random_perturbation, [0, 1], *grid, 0.1)
-    s = pcf.Solver(*grid, batch=2, precision=1, plane_kernel=plane_kernel)
+    s = pcf.Solver(*grid, batch=2, precision=1, plane_kernel=plane_kernel, contraction_kernel=contraction_kernel)
     warp_ok = grid[0] in (32, 64, 96, 128) and grid[2] in (32, 64, 96, 128)
     assert s.plane_variant() == (1 if warp_ok and plane_kernel == 0 else 0)
+    assert s.contraction_variant() == 1 - contraction_kernel
     ud = torch.from_numpy(u).cuda()
     r, J = s.residual(ud)
     f = s.adjoint_gradient(ud, r)
