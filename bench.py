@@ -483,9 +483,12 @@ def run_forms(pcf, gi, flush, stream, dev, args):
     ss.descent_step(us_, DTAU, 3)
     ms = _timed_steps(ss, us_, DTAU, 50, flush, stream)
     out["symmetric"] = {"config": "8 streak/roll guesses projected onto the s1,s2-symmetric subspace and kept there "
-                                  "(one projection launch per step), 32x33x32, Re 400, FP64",
+                                  "(per-mode work on the modes m >= 0 when the split kernels run; "
+                                  "modes m < 0 rebuilt from the s2 relation), 32x33x32, Re 400, FP64",
                         "gradient_evals_per_s": BATCH * 50 / (ms * 1e-3), "ms_per_step": ms / 50,
-                        "launches_per_step": ss.launches_per_step()}
+                        "launches_per_step": ss.launches_per_step(),
+                        "solve_variant": ss.solve_variant(),
+                        "modes_per_instance": ss.symmetric_modes()}
     ss.close()
     if not args.no_robust:
         out["robustness"] = run_robustness(pcf, gi, dev, args)

@@ -178,6 +178,14 @@ int pcf_plane_variant(const pcf_ctx* ctx);
  * memory accumulator), 0 mma.sync, -1 for a NULL context (see pcf_params.contraction_kernel). */
 int pcf_contraction_variant(const pcf_ctx* ctx);
 
+/* Fourier modes the per-mode kernels of one descent step process per instance: Mx*Mz, or
+ * (Kx+1)*Mz (the modes m >= 0) when every instance enforces s2 (pcf_params.symmetry) and the
+ * step runs the split per-mode kernels.  A state invariant under s2 satisfies
+ * a_{-m,p,n} = e2_c (-1)^m conj(a_{m,p,n}) with e2 = (+1, +1, -1) for (u, v, w); the step then
+ * computes the modes m >= 0, mirrors their y-values, and rebuilds the modes m < 0 of the
+ * updated state in its projection.  -1 for a NULL context. */
+int pcf_symmetric_modes(const pcf_ctx* ctx);
+
 /* Release a context (waits for its stream).  NULL is ignored. */
 void pcf_destroy(pcf_ctx* ctx);
 

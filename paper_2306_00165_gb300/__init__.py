@@ -98,6 +98,7 @@ def load_library(path=None):
         "pcf_solve_variant": (I, [P]),
         "pcf_plane_variant": (I, [P]),
         "pcf_contraction_variant": (I, [P]),
+        "pcf_symmetric_modes": (I, [P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -355,6 +356,10 @@ class Solver:
     def contraction_variant(self):
         """1 tcgen05 (tensor-memory accumulator), 0 mma.sync: the mixed form's Chebyshev transforms."""
         return int(self.lib.pcf_contraction_variant(self._h))
+
+    def symmetric_modes(self):
+        """Fourier modes per instance the per-mode kernels of a descent step process."""
+        return int(self.lib.pcf_symmetric_modes(self._h))
 
     def solve_variant(self):
         """0 banded sweeps, 1 dense operators (single per-mode kernel), 2 dense split kernels."""

@@ -17,9 +17,9 @@
 // stride-dimension byte offset (next 8 rows) is 128.  Every 16-byte chunk of a row (8
 // consecutive K elements) is one shared-memory store.
 //
-// The accumulator (128 lanes x 64 FP32 columns) is read back by the four warps (warp w owns
-// TMEM lanes 32w..32w+31, i.e. output rows), staged in shared memory and written out row by
-// row with coalesced stores.  The wait for the MMAs is bounded: after about two seconds the
+// The accumulator (128 lanes x 64 FP32 columns) is read back by the eight warps (warp w owns
+// TMEM lanes 32 (w mod 4) .. + 31, i.e. output rows, and columns 32 (w / 4) .. + 31), staged
+// in shared memory and written out row by row with coalesced stores.  The wait for the MMAs is bounded: after about two seconds the
 // CTA gives up, writes NaN to its outputs (the residual norm then reports PCF_ENAN), frees its
 // tensor memory and returns.
 #include <cuda_bf16.h>
@@ -33,7 +33,7 @@ namespace {
 
 constexpr int kT5Rows = 128;    // MMA M (output rows, padded)
 constexpr int kT5Cols = 64;     // MMA N (columns per CTA)
-constexpr int kT5Threads = 128;
+constexpr int kT5Threads = 256;  // 8 warps: warp w reads TMEM lanes 32 (w % 4).., column half w / 4
 
 __host__ __device__ inline int pad16_5(int n) { return (n + 15) & ~15; }
 
@@ -110,8 +110,9 @@ __global__ void __launch_bounds__(kT5Threads) k_cheb_tc05(LaunchInfo li, int slo
   const int mat = SYN ? (q < 3 ? 0 : 1) : 2;
   const uint4* Ahg = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(I.tcA) + (size_t)(2 * mat) * P * P);
   const uint4* Alg = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(I.tcA) + (size_t)(2 * mat + 1) * P * P);
+  // consecutive threads take consecutive rows of one K chunk: contiguous 16-byte stores
   for (int t = threadIdx.x; t < kT5Rows * KC; t += blockDim.x) {
-    const int r = t / KC, kc = t - r * KC;
+    const int kc = t / kT5Rows, r = t - kc * kT5Rows;
     uint4 h = make_uint4(0u, 0u, 0u, 0u), l = h;
     if (r < P) {
       h = Ahg[(size_t)r * KC + kc];
@@ -205,10 +206,10 @@ __global__ void __launch_bounds__(kT5Threads) k_cheb_tc05(LaunchInfo li, int slo
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   // tcgen05.ld is warp-collective: read the accumulator only if every lane saw the MMAs finish
   if (__all_sync(0xffffffffu, done)) {
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
+    {
+      const int quarter = warp & 3, half = warp >> 2;
       uint32_t r[32];
-      const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + 32u * half;
+      const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + 32u * half;
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
           "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(kT5Threads) k_cheb_tc05(LaunchInfo li, int slo
             "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      float* row = sD + (size_t)(32 * warp + lane) * (kT5Cols + 1) + 32 * half;
+      float* row = sD + (size_t)(32 * quarter + lane) * (kT5Cols + 1) + 32 * half;
 #pragma unroll
       for (int c = 0; c < 32; ++c) row[c] = __uint_as_float(r[c]);
     }

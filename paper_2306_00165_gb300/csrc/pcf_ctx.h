@@ -16,6 +16,13 @@ struct pcf_ctx {
   int plane_kind = 0;    // arithmetic of the x-z plane kernels: 0 FP64, 1 FP32, 2 float-float
   bool plane_warp = false;  // FP32 plane kernels with the transforms in warp registers
   bool tc05 = false;        // Chebyshev contractions of the mixed form on tcgen05 (else mma.sync)
+  // descent steps in the symmetric subspace run the per-mode kernels on the modes m >= 0 only
+  // (every instance enforces s2; split FP64 or float-float kernels); the reduced CTA maps:
+  bool reduced = false;
+  int* pre_ya_r = nullptr;
+  int* pre_yy_r = nullptr;
+  int* pre_ys_r = nullptr;
+  int cta_ya_r = 0, cta_yy_r = 0, cta_ys_r = 0, grid_ys_r = 0;
   double tuned_ms = 0.0; // autotuner: time of the chosen mode-kernel launch
   cudaStream_t user = nullptr, cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;

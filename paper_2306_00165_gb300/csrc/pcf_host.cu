@@ -436,15 +436,23 @@ pcf_status launch_tc_analysis(pcf_ctx* c) {
   });
 }
 // split mode kernels of the FP64 descent step
-GroupLaunch gl_of(pcf_ctx* c, const int* pre) { return GroupLaunch{c->dinst, pre, c->d_groups, c->ngroups}; }
-pcf_status launch_split_analysis(pcf_ctx* c, int op) {
-  return timed(c, 7,
-               [&] { launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), op, c->plane_kind == 2, c->smt); });
+GroupLaunch gl_of(pcf_ctx* c, const int* pre, int red = 0) {
+  return GroupLaunch{c->dinst, pre, c->d_groups, c->ngroups, red};
 }
-GroupLaunch gl_solve(pcf_ctx* c) { return GroupLaunch{c->dinst, c->pre_ys, c->d_groups_s, c->ngroups_s}; }
-pcf_status launch_split_solve(pcf_ctx* c, int op) {
+// red: the reduced launch of a symmetric descent step (modes m >= 0 only)
+pcf_status launch_split_analysis(pcf_ctx* c, int op, bool red = false) {
+  return timed(c, 7, [&] {
+    launch_yanalysis(red ? c->cta_ya_r : c->cta_ya, c->sm_ya, c->cs, gl_of(c, red ? c->pre_ya_r : c->pre_ya, red), op,
+                     c->plane_kind == 2, c->smt);
+  });
+}
+GroupLaunch gl_solve(pcf_ctx* c, bool red = false) {
+  return GroupLaunch{c->dinst, red ? c->pre_ys_r : c->pre_ys, c->d_groups_s, c->ngroups_s, red ? 1 : 0};
+}
+pcf_status launch_split_solve(pcf_ctx* c, int op, bool red = false) {
   return timed(c, op == MODE_PHI ? 3 : 6, [&] {
-    launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_solve(c), op);
+    launch_ysolve(red ? c->grid_ys_r : c->grid_ys, red ? c->cta_ys_r : c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys,
+                  c->cs, gl_solve(c, red), op);
   });
 }
 pcf_status launch_fused_step(pcf_ctx* c, int op) {
@@ -454,12 +462,11 @@ pcf_status launch_fused_step(pcf_ctx* c, int op) {
 pcf_status launch_split_jnorm(pcf_ctx* c, int step_index) {
   return timed(c, 9, [&] { launch_jnorm(c->B, c->cs, c->dinst, step_index); });
 }
-pcf_status launch_split_synth(pcf_ctx* c, int slot, int in_step) {
-  return timed(c, in_step ? 8 : 0,
-               [&] {
-                 launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), slot, in_step,
-                                     c->plane_kind == 2, c->smt_y);
-               });
+pcf_status launch_split_synth(pcf_ctx* c, int slot, int in_step, bool red = false) {
+  return timed(c, in_step ? 8 : 0, [&] {
+    launch_ysynth_split(red ? c->cta_yy_r : c->cta_yy, c->sm_yy, c->cs, gl_of(c, red ? c->pre_yy_r : c->pre_yy, red),
+                        slot, in_step, c->plane_kind == 2, c->smt_y);
+  });
 }
 
 // y-synthesis of the state (slot 0) or of r1 (slot 1) in either form
@@ -470,8 +477,8 @@ pcf_status launch_ysynth(pcf_ctx* c, int slot) {
 }
 
 // projection onto the symmetric subspace: each instance's own mask (mask_override < 0) or mask
-pcf_status launch_sym(pcf_ctx* c, int mask_override) {
-  return timed(c, 10, [&] { launch_symmetrize(c->sym_ctas, c->B, c->cs, c->dinst, mask_override); });
+pcf_status launch_sym(pcf_ctx* c, int mask_override, bool red = false) {
+  return timed(c, 10, [&] { launch_symmetrize(c->sym_ctas, c->B, c->cs, c->dinst, mask_override, red ? 1 : 0); });
 }
 
 pcf_status check_launch() {
@@ -538,19 +545,23 @@ pcf_status step_body(pcf_ctx* c, int s) {
     return PCF_OK;
   }
   if (c->split) {
+    // in the symmetric subspace of s2 the per-mode work covers the modes m >= 0; the
+    // synthesis mirrors their y-values to -m, and the projection after the update rebuilds
+    // the state's modes -m
+    const bool red = c->reduced;
     // the y-values of the state the previous step updated (the call's first step reads the
     // synthesis done at the call's start)
-    if (s > 0) PCF_TRY(launch_split_synth(c, 0, 1));
+    if (s > 0) PCF_TRY(launch_split_synth(c, 0, 1, red));
     PCF_TRY(launch_synth(c, 0, kFieldsSynth));
     PCF_TRY(launch_prodM(c));
-    PCF_TRY(launch_split_analysis(c, MODE_PHI));
-    PCF_TRY(launch_split_solve(c, MODE_PHI));
-    PCF_TRY(launch_split_synth(c, 1, 1));
+    PCF_TRY(launch_split_analysis(c, MODE_PHI, red));
+    PCF_TRY(launch_split_solve(c, MODE_PHI, red));
+    PCF_TRY(launch_split_synth(c, 1, 1, red));
     PCF_TRY(launch_synth(c, 1, kFieldsSynth));
     PCF_TRY(launch_prodN(c, s));  // with J, its history entry and the convergence mask
-    PCF_TRY(launch_split_analysis(c, MODE_PSI_UPDATE));
-    PCF_TRY(launch_split_solve(c, MODE_PSI_UPDATE));
-    if (c->any_sym) PCF_TRY(launch_sym(c, -1));
+    PCF_TRY(launch_split_analysis(c, MODE_PSI_UPDATE, red));
+    PCF_TRY(launch_split_solve(c, MODE_PSI_UPDATE, red));
+    if (c->any_sym) PCF_TRY(launch_sym(c, -1, red));
     return PCF_OK;
   }
   PCF_TRY(launch_synth(c, 0, kFieldsSynth));
@@ -776,16 +787,24 @@ static pcf_status set_solve_groups(pcf_ctx* c, int G) {
   const int ng = (int)groups.size();
   int gmax = 1;
   for (const int2& gq : groups) gmax = std::max(gmax, gq.y);
-  std::vector<int> ps(ng + 1, 0);
-  for (int q = 0; q < ng; ++q) ps[q + 1] = ps[q] + split_ctas_per_group(1, c->hinst[groups[q].x].nmodes, 1);
+  std::vector<int> ps(ng + 1, 0), psr(ng + 1, 0);
+  for (int q = 0; q < ng; ++q) {
+    const Inst& I = c->hinst[groups[q].x];
+    ps[q + 1] = ps[q] + split_ctas_per_group(1, I.nmodes, 1);
+    psr[q + 1] = psr[q] + split_ctas_per_group(1, (I.Kx + 1) * I.Mz, 1);  // modes m >= 0
+  }
   // the persistent solve lays out every item in buffers sized for the largest grid and group
   const size_t ss = smem_ysolve(Nmax, gmax);
   if (ss > 227 * 1024) return PCF_ENOTSUP;
   if (!c->d_groups_s) {
-    if (ctx_alloc(c, &c->d_groups_s, (size_t)c->B) || ctx_alloc(c, &c->pre_ys, (size_t)c->B + 1)) return PCF_ENOMEM;
+    if (ctx_alloc(c, &c->d_groups_s, (size_t)c->B) || ctx_alloc(c, &c->pre_ys, (size_t)c->B + 1) ||
+        ctx_alloc(c, &c->pre_ys_r, (size_t)c->B + 1))
+      return PCF_ENOMEM;
   }
   PCF_CUDA(cudaMemcpy(c->d_groups_s, groups.data(), sizeof(int2) * ng, cudaMemcpyHostToDevice));
   PCF_CUDA(cudaMemcpy(c->pre_ys, ps.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
+  PCF_CUDA(cudaMemcpy(c->pre_ys_r, psr.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
+  c->cta_ys_r = psr[ng];
   c->sgrp_s = G;
   c->ngroups_s = ng;
   c->cta_ys = ps[ng];
@@ -798,6 +817,7 @@ static pcf_status set_solve_groups(pcf_ctx* c, int G) {
   PCF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int per_sm = std::max(1, ysolve_ctas_per_sm(ss));
   c->grid_ys = std::min(c->cta_ys, nsm * per_sm);
+  c->grid_ys_r = std::min(c->cta_ys_r, nsm * per_sm);
   return PCF_OK;
 }
 
@@ -816,22 +836,30 @@ static pcf_status set_split_groups(pcf_ctx* c, int G, int mt = 1, int mt_y = 0) 
   while (mt > 1 && split_col_pad(gmax) * mt > 32) mt >>= 1;
   mt_y = mt_y < 1 ? mt : mt_y;
   while (mt_y > 1 && split_col_pad(gmax) * mt_y > 32) mt_y >>= 1;
-  std::vector<int> pa(ng + 1, 0), py(ng + 1, 0), pf(ng + 1, 0);
+  std::vector<int> pa(ng + 1, 0), py(ng + 1, 0), pf(ng + 1, 0), par(ng + 1, 0), pyr(ng + 1, 0);
   size_t sa = 0, sy = 0;
   for (int q = 0; q < ng; ++q) {
     const Inst& I = c->hinst[groups[q].x];
+    const int nrun = (I.Kx + 1) * I.Mz;  // the reduced launches: modes m >= 0
     pf[q + 1] = pf[q] + I.nmodes;
     pa[q + 1] = pa[q] + split_ctas_per_group(0, I.nmodes, mt);
     py[q + 1] = py[q] + split_ctas_per_group(2, I.nmodes, mt_y);
+    par[q + 1] = par[q] + split_ctas_per_group(0, nrun, mt);
+    pyr[q + 1] = pyr[q] + split_ctas_per_group(2, nrun, mt_y);
     sa = std::max(sa, smem_yanalysis(I.N, groups[q].y, mt));
     sy = std::max(sy, smem_ysynth(I.N, groups[q].y, mt_y));
   }
   if (std::max(sa, sy) > 227 * 1024) return PCF_ENOTSUP;
   if (!c->d_groups) {
     if (ctx_alloc(c, &c->d_groups, (size_t)c->B) || ctx_alloc(c, &c->pre_ya, (size_t)c->B + 1) ||
-        ctx_alloc(c, &c->pre_yy, (size_t)c->B + 1) || ctx_alloc(c, &c->pre_yf, (size_t)c->B + 1))
+        ctx_alloc(c, &c->pre_yy, (size_t)c->B + 1) || ctx_alloc(c, &c->pre_yf, (size_t)c->B + 1) ||
+        ctx_alloc(c, &c->pre_ya_r, (size_t)c->B + 1) || ctx_alloc(c, &c->pre_yy_r, (size_t)c->B + 1))
       return PCF_ENOMEM;
   }
+  PCF_CUDA(cudaMemcpy(c->pre_ya_r, par.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
+  PCF_CUDA(cudaMemcpy(c->pre_yy_r, pyr.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
+  c->cta_ya_r = par[ng];
+  c->cta_yy_r = pyr[ng];
   PCF_CUDA(cudaMemcpy(c->pre_yf, pf.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice));
   c->cta_yf = pf[ng];
   c->sm_yf = smem_ystep(Nmax, gmax);
@@ -1139,6 +1167,10 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
   // instance's nx and nz allow it (unless the caller asks for the shared-memory kernels)
   c->plane_warp = c->mixed && list[0].plane_kernel != 1;
   c->tc05 = c->mixed && list[0].contraction_kernel != 1;
+  // symmetric descent on the modes m >= 0 when every instance enforces s2 (split kernels)
+  c->reduced = true;
+  for (int k = 0; k < nlist; ++k)
+    if (!(list[k].symmetry & PCF_SYM_S2)) c->reduced = false;
   int b = 0;
   for (int k = 0; k < nlist; ++k)
     for (int r = 0; r < list[k].batch; ++r, ++b) {
@@ -1238,6 +1270,11 @@ int pcf_mode_tile(const pcf_ctx* c) { return c ? (c->split ? c->sgrp : c->mpc) :
 int pcf_plane_variant(const pcf_ctx* c) { return c ? (c->plane_warp ? 1 : 0) : -1; }
 
 int pcf_contraction_variant(const pcf_ctx* c) { return c ? (c->tc05 ? 1 : 0) : -1; }
+
+int pcf_symmetric_modes(const pcf_ctx* c) {
+  if (!c) return -1;
+  return c->reduced && c->split && !c->fused ? (c->Kx + 1) * c->Mz : c->Mx * c->Mz;
+}
 
 int pcf_solve_variant(const pcf_ctx* c) {
   if (!c) return -1;

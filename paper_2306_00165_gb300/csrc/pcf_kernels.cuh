@@ -25,7 +25,16 @@ struct GroupLaunch {
   const int* prefix;   // CTA prefix over groups (length ngroups + 1)
   const int2* groups;  // (first instance, instance count) per group
   int ngroups;
+  // 1: the modes m >= 0 only (storage indices i <= Kx, the first (Kx + 1) Mz modes); the
+  // synthesis also writes the y-values of mode -m from those of m by the s2 relation
+  // a_{-m} = e2_c (-1)^m conj(a_m), which every state in an s2-invariant subspace satisfies
+  int reduced;
 };
+
+// Number of (Fourier) modes a launch over instance I processes.
+__device__ __forceinline__ int run_modes(const GroupLaunch& gl, const Inst& I) {
+  return gl.reduced ? (I.Kx + 1) * I.Mz : I.nmodes;
+}
 
 __device__ __forceinline__ int find_inst(const LaunchInfo& li, int cta, int* local) {
   int lo = 0, hi = li.ninst - 1;
@@ -131,7 +140,8 @@ cudaError_t set_ystep_smem(size_t smem);
 
 // Symmetric-subspace projection and the DNS helpers (pcf_sym_dns.cu).
 int symmetrize_ctas(const Inst& I);
-void launch_symmetrize(int ctas_x, int ninst, cudaStream_t s, const Inst* insts, int mask_override);
+void launch_symmetrize(int ctas_x, int ninst, cudaStream_t s, const Inst* insts, int mask_override,
+                       int reduced = 0);
 int dns_ctas(const Inst& I);
 void launch_dns_norm(int ninst, cudaStream_t s, const Inst* insts, DnsInst* dns);
 void launch_dns_capture(int ctas_x, int ninst, cudaStream_t s, const Inst* insts, const DnsInst* dns);

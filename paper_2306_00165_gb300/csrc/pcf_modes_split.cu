@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(kAnalysisThreads, 5) k_yanalysis(GroupLaunch g
   const int first = grp.x, nI = grp.y;
   const Inst& I0 = gl.insts[first];
   const int N = I0.N, H = N / 2 + 1, Mh = H, L2 = 2 * H, ny = I0.ny, nm = I0.nmodes, half = N / 2;
+  const int nrun = run_modes(gl, I0);
   const int tile = local / 3, c = local - 3 * tile, m0 = tile * mt;
   // columns: (mode m0 + mm, instance i, part) = mm SP + 2 i + part, SPt = SP mt <= 32
   const int SP = col_pad(nI), SPt = SP * mt, XS = SPt + 1, RW = 32 / SPt;
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(kAnalysisThreads, 5) k_yanalysis(GroupLaunch g
     const int pr = t % (SPt / 2), j = t / (SPt / 2), mm = pr / (SP / 2), i = pr - mm * (SP / 2);
     const int m = m0 + mm;
     double2 a = make_double2(0.0, 0.0), b = a;
-    if (i < nI && m < nm) {
+    if (i < nI && m < nrun) {
       const double2* xz = gl.insts[first + i].xz + (size_t)c * ny * nm + m;
       a = xz[(size_t)j * nm];
       if (j < half) b = xz[(size_t)(N - j) * nm];
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(kAnalysisThreads, 5) k_yanalysis(GroupLaunch g
     const int k0 = single ? hh - 1 : (even ? rs : rs - ER), k1 = k0 + hh;
     const bool v0 = single || k0 < pp, v1 = !single && v0 && k1 < nrow;
     const int i = (sc - mm * SP) >> 1, part = sc & 1;
-    const bool out = i < nI && m < nm && live[i];
+    const bool out = i < nI && m < nrun && live[i];
     const double* st = nullptr;
     double u0a = 0.0, u0b = 0.0;
     if (out) {
@@ -473,7 +474,24 @@ __global__ void __launch_bounds__(kSolveThreads) k_ysolve(GroupLaunch gl, int op
 
 // slot 0: synthesis of uhat, slot 1: of rhat.  q = 0..4: V_u V_v V_w W_u W_w.  Ten resident
 // CTAs per SM (48 registers): one mode per CTA gives a 32x33x32 batch of 8 12.5 CTAs per SM.
-template <class A>
+// In a reduced launch (modes m >= 0 only), the y-value slot of mode -m that mirrors part
+// `part` of mode m (flattened index m = i Mz + p, 0 < i <= Kx) of field qf (velocity
+// component c), and the sign of the s2 relation a_{-m} = e2_c (-1)^m conj(a_m), e2 = (+1, +1, -1)
+// (the conjugate flips the imaginary part).  Null for m = 0 or a full launch.
+template <bool RED>
+__device__ __forceinline__ double* mirror_dst(const GroupLaunch& gl, const Inst& I0, double2* yv, int slot, int qf,
+                                              int c, int m, int part, double* sgn) {
+  if (!RED) return nullptr;
+  const int ix = m / I0.Mz;
+  if (ix == 0) return nullptr;
+  *sgn = ((ix & 1) ? -1.0 : 1.0) * (c == 2 ? -1.0 : 1.0) * (part ? -1.0 : 1.0);
+  const int mm = (I0.Mx - ix) * I0.Mz + (m - ix * I0.Mz);
+  return reinterpret_cast<double*>(yv + ((size_t)slot * kFieldsY + qf) * I0.ny * I0.nmodes + mm) + part;
+}
+
+template <class A, bool RED>
+// RED: a reduced launch (gl.reduced), which also writes the mirrored y-values of mode -m
+// (a separate instantiation, so that the full launch keeps its register budget).
 __global__ void __launch_bounds__(kSplitThreads, 10) k_ysynth(GroupLaunch gl, int slot, int check_active, int mt) {
   extern __shared__ double sm[];
   __shared__ int live[kMaxGroup];
@@ -482,6 +500,7 @@ __global__ void __launch_bounds__(kSplitThreads, 10) k_ysynth(GroupLaunch gl, in
   const int first = grp.x, nI = grp.y;
   const Inst& I0 = gl.insts[first];
   const int N = I0.N, H = N / 2 + 1, ny = I0.ny, nm = I0.nmodes, half = N / 2;
+  const int nrun = run_modes(gl, I0);
   const int tile = local / kFieldsY, qf = local - kFieldsY * tile, m0 = tile * mt;
   const int c = qf < 3 ? qf : (qf == 3 ? 0 : 2);
   const bool deriv = qf >= 3;
@@ -501,7 +520,7 @@ __global__ void __launch_bounds__(kSplitThreads, 10) k_ysynth(GroupLaunch gl, in
   for (int t = threadIdx.x; t < ny * (SPt / 2); t += blockDim.x) {
     const int n = t % ny, pr = t / ny, mm = pr / (SP / 2), i = pr - mm * (SP / 2), m = m0 + mm;
     double2 v = make_double2(0.0, 0.0);
-    if (i < nI && m < nm)
+    if (i < nI && m < nrun)
       v = (slot == 0 ? gl.insts[first + i].uhat : gl.insts[first + i].rhat)[((size_t)c * nm + m) * ny + n];
     A* d = ((n & 1) ? AO : AE) + (n >> 1) * XS + 2 * pr;
     d[0] = A(v.x);
@@ -522,10 +541,18 @@ __global__ void __launch_bounds__(kSplitThreads, 10) k_ysynth(GroupLaunch gl, in
       A e = A(0.0), o = A(0.0);
       dot_eo(ME + j * H, MO + j * H, AE + sc, AO + sc, XS, H, e, o);
       const int i = (sc - mm * SP) >> 1, part = sc & 1;
-      if (i >= nI || m >= nm || !live[i]) continue;
+      if (i >= nI || m >= nrun || !live[i]) continue;
       double* dst = reinterpret_cast<double*>(gl.insts[first + i].yv + ((size_t)slot * kFieldsY + qf) * ny * nm + m) + part;
-      dst[(size_t)j * nm * 2] = to_double(e + o);
-      if (j < half) dst[(size_t)(N - j) * nm * 2] = to_double(deriv ? o - e : e - o);
+      double sgn;
+      double* dsm = mirror_dst<RED>(gl, I0, gl.insts[first + i].yv, slot, qf, c, m, part, &sgn);
+      const double v0_ = to_double(e + o);
+      dst[(size_t)j * nm * 2] = v0_;
+      if (dsm) dsm[(size_t)j * nm * 2] = sgn * v0_;
+      if (j < half) {
+        const double v1_ = to_double(deriv ? o - e : e - o);
+        dst[(size_t)(N - j) * nm * 2] = v1_;
+        if (dsm) dsm[(size_t)(N - j) * nm * 2] = sgn * v1_;
+      }
       continue;
     }
     const int sc = t % SPt, j0 = t / SPt, j1 = j0 + hJ, mm = sc / SP, m = m0 + mm;
@@ -538,14 +565,28 @@ __global__ void __launch_bounds__(kSplitThreads, 10) k_ysynth(GroupLaunch gl, in
     dot2(re0, re1, AE + sc, XS, H, e0, e1);
     dot2(ro0, ro1, AO + sc, XS, H - 1, o0, o1);
     const int i = (sc - mm * SP) >> 1, part = sc & 1;
-    if (!v0 || i >= nI || m >= nm || !live[i]) continue;
+    if (!v0 || i >= nI || m >= nrun || !live[i]) continue;
     double* dst = reinterpret_cast<double*>(gl.insts[first + i].yv + ((size_t)slot * kFieldsY + qf) * ny * nm + m) + part;
+    double sgn;
+    double* dsm = mirror_dst<RED>(gl, I0, gl.insts[first + i].yv, slot, qf, c, m, part, &sgn);
     // T_{2k} even, T_{2k+1} odd in y; T'_{2k} odd, T'_{2k+1} even
-    dst[(size_t)j0 * nm * 2] = to_double(e0 + o0);
-    if (j0 < half) dst[(size_t)(N - j0) * nm * 2] = to_double(deriv ? o0 - e0 : e0 - o0);
+    const double a0 = to_double(e0 + o0);
+    dst[(size_t)j0 * nm * 2] = a0;
+    if (dsm) dsm[(size_t)j0 * nm * 2] = sgn * a0;
+    if (j0 < half) {
+      const double b0 = to_double(deriv ? o0 - e0 : e0 - o0);
+      dst[(size_t)(N - j0) * nm * 2] = b0;
+      if (dsm) dsm[(size_t)(N - j0) * nm * 2] = sgn * b0;
+    }
     if (v1) {
-      dst[(size_t)j1 * nm * 2] = to_double(e1 + o1);
-      if (j1 < half) dst[(size_t)(N - j1) * nm * 2] = to_double(deriv ? o1 - e1 : e1 - o1);
+      const double a1 = to_double(e1 + o1);
+      dst[(size_t)j1 * nm * 2] = a1;
+      if (dsm) dsm[(size_t)j1 * nm * 2] = sgn * a1;
+      if (j1 < half) {
+        const double b1 = to_double(deriv ? o1 - e1 : e1 - o1);
+        dst[(size_t)(N - j1) * nm * 2] = b1;
+        if (dsm) dsm[(size_t)(N - j1) * nm * 2] = sgn * b1;
+      }
     }
   }
 }
@@ -952,16 +993,23 @@ int ysolve_ctas_per_sm(size_t smem) {
 }
 void launch_ysynth_split(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int slot, int check_active,
                          bool ff_arith, int mt) {
-  if (ff_arith) k_ysynth<ff><<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active, mt);
-  else k_ysynth<double><<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active, mt);
+  if (gl.reduced) {
+    if (ff_arith) k_ysynth<ff, true><<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active, mt);
+    else k_ysynth<double, true><<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active, mt);
+  } else {
+    if (ff_arith) k_ysynth<ff, false><<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active, mt);
+    else k_ysynth<double, false><<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active, mt);
+  }
 }
 cudaError_t set_split_smem(size_t analysis, size_t solve, size_t synth) {
   cudaError_t e;
   if ((e = raise_smem_limit((const void*)k_yanalysis<double>, analysis))) return e;
   if ((e = raise_smem_limit((const void*)k_yanalysis<ff>, analysis))) return e;
   if ((e = raise_smem_limit((const void*)k_ysolve, solve))) return e;
-  if ((e = raise_smem_limit((const void*)k_ysynth<double>, synth))) return e;
-  return raise_smem_limit((const void*)k_ysynth<ff>, synth);
+  if ((e = raise_smem_limit((const void*)k_ysynth<double, false>, synth))) return e;
+  if ((e = raise_smem_limit((const void*)k_ysynth<double, true>, synth))) return e;
+  if ((e = raise_smem_limit((const void*)k_ysynth<ff, true>, synth))) return e;
+  return raise_smem_limit((const void*)k_ysynth<ff, false>, synth);
 }
 
 }  // namespace pcf

@@ -17,7 +17,10 @@ namespace pcf {
 // One thread per (c, m >= 0, p, n) reads modes m and -m and writes both, in place.
 // mask_override >= 0 replaces every instance's own mask (I.sym); inactive instances
 // (converged, I.active == 0) are left alone.
-__global__ void __launch_bounds__(256) k_symmetrize(const Inst* insts, int mask_override) {
+// reduced (every mask contains s2; the descent updated the modes m >= 0 only): mode -m is
+// rebuilt from mode m by the s2 relation instead of averaged with it, and with s1 as well
+// mode m is first projected by its own s1 s2 relation, a <- (a + s1 s2 a)/2.
+__global__ void __launch_bounds__(256) k_symmetrize(const Inst* insts, int mask_override, int reduced) {
   const Inst& I = insts[blockIdx.y];
   const int mask = mask_override >= 0 ? mask_override : I.sym;
   if (mask == 0 || !inst_active(I)) return;
@@ -40,6 +43,13 @@ __global__ void __launch_bounds__(256) k_symmetrize(const Inst* insts, int mask_
     const double e1 = c == 2 ? 1.0 : -1.0, e2 = -e1;
     const double f1 = e1 * sm * spn, f2 = e2 * sm;
     double2 oa, ob;
+    if (reduced && i > 0) {
+      if (mask == 3) oa = make_double2(0.5 * (a.x - spn * a.x), 0.5 * (a.y + spn * a.y));
+      else oa = a;
+      base[ka] = oa;
+      base[kb] = make_double2(f2 * oa.x, -f2 * oa.y);
+      continue;
+    }
     if (mask == 1) {
       oa = make_double2(a.x + f1 * b.x, a.y + f1 * b.y);
       ob = make_double2(b.x + f1 * a.x, b.y + f1 * a.y);
@@ -60,8 +70,8 @@ int symmetrize_ctas(const Inst& I) {
   return (n + 255) / 256;
 }
 
-void launch_symmetrize(int ctas_x, int ninst, cudaStream_t s, const Inst* insts, int mask_override) {
-  k_symmetrize<<<dim3(ctas_x, ninst), 256, 0, s>>>(insts, mask_override);
+void launch_symmetrize(int ctas_x, int ninst, cudaStream_t s, const Inst* insts, int mask_override, int reduced) {
+  k_symmetrize<<<dim3(ctas_x, ninst), 256, 0, s>>>(insts, mask_override, reduced);
 }
 
 // ------------------------------------------------------------------ DNS with the Stokes step

@@ -50,15 +50,26 @@ def test_symmetrize_matches_oracle(pcf, grid, mask):
 
 
 @pytest.mark.parametrize("grid", [(16, 17, 16), (32, 33, 32)])
-def test_enforced_descent_matches_oracle(pcf, grid):
+@pytest.mark.parametrize("mask,solve_kind", [(3, 0), (3, 3), (2, 3), (1, 3), (3, 4)])
+def test_enforced_descent_matches_oracle(pcf, grid, mask, solve_kind):
+    """With s2 enforced and the split per-mode kernels (solve_kind 3), a step computes the
+    modes m >= 0 only and rebuilds the modes m < 0 from the s2 relation (symmetric_modes);
+    with s1 alone, or the fused kernel (4), it computes every mode.  Both match the
+    oracle's projected descent."""
     o = PCFOracle(*grid)
     u0 = gi.random_perturbation(*grid, 0.1, 22)
-    ref, href = _oracle_run(o, u0, 3, 20)
-    s = pcf.Solver(*grid, batch=1, symmetry=pcf.SYM_S1 | pcf.SYM_S2)
-    u = torch.from_numpy(u0[None].copy()).cuda()
-    H = s.descent_step(u, 0.01, 20).cpu().numpy()[:, 0]
-    assert np.max(np.abs(H - href) / href) <= TOL
-    assert _rel(u.cpu().numpy()[0], ref) <= TOL
+    ref, href = _oracle_run(o, u0, mask, 20)
+    s = pcf.Solver(*grid, batch=2, symmetry=mask, solve_kind=solve_kind)
+    Kx, Mz, Mx = grid[0] // 3 - 1, grid[2] // 3, 2 * (grid[0] // 3 - 1) + 1
+    if solve_kind == 3:
+        assert s.symmetric_modes() == ((Kx + 1) * Mz if mask & 2 else Mx * Mz)
+    if solve_kind == 4:
+        assert s.symmetric_modes() == Mx * Mz
+    u = torch.from_numpy(np.stack([u0, u0])).cuda()
+    H = s.descent_step(u, 0.01, 20).cpu().numpy()
+    for b in range(2):
+        assert np.max(np.abs(H[:, b] - href) / href) <= TOL
+        assert _rel(u.cpu().numpy()[b], ref) <= TOL
 
 
 def test_descent_preserves_the_subspace_without_enforcement(pcf):
@@ -109,18 +120,29 @@ def test_float_float_form_with_symmetry(pcf):
 
 
 def test_kernel_organisations_agree_with_symmetry(pcf):
-    """Single per-mode kernel, split kernels and the fused kernel run the projection and the
-    re-synthesis at different places; the bits agree."""
+    """The single per-mode kernel and the fused kernel compute every mode and project after
+    the update: the bits agree.  The split kernels compute the modes m >= 0 and rebuild the
+    modes m < 0 from the s2 relation: the same states to rounding, and the modes m < 0 are
+    exactly the s2 images of the modes m > 0."""
     grid = (32, 33, 32)
     u0 = torch.from_numpy(gi.batch(gi.streak_roll, range(4), *grid)).cuda()
     outs = []
-    for kind in (2, 3, 4):
+    for kind in (2, 4, 3):
         s = pcf.Solver(*grid, batch=4, solve_kind=kind, modes_per_block=2, symmetry=3)
         u = u0.clone()
         H = s.descent_step(u, 0.01, 5)
-        outs.append((u.cpu(), H.cpu()))
-    for u, H in outs[1:]:
-        assert torch.equal(u, outs[0][0]) and torch.equal(H, outs[0][1])
+        outs.append((u.cpu(), H.cpu(), s.symmetric_modes()))
+    assert torch.equal(outs[1][0], outs[0][0]) and torch.equal(outs[1][1], outs[0][1])
+    u3, H3, modes3 = outs[2]
+    Kx, Mz, Mx = 9, 10, 19
+    assert modes3 == (Kx + 1) * Mz
+    assert _rel(u3.numpy(), outs[0][0].numpy()) <= 1e-12
+    assert np.max(np.abs(H3.numpy() - outs[0][1].numpy()) / outs[0][1].numpy()) <= 1e-12
+    a = u3.numpy()
+    sgn_m = (-1.0) ** np.arange(1, Kx + 1)
+    e2 = np.array([1.0, 1.0, -1.0])
+    mirror = e2[None, :, None, None, None] * sgn_m[None, None, :, None, None] * np.conj(a[:, :, 1:Kx + 1])
+    assert np.array_equal(a[:, :, Mx - 1:Kx:-1], mirror)
 
 
 def test_invalid_symmetry_requests(pcf):
