@@ -374,6 +374,21 @@ TTC_SNAPSHOTS, TTC_SPACING = 41, 1000
 TTC_CHUNK = 100000
 
 
+def _tail_fit(taus, Js, target=1e-10):
+    """Exponential tail of J(tau): least-squares slope of ln J over the given points (the
+    last half of a run), the rate lam = -d ln J / d tau, and the pseudo-time at which that
+    rate would bring the last J to the target (None when J does not fall)."""
+    import numpy as np
+    t = np.asarray(taus, dtype=np.float64)
+    y = np.log(np.asarray(Js, dtype=np.float64))
+    if len(t) < 2 or not np.all(np.isfinite(y)):
+        return {"rate_per_tau": None, "tau_to_target": None}
+    lam = -float(np.polyfit(t, y, 1)[0])
+    tau = float(t[-1] + np.log(Js[-1] / target) / lam) if lam > 0 and Js[-1] > target else None
+    return {"rate_per_tau": lam, "tau_to_target": tau, "fit_tau_range": [float(t[0]), float(t[-1])],
+            "target": target}
+
+
 def _ttc_run(pcf, u0, dev, precision, max_steps, seeds):
     """Chunks of run_schedule until every instance has J(dt 0.25) < 1e-10 or max_steps; returns
     per instance the steps to convergence (-1: not converged), the final J, the wall time
@@ -433,6 +448,21 @@ def run_time_to_converge(pcf, gi, dev, args):
         plain.append({"seed": seeds[b], "steps_to_converge": r["steps_to_converge"][0], "wall_s": r["wall_s"],
                       "J_final": r["J_final"][0]})
     out["plain_fp64_one_guess_at_a_time"] = plain
+    # the guesses that did not converge: exponential tail of J over the second half of the
+    # run (DMD jumps included), extrapolated to 1e-10
+    hb = out["batched_fp64"]["history"]
+    half = [h for h in hb if h["steps"] > hb[-1]["steps"] / 2]
+    tails = []
+    for b, c in enumerate(out["batched_fp64"]["steps_to_converge"]):
+        if c >= 0:
+            continue
+        fit = _tail_fit([h["steps"] * TTC_DTAU for h in half], [h["J"][b] for h in half])
+        if fit["tau_to_target"] is not None:
+            fit["steps_to_target"] = fit["tau_to_target"] / TTC_DTAU
+            fit["wall_s_to_target_batched"] = fit["steps_to_target"] * out["batched_fp64"]["wall_s"] / max(
+                1, out["batched_fp64"]["steps_run"])
+        tails.append(dict(fit, seed=seeds[b], J_final=out["batched_fp64"]["J_final"][b]))
+    out["not_converged_tail"] = tails
     if done:
         tb = out["batched_fp64"]["history"]
         t_batched = next(h["wall_s"] for h in tb if h["steps"] >= last)
@@ -684,6 +714,27 @@ def run_ours(args):
     # time to ||r1|| < 1e-10 (or 20k steps) with DMD every 100 steps from 20 snapshots, and without
     ttc = {}
     if not args.no_ttc:
+        # no DMD, in four chunks: the descent's exponential tail rate over the last half and
+        # the pseudo-time it would need to reach J = 1e-10
+        ut = torch.from_numpy(u0.copy()).to(dev)
+        pts, t_nd = [], 0.0
+        q = max(1, args.ttc_steps // 4)
+        for k in range(4):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, Jq, _ = s.run(ut, DTAU, q, tol=1e-300, dmd_period=0)
+            torch.cuda.synchronize()
+            t_nd += time.perf_counter() - t0
+            pts.append(((k + 1) * q * DTAU, [float(x) for x in Jq]))
+        tail = []
+        for b in range(BATCH):
+            fit = _tail_fit([p[0] for p in pts[1:]], [p[1][b] for p in pts[1:]])
+            if fit["tau_to_target"] is not None:
+                fit["steps_to_target"] = fit["tau_to_target"] / DTAU
+                fit["wall_s_to_target"] = fit["steps_to_target"] * t_nd / (4 * q)
+            tail.append(fit)
+        ttc["no_dmd_tail"] = {"steps": 4 * q, "wall_s": round(t_nd, 3),
+                              "J_at_tau": [{"tau": p[0], "J": p[1]} for p in pts], "per_guess": tail}
         for name, period in (("dmd", 100), ("no_dmd", 0)):
             ut = torch.from_numpy(u0.copy()).to(dev)
             torch.cuda.synchronize()

@@ -35,6 +35,7 @@ class DiscreteCost:
         self.xi = torch.tensor(o.x_index)
         self.U = t(o.U_phys)
         self.dU = t(o.dU_phys)
+        self.V = float(o.V_base)
         self._sys = {}
 
     # ---------------------------------------------------------------- the oracle's stages, in torch
@@ -63,7 +64,7 @@ class DiscreteCost:
         out = []
         for i in range(3):
             conv = u[0] * g[i, 0] + u[1] * g[i, 1] + u[2] * g[i, 2]
-            m = -self.U * g[i, 0] - conv
+            m = -self.U * g[i, 0] - self.V * g[i, 1] - conv
             if i == 0:
                 m = m - self.dU * u[1]
             out.append(m)

@@ -9,8 +9,8 @@ What it computes (Ashtari & Schneider, arXiv 2306.00165):
   |m| <= Kx = Nx//3 - 1, 0 <= p <= Kz = Nz//3 - 1 (2/3 rule in x and z, none in y).
   Collocation: y_j = cos(pi j/N), j = 0..N (N = Ny - 1); x, z uniform.
 * Nonlinear terms pseudo-spectrally in the convective forms written in the paper:
-  M(u) = -(u_b.grad)u - (u.grad)u_b - (u.grad)u with u_b = (y, 0, 0)  (§4 Eq. (u_trick),
-  §5), and N(q) = (grad q)(u_b + u) - (grad(u_b + u))^T q  (§4, below Eq. (g_trick)),
+  M(u) = -(u_b.grad)u - (u.grad)u_b - (u.grad)u with u_b = (y, 0, 0) for plane Couette
+  flow (other base flows: base_profile) (§4 Eq. (u_trick), §5), and N(q) = (grad q)(u_b + u) - (grad(u_b + u))^T q  (§4, below Eq. (g_trick)),
   read as component i: U_j d_j q_i - q_j d_i U_j with U = u_b + u.
 * Stokes step (the influence-matrix algorithm's discrete target, §4): per mode
   (m, p) != (0, 0), unknowns u, v, w, P in span{T_0..T_N} with
@@ -75,41 +75,53 @@ def clenshaw_curtis_weights(N):
     return w
 
 
-def base_profile(kind, y):
-    """Streamwise laminar base flow u_b = (U(y), 0, 0) and U'(y) (§3.1: the method is derived
-    for a general u_b; §7 names plane Poiseuille flow as the next case).
-    couette: U = y (walls moving at +-1); poiseuille: U = 1 - y^2 (driven by a fixed
-    pressure gradient that the base flow absorbs)."""
+def base_profile(kind, y, nu=None, delta=None):
+    """Laminar base flow u_b = (U(y), V, 0): returns U(y), U'(y) and the constant wall-normal
+    velocity V (§3.1: the method is derived for a general u_b; §7 names plane Poiseuille and
+    the asymptotic suction boundary layer as flows where only u_b changes).
+    couette: U = y, V = 0 (walls moving at +-1); poiseuille: U = 1 - y^2, V = 0 (driven by a
+    fixed pressure gradient that the base flow absorbs); asbl: the asymptotic suction
+    boundary layer over the wall y = -1, U = 1 - exp(-(1 + y)/delta) with uniform suction
+    V = -nu/delta (delta: suction length in units of the half-height), which solves
+    V U' = nu U'' with no pressure gradient; the wall y = +1 moves at U(1) with the same
+    uniform wall-normal velocity."""
     if kind == "couette":
-        return y, np.ones_like(y)
+        return y, np.ones_like(y), 0.0
     if kind == "poiseuille":
-        return 1.0 - y * y, -2.0 * y
+        return 1.0 - y * y, -2.0 * y, 0.0
+    if kind == "asbl":
+        if nu is None or delta is None or not delta > 0:
+            raise ValueError("asbl needs nu and a suction length delta > 0")
+        e = np.exp(-(1.0 + y) / delta)
+        return 1.0 - e, e / delta, -nu / delta
     raise ValueError(kind)
 
 
-def nonlinear_M(u, gu, U, dU=1.0):
-    """M(u) = -(u_b.grad) u - (u.grad) u_b - (u.grad) u = -U d_x u - U' v e_x - (u.grad) u,
-    pointwise, for u_b = (U(y), 0, 0).
+def nonlinear_M(u, gu, U, dU=1.0, V=0.0):
+    """M(u) = -(u_b.grad) u - (u.grad) u_b - (u.grad) u = -U d_x u - V d_y u - U' v e_x
+    - (u.grad) u, pointwise, for u_b = (U(y), V, 0) with V constant.
 
     u: (3, ...) velocity values; gu: (3, 3, ...) with gu[i, j] = d_j u_i; U, dU broadcastable.
     """
     out = np.empty_like(u)
     for i in range(3):
         conv = u[0] * gu[i, 0] + u[1] * gu[i, 1] + u[2] * gu[i, 2]
-        out[i] = -U * gu[i, 0] - conv
+        out[i] = -U * gu[i, 0] - V * gu[i, 1] - conv
     out[0] = out[0] - dU * u[1]
     return out
 
 
-def adjoint_N(q, gq, u, gu, U, dU=1.0):
-    """N(q) = (W.grad) q - (grad W)^T q with W = u_b + u = (U(y), 0, 0) + u, pointwise.
+def adjoint_N(q, gq, u, gu, U, dU=1.0, V=0.0):
+    """N(q) = (W.grad) q - (grad W)^T q with W = u_b + u = (U(y), V, 0) + u, pointwise.
 
-    Component i: W_j d_j q_i - q_j d_i W_j, where d_i W_j = d_i u_j + delta_{j x} delta_{i y} U'.
+    Component i: W_j d_j q_i - q_j d_i W_j, where d_i W_j = d_i u_j + delta_{j x} delta_{i y} U'
+    (V is constant and adds no gradient).
     """
     U0 = u[0] + U
+    V0 = u[1] + V
     out = np.empty_like(q)
     for i in range(3):
-        adv = U0 * gq[i, 0] + u[1] * gq[i, 1] + u[2] * gq[i, 2]
+        adv = U0 * gq[i, 0] + V0 * gq[i, 1] + u[2] * gq[i, 2]
         tr = q[0] * gu[0, i] + q[1] * gu[1, i] + q[2] * gu[2, i]
         out[i] = adv - tr
     out[1] = out[1] - dU * q[0]
@@ -120,7 +132,7 @@ class PCFOracle:
     """Oracle for one grid; all state arrays are complex128 [3][Mx][Mz][Ny]."""
 
     def __init__(self, nx, ny, nz, Lx=TWO_PI / 1.14, Lz=TWO_PI / 2.5, Re=400.0,
-                 dt=0.25, dtau_hat=0.25, base_flow="couette"):
+                 dt=0.25, dtau_hat=0.25, base_flow="couette", suction_length=None):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.Lx, self.Lz, self.Re = float(Lx), float(Lz), float(Re)
         self.nu = 1.0 / self.Re
@@ -145,7 +157,8 @@ class PCFOracle:
         self._lu = {}
         self.y_phys = self.y[:, None, None]   # broadcast over (Ny, Nx, Nz)
         self.base_flow = base_flow
-        Ub, dUb = base_profile(base_flow, self.y)
+        self.suction_length = suction_length
+        Ub, dUb, self.V_base = base_profile(base_flow, self.y, self.nu, suction_length)
         self.U_phys, self.dU_phys = Ub[:, None, None], dUb[:, None, None]
 
     # ---------------------------------------------------------------- transforms
@@ -259,10 +272,10 @@ class PCFOracle:
 
     # ---------------------------------------------------------------- method
     def M_hat(self, uval, ugrad):
-        return self.to_spec(nonlinear_M(uval, ugrad, self.U_phys, self.dU_phys))
+        return self.to_spec(nonlinear_M(uval, ugrad, self.U_phys, self.dU_phys, self.V_base))
 
     def N_hat(self, qval, qgrad, uval, ugrad):
-        return self.to_spec(adjoint_N(qval, qgrad, uval, ugrad, self.U_phys, self.dU_phys))
+        return self.to_spec(adjoint_N(qval, qgrad, uval, ugrad, self.U_phys, self.dU_phys, self.V_base))
 
     def norm_phys(self, val):
         """Volume-normalised L2 norm of physical values (3, Ny, Nx, Nz)."""

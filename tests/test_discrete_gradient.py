@@ -45,10 +45,10 @@ def test_cost_matches_the_numpy_oracle():
     assert abs(DiscreteCost(o).value(u) - _half_J2(o, u)) <= 1e-13 * _half_J2(o, u)
 
 
-@pytest.mark.parametrize("base", ["couette", "poiseuille"])
+@pytest.mark.parametrize("base", ["couette", "poiseuille", "asbl"])
 @pytest.mark.parametrize("kind", ["admissible", "arbitrary"])
 def test_gradient_against_finite_differences(base, kind):
-    o = PCFOracle(*GRID, base_flow=base)
+    o = PCFOracle(*GRID, base_flow=base, suction_length=0.5 if base == "asbl" else None)
     c = DiscreteCost(o)
     u = gi.streak_roll(*GRID, seed=2)
     g = c.gradient(u)

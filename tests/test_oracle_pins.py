@@ -128,9 +128,11 @@ def test_laminar_is_equilibrium(o16):
     assert np.all(o16.adjoint_direction(z, r1) == 0)
 
 
-def test_poiseuille_laminar_is_equilibrium():
-    """u = 0 is an equilibrium for the plane Poiseuille base flow too: r1 = f = 0 exactly."""
-    o = PCFOracle(16, 17, 16, base_flow="poiseuille")
+@pytest.mark.parametrize("base", ["poiseuille", "asbl"])
+def test_laminar_is_equilibrium_for_other_base_flows(base):
+    """u = 0 is an equilibrium for the plane Poiseuille and suction boundary layer base flows
+    too: r1 = f = 0 exactly."""
+    o = PCFOracle(16, 17, 16, base_flow=base, suction_length=0.5 if base == "asbl" else None)
     z = np.zeros((3, o.Mx, o.Mz, o.N + 1), np.complex128)
     r1, J = o.residual(z)
     assert J == 0.0 and np.all(r1 == 0)
@@ -145,11 +147,12 @@ def _mirror_y(o, a):
     return out
 
 
-@pytest.mark.parametrize("base,symmetric", [("poiseuille", True), ("couette", False)])
+@pytest.mark.parametrize("base,symmetric", [("poiseuille", True), ("couette", False), ("asbl", False)])
 def test_mirror_symmetry_of_the_base_flow(base, symmetric):
     """U = 1 - y^2 is even in y, so the Poiseuille descent commutes with the y mirror; the
-    odd Couette profile U = y breaks it (the test tells the two base flows apart)."""
-    o = PCFOracle(16, 17, 16, base_flow=base)
+    odd Couette profile U = y breaks it, and so does the suction boundary layer (one-sided
+    profile, suction V != 0): the test tells the base flows apart."""
+    o = PCFOracle(16, 17, 16, base_flow=base, suction_length=0.5 if base == "asbl" else None)
     u = gi.random_perturbation(16, 17, 16, 0.1, 4)
     a1 = _mirror_y(o, o.descent_step(u, 0.01)[0])
     a2 = o.descent_step(_mirror_y(o, u), 0.01)[0]
@@ -361,13 +364,15 @@ def test_equivariance(o16, op):
 
 
 # ------------------------------------------------------------------ continuous pins
-BASES = ["couette", "poiseuille"]
+BASES = ["couette", "poiseuille", "asbl"]
+NU_PIN, DELTA_PIN = 1.0 / 400.0, 0.5   # viscosity of the pins; suction length of the ASBL profile
 
 
-def _profile(base):
+def _profile(base, nu=NU_PIN):
     """M and N of the oracle for the base flow `base`, as functions of (..., Y)."""
-    M = lambda u, gu, Y: po.nonlinear_M(u, gu, *po.base_profile(base, Y))
-    N = lambda q, gq, u, gu, Y: po.adjoint_N(q, gq, u, gu, *po.base_profile(base, Y))
+    prof = lambda Y: po.base_profile(base, Y, nu, DELTA_PIN)  # noqa: E731
+    M = lambda u, gu, Y: po.nonlinear_M(u, gu, *prof(Y))  # noqa: E731
+    N = lambda q, gq, u, gu, Y: po.adjoint_N(q, gq, u, gu, *prof(Y))  # noqa: E731
     return M, N
 
 
@@ -456,20 +461,74 @@ def test_adjoint_identity_catches_planted_mistakes(bad):
     assert _adjoint_identity_gap(Nfun=bad) > 1e-4
 
 
-@pytest.mark.parametrize("base,U,dU", [("couette", lambda Y: Y, lambda Y: 1.0 + 0.0 * Y),
-                                        ("poiseuille", lambda Y: 1.0 - Y * Y, lambda Y: -2.0 * Y)])
-def test_M_is_perturbative_nse(base, U, dU):
-    """M(u) = -((u_b+u).grad)(u_b+u) + (u_b.grad)u_b with u_b = (U(y),0,0) (§3.1);
-    (u_b.grad)u_b = U d_x U = 0.  The profile is written out here, not taken from the oracle."""
+def test_adjoint_identity_catches_a_dropped_suction_term():
+    """With suction V = -0.1 (nu = 0.05), an N that advects with u alone instead of u_b + u
+    (V dropped from its advection) breaks the identity by eleven orders of magnitude more
+    than the quadrature's rounding; the oracle's N keeps it."""
+    M, N = _profile("asbl", nu=0.05)
+
+    def no_v(q, gq, u, gu, Y):
+        U, dU, _ = po.base_profile("asbl", Y, 0.05, DELTA_PIN)
+        return po.adjoint_N(q, gq, u, gu, U, dU, 0.0)
+
+    assert _adjoint_identity_gap(Nfun=N, M=M) <= 1e-12
+    assert _adjoint_identity_gap(Nfun=no_v, M=M) > 1e-6
+
+
+def test_asbl_profile_is_the_laminar_suction_solution():
+    """The asymptotic suction boundary layer (named with plane Poiseuille flow in §7): U = 0
+    at the suction wall y = -1, uniform suction V < 0, and the profile solves the steady
+    x-momentum balance V U' = nu U'' (no pressure gradient); U' is the derivative of U.  The
+    derivatives are taken here by Chebyshev interpolation of U's values at 25 points (the
+    interpolant's error at delta = 0.5 is below rounding there)."""
+    N = 24
+    y = np.cos(np.pi * np.arange(N + 1) / N)
+    U, dU, V = po.base_profile("asbl", y, NU_PIN, DELTA_PIN)
+    c = npC.chebfit(y, U, N)
+    d1 = npC.chebval(y, npC.chebder(c))
+    d2 = npC.chebval(y, npC.chebder(c, 2))
+    assert abs(U[-1]) < 1e-15 and V < 0 and U[0] > 0.98
+    assert np.max(np.abs(d1 - dU)) <= 1e-10 * np.max(np.abs(dU))
+    assert np.max(np.abs(V * d1 - NU_PIN * d2)) <= 1e-9 * NU_PIN * np.max(np.abs(d2))
+
+
+def test_asbl_mean_flow_term_is_the_suction_advection():
+    """For u = (f(y), 0, 0) every term of M vanishes except the advection by the base flow's
+    suction: M = -V f'(y) e_x.  f = 1 - y^2 gives M_x = 2 V y, i.e. the T_1 coefficient 2 V
+    of the mean mode, and nothing else."""
+    o = PCFOracle(16, 17, 16, base_flow="asbl", suction_length=DELTA_PIN)
+    u = np.zeros((3, o.Mx, o.Mz, o.ny), np.complex128)
+    u[0, 0, 0, 0], u[0, 0, 0, 2] = 0.5, -0.5          # 1 - y^2 = T_0/2 - T_2/2
+    m = o.M_hat(*o.fields(u))
+    want = np.zeros_like(m)
+    want[0, 0, 0, 1] = 2.0 * o.V_base
+    assert o.V_base == -NU_PIN / DELTA_PIN
+    assert np.max(np.abs(m - want)) <= 1e-15
+
+
+
+_E = lambda Y: np.exp(-(1.0 + Y) / DELTA_PIN)  # noqa: E731
+
+
+@pytest.mark.parametrize("base,U,dU,V", [
+    ("couette", lambda Y: Y, lambda Y: 1.0 + 0.0 * Y, 0.0),
+    ("poiseuille", lambda Y: 1.0 - Y * Y, lambda Y: -2.0 * Y, 0.0),
+    ("asbl", lambda Y: 1.0 - _E(Y), lambda Y: _E(Y) / DELTA_PIN, -NU_PIN / DELTA_PIN)])
+def test_M_is_perturbative_nse(base, U, dU, V):
+    """M(u) = -((u_b+u).grad)(u_b+u) + (u_b.grad)u_b with u_b = (U(y), V, 0) (§3.1);
+    (u_b.grad)u_b = V U' e_x (zero without suction).  The profile is written out here, not
+    taken from the oracle."""
     rng = np.random.default_rng(3)
     g = Grid(LX, LZ, nf=8, ng=10)
     comps = _fields(rng, 1, 4, [1, 1, 1])
     u, gu, _ = vector_eval(comps, g)
     Ut = u.copy()
     Ut[0] += U(g.Y)
+    Ut[1] += V
     gUt = gu.copy()
     gUt[0, 1] += dU(g.Y)
     full = -np.einsum("j...,ij...->i...", Ut, gUt)
+    full[0] += V * dU(g.Y)
     got = _profile(base)[0](u, gu, g.Y)
     assert np.max(np.abs(got - full)) <= 1e-13
 
@@ -670,10 +729,12 @@ def test_descent_preserves_the_symmetric_subspace(o16):
     assert np.max(np.abs(o16.symmetrize(uT, 3) - uT)) < 1e-14 * np.max(np.abs(uT))
 
 
-def test_s1_is_not_a_symmetry_of_poiseuille_flow():
-    """s1 turns U = 1 - y^2 into -(1 - y^2): it maps plane Poiseuille flow to another flow, so
-    the descent there is not s1-equivariant; s2 leaves U(y) alone and still is."""
-    o = PCFOracle(16, 17, 16, base_flow="poiseuille")
+@pytest.mark.parametrize("base", ["poiseuille", "asbl"])
+def test_s1_is_not_a_symmetry_of_poiseuille_flow(base):
+    """s1 turns U = 1 - y^2 into -(1 - y^2) (and the suction profile into a blowing one): it
+    maps these flows to other flows, so the descent there is not s1-equivariant; s2 leaves
+    U(y) and V alone and still is."""
+    o = PCFOracle(16, 17, 16, base_flow=base, suction_length=0.5 if base == "asbl" else None)
     u = gi.random_perturbation(16, 17, 16, 0.1, 16)
     gap1 = np.max(np.abs(o.s1(o.descent_step(u, 0.01)[0]) - o.descent_step(o.s1(u), 0.01)[0]))
     gap2 = np.max(np.abs(o.s2(o.descent_step(u, 0.01)[0]) - o.descent_step(o.s2(u), 0.01)[0]))
