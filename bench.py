@@ -789,6 +789,13 @@ def run_ours(args):
             "kernel_share": round(kt[dom][0] / total_ms, 4), "mode_tile": s.mode_tile(), "split_config": s.split_config(),
             "kernel_ms_per_launch": round(dom_ms, 5),
             "per_kernel_ms_per_step": {k: round(v[0] / nk, 5) for k, v in kt.items()}}
+    # the same against the FP64 pipe's nominal rate (2 DFMA per clock per SM at the maximum SM
+    # clock); a DFMA-only loop (k_fp64_probe) sustains about 0.84 of it on GB300
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    if ck.get("sm_max_mhz"):
+        nominal = nsm * 4.0 * ck["sm_max_mhz"] * 1e6 / 1e12
+        roof.update(nominal_fp64_peak=round(nominal, 4), frac_vs_nominal=round(achieved / nominal, 4),
+                    probe_vs_nominal=round(peak_tf / nominal, 4))
 
     if rank == 0:
         line = {"metric": "gradient evals/s", "value": value, "unit": "gradient evals/s", "n_gpus": ws,

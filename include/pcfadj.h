@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define PCF_ABI_VERSION 2
+#define PCF_ABI_VERSION 3
 
 typedef enum {
   PCF_OK = 0,
@@ -83,10 +83,10 @@ typedef struct pcf_params {
                            operators inside the single per-mode kernel.  3: FP64 split
                            analysis / solve / synthesis kernels.  4: FP64 fused per-mode
                            half-step kernel.  2, 3 and 4 give bit-identical results. */
-  int base_flow;        /* pcf_base_flow: the laminar base flow u_b = (U(y), 0, 0) */
+  int base_flow;        /* pcf_base_flow: the laminar base flow u_b = (U(y), V, 0) */
   int symmetry;         /* pcf_symmetry mask enforced along the descent and the DNS (0: none).
                            s1 requires PCF_COUETTE (it maps the Poiseuille profile to its
-                           negative); PCF_EINVAL otherwise. */
+                           negative and suction to blowing); PCF_EINVAL otherwise. */
   int plane_kernel;     /* x-z plane kernels of the mixed form (FP32): 0 = transforms in warp
                            registers when every instance has nx, nz in {32, 64, 96, 128}, else
                            the shared-memory Stockham kernels; 1 = always the Stockham kernels.
@@ -96,15 +96,25 @@ typedef struct pcf_params {
                            accumulation): 0 = tcgen05 MMAs with the accumulator in tensor
                            memory; 1 = warp-level mma.sync.  pcf_contraction_variant reports
                            the choice.  Ignored by the other forms. */
+  double suction_length; /* PCF_ASBL only: suction length delta of the boundary layer in
+                           units of the half-height (> 0, finite; PCF_EINVAL otherwise).
+                           Ignored by the other base flows. */
 } pcf_params;
 
 /* Base flows (§3.1 derives the method for a general laminar base flow u_b; §7 names plane
- * Poiseuille flow as a direct next case).  The perturbation u vanishes at both walls in
- * either case; the Poiseuille base flow absorbs the fixed driving pressure gradient, so the
- * perturbation's mean pressure gradient stays zero. */
+ * Poiseuille flow and the asymptotic suction boundary layer as flows where only u_b
+ * changes).  The perturbation u vanishes at both walls in every case; the Poiseuille base
+ * flow absorbs the fixed driving pressure gradient, so the perturbation's mean pressure
+ * gradient stays zero.  The suction boundary layer sits on the wall y = -1 (lengths in units
+ * of the half-height, Re = U/(nu h)): U = 1 - exp(-(1 + y)/delta) with the uniform suction
+ * V = -nu/delta, which solve V U' = nu U'' without a pressure gradient; the wall y = +1 moves
+ * at U(1) with the same uniform wall-normal velocity (a finite box standing in for the free
+ * stream).  The suction enters M and N as advection by V (u_b + u advects). */
 typedef enum {
   PCF_COUETTE = 0,     /* plane Couette flow:    U = y       (walls moving at +-1) */
-  PCF_POISEUILLE = 1   /* plane Poiseuille flow: U = 1 - y^2 (pressure-driven) */
+  PCF_POISEUILLE = 1,  /* plane Poiseuille flow: U = 1 - y^2 (pressure-driven) */
+  PCF_ASBL = 2         /* asymptotic suction boundary layer: U = 1 - exp(-(1+y)/delta),
+                          V = -nu/delta (pcf_params.suction_length = delta) */
 } pcf_base_flow;
 
 /* Symmetries of §5.1 (bit mask).  s1 = shift-and-rotate, s2 = shift-and-reflect:

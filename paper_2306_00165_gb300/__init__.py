@@ -36,9 +36,12 @@ class _Params(ctypes.Structure):
                 ("dt", ctypes.c_double), ("dtau_hat", ctypes.c_double),
                 ("precision", ctypes.c_int), ("modes_per_block", ctypes.c_int),
                 ("solve_kind", ctypes.c_int), ("base_flow", ctypes.c_int), ("symmetry", ctypes.c_int),
-                ("plane_kernel", ctypes.c_int), ("contraction_kernel", ctypes.c_int)]
+                ("plane_kernel", ctypes.c_int), ("contraction_kernel", ctypes.c_int),
+                ("suction_length", ctypes.c_double)]
 
-COUETTE, POISEUILLE = 0, 1   # laminar base flows u_b = (y,0,0) and (1-y^2,0,0)
+# laminar base flows: u_b = (y,0,0), (1-y^2,0,0), and the asymptotic suction boundary layer
+# (1 - exp(-(1+y)/delta), -nu/delta, 0) with delta = suction_length
+COUETTE, POISEUILLE, ASBL = 0, 1, 2
 SYM_S1, SYM_S2 = 1, 2        # symmetries of §5.1 (bit mask): shift-and-rotate, shift-and-reflect
 FP64, MIXED, FLOAT_FLOAT = 0, 1, 2   # precision forms (pcf_precision)
 
@@ -152,14 +155,14 @@ class Solver:
 
     def __init__(self, nx, ny, nz, batch=1, Lx=LX_PAPER, Lz=LZ_PAPER, Re=400.0, dt=0.25, dtau_hat=0.25,
                  precision=0, modes_per_block=0, solve_kind=0, base_flow=COUETTE, symmetry=0, plane_kernel=0,
-                 contraction_kernel=0):
+                 contraction_kernel=0, suction_length=0.0):
         import torch
         self.lib = load_library()
         self.shape = state_shape(nx, ny, nz, batch)
         self.nx, self.ny, self.nz, self.batch = nx, ny, nz, batch
         self.dt, self.dtau_hat = dt, dtau_hat
         p = _Params(nx, ny, nz, batch, Lx, Lz, Re, dt, dtau_hat, precision, modes_per_block, solve_kind, base_flow,
-                    symmetry, plane_kernel, contraction_kernel)
+                    symmetry, plane_kernel, contraction_kernel, suction_length)
         h = ctypes.c_void_p()
         _check(self.lib.pcf_create(ctypes.byref(p), _stream(), ctypes.byref(h)))
         self._h = h
@@ -169,7 +172,7 @@ class Solver:
     @classmethod
     def batched(cls, grids, Lx=LX_PAPER, Lz=LZ_PAPER, Re=400.0, dt=0.25, dtau_hat=0.25, modes_per_block=0,
                 solve_kind=0, precision=0):
-        """grids: list of (nx, ny, nz, count[, base_flow[, symmetry]])."""
+        """grids: list of (nx, ny, nz, count[, base_flow[, symmetry[, suction_length]]])."""
         import torch
         self = cls.__new__(cls)
         self.lib = load_library()
@@ -177,7 +180,8 @@ class Solver:
         for k, g in enumerate(grids):
             nx, ny, nz, cnt = g[:4]
             arr[k] = _Params(nx, ny, nz, cnt, Lx, Lz, Re, dt, dtau_hat, precision, modes_per_block if k == 0 else 0,
-                             solve_kind, g[4] if len(g) > 4 else COUETTE, g[5] if len(g) > 5 else 0)
+                             solve_kind, g[4] if len(g) > 4 else COUETTE, g[5] if len(g) > 5 else 0, 0, 0,
+                             g[6] if len(g) > 6 else 0.0)
         h = ctypes.c_void_p()
         _check(self.lib.pcf_batch_create(arr, len(grids), _stream(), ctypes.byref(h)))
         self._h = h

@@ -347,6 +347,31 @@ std::vector<double2> make_twiddles(int L) {
   return w;
 }
 
+// Tangent form of the twiddles w^q = c + i s (w = e^{-2 pi i/L}) for the FMA butterflies:
+// w^q = m (1 + i t) with t = s/c, m = c where |c| >= |s|; else w^q = m i (1 + i t) with
+// m = s, t = -c/s (rot = 1).  |t| <= 1 either way.  rot[q] = 1 exactly where the angle's
+// distance to the nearest multiple of pi exceeds pi/4: 2q mod L in (L/4, 3L/4), decided in
+// integers.  tan[0, L): w^q; tan[L, 2L): its conjugate c - i s (t -> -t, and m -> -m where
+// rot = 1).
+void make_tangent_twiddles(int L, std::vector<double2>* tan, std::vector<unsigned char>* rot) {
+  tan->assign(2 * (size_t)L, make_double2(0.0, 0.0));
+  rot->assign(L, 0);
+  for (int q = 0; q < L; ++q) {
+    const double a = -2.0 * kPi * (double)q / (double)L;
+    const double c = std::cos(a), s = std::sin(a);
+    const int r2 = (2 * q) % L;
+    const bool r = 4 * r2 > L && 4 * r2 < 3 * L;
+    (*rot)[q] = r ? 1 : 0;
+    if (!r) {
+      (*tan)[q] = make_double2(s / c, c);
+      (*tan)[L + q] = make_double2(-s / c, c);
+    } else {
+      (*tan)[q] = make_double2(-c / s, s);
+      (*tan)[L + q] = make_double2(c / s, -s);
+    }
+  }
+}
+
 template <class T>
 cudaError_t upload(const std::vector<T>& h, T** d) {
   cudaError_t e = cudaMalloc((void**)d, h.size() * sizeof(T));
@@ -413,13 +438,15 @@ pcf_status launch_synth(pcf_ctx* c, int slot, int nf) {
 pcf_status launch_prodM(pcf_ctx* c) {
   return timed(c, 2, [&] {
     if (c->plane_warp) launch_prod_warp(false, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod), -1);
-    else launch_prod(c->plane_kind, false, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod));
+    else launch_prod(c->plane_kind, false, c->suction, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod));
   });
 }
 pcf_status launch_prodN(pcf_ctx* c, int step_index = -1) {
   return timed(c, 5, [&] {
     if (c->plane_warp) launch_prod_warp(true, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod), step_index);
-    else launch_prod(c->plane_kind, true, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod), step_index);
+    else
+      launch_prod(c->plane_kind, true, c->suction, c->cta_prod, c->sm_prod, c->cs, li_of(c, c->pre_prod),
+                  step_index);
   });
 }
 
@@ -641,7 +668,9 @@ long long pcf_psi_len(int nx, int ny, int nz) {
 static bool params_ok(const pcf_params* prm) {
   return grid_ok(prm->nx, prm->ny, prm->nz) && prm->batch >= 1 && prm->Re > 0 && prm->dt > 0 &&
          prm->dtau_hat > 0 && prm->Lx > 0 && prm->Lz > 0 && prm->solve_kind >= 0 && prm->solve_kind <= 4 &&
-         prm->modes_per_block >= 0 && (prm->base_flow == PCF_COUETTE || prm->base_flow == PCF_POISEUILLE) &&
+         prm->modes_per_block >= 0 &&
+         (prm->base_flow == PCF_COUETTE || prm->base_flow == PCF_POISEUILLE ||
+          (prm->base_flow == PCF_ASBL && prm->suction_length > 0 && std::isfinite(prm->suction_length))) &&
          prm->symmetry >= 0 && prm->symmetry <= 3 && prm->plane_kernel >= 0 && prm->plane_kernel <= 1 &&
          prm->contraction_kernel >= 0 && prm->contraction_kernel <= 1 &&
          !((prm->symmetry & PCF_SYM_S1) && prm->base_flow != PCF_COUETTE);
@@ -651,7 +680,8 @@ static bool params_ok(const pcf_params* prm) {
 struct GridTables {
   double *cheb, *rco, *ccw, *kx, *kz, *y, *ub, *tab0, *tab1, *dense0, *dense1;
   float2* cheb_ff = nullptr;
-  double2 *twx, *twz;
+  double2 *twx, *twz, *tanx, *tanz;
+  unsigned char *rotx, *rotz;
   float2 *twxf = nullptr, *twzf = nullptr;
   uint16_t* tcA = nullptr;
   double sig[2];
@@ -665,24 +695,41 @@ static pcf_status build_tables(pcf_ctx* c, const pcf_params* prm, GridTables* g)
   for (int i = 0; i < Mx; ++i) kx[i] = 2.0 * kPi * (i <= Kx ? i : i - Mx) / prm->Lx;
   for (int p = 0; p < Mz; ++p) kz[p] = 2.0 * kPi * p / prm->Lz;
   for (int j = 0; j < ny; ++j) yg[j] = cospi_frac(j, N);
-  // base-flow profile U(y_j), U'(y_j) (one explicit fma, so every host rounds alike)
-  std::vector<double> ub(2 * (size_t)ny);
+  // base-flow profile U(y_j), U'(y_j) and the constant wall-normal velocity V (one explicit
+  // fma, so every host rounds alike; the suction profile goes through the host's exp)
+  std::vector<double> ub(3 * (size_t)ny, 0.0);
   for (int j = 0; j < ny; ++j) {
     const double y = yg[j];
-    ub[j] = prm->base_flow == PCF_POISEUILLE ? std::fma(-y, y, 1.0) : y;
-    ub[ny + j] = prm->base_flow == PCF_POISEUILLE ? -2.0 * y : 1.0;
+    if (prm->base_flow == PCF_POISEUILLE) {
+      ub[j] = std::fma(-y, y, 1.0);
+      ub[ny + j] = -2.0 * y;
+    } else if (prm->base_flow == PCF_ASBL) {
+      const double d = prm->suction_length, e = std::exp(-(1.0 + y) / d);
+      ub[j] = 1.0 - e;
+      ub[ny + j] = e / d;
+      ub[2 * ny + j] = -nu / d;
+    } else {
+      ub[j] = y;
+      ub[ny + j] = 1.0;
+    }
   }
   const std::vector<double> cheb = make_cheb(N), rco = make_rco(N), ccw = make_ccw(N);
   g->sig[0] = 1.0 / (nu * prm->dt);
   g->sig[1] = 1.0 / (nu * prm->dtau_hat);
   const std::vector<double> tab0 = make_mode_tables(N, kx, kz, g->sig[0], rco);
   const std::vector<double2> twx = make_twiddles(nx), twz = make_twiddles(nz);
+  std::vector<double2> tanx, tanz;
+  std::vector<unsigned char> rotx, rotz;
+  make_tangent_twiddles(nx, &tanx, &rotx);
+  make_tangent_twiddles(nz, &tanz, &rotz);
   if (upload(cheb, &g->cheb) || upload(rco, &g->rco) || upload(ccw, &g->ccw) || upload(kx, &g->kx) ||
       upload(kz, &g->kz) || upload(yg, &g->y) || upload(ub, &g->ub) || upload(twx, &g->twx) ||
-      upload(twz, &g->twz) || upload(tab0, &g->tab0))
+      upload(twz, &g->twz) || upload(tab0, &g->tab0) || upload(tanx, &g->tanx) || upload(tanz, &g->tanz) ||
+      upload(rotx, &g->rotx) || upload(rotz, &g->rotz))
     return PCF_ECUDA;
   for (void* p : {(void*)g->cheb, (void*)g->rco, (void*)g->ccw, (void*)g->kx, (void*)g->kz, (void*)g->y,
-                  (void*)g->ub, (void*)g->twx, (void*)g->twz, (void*)g->tab0})
+                  (void*)g->ub, (void*)g->twx, (void*)g->twz, (void*)g->tab0, (void*)g->tanx, (void*)g->tanz,
+                  (void*)g->rotx, (void*)g->rotz})
     c->allocs.push_back(p);
   std::vector<double> tab1;
   if (prm->dtau_hat == prm->dt) {
@@ -1104,12 +1151,14 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
   std::vector<GridTables> gts;
   std::vector<int> grid_of(nlist);
   c->uniform = true;
+  for (int k = 0; k < nlist; ++k) c->suction = c->suction || list[k].base_flow == PCF_ASBL;
   for (int k = 0; k < nlist; ++k) {
     int found = -1;
     for (int q = 0; q < k; ++q) {
       const pcf_params &a = list[k], &p = list[q];
       if (a.nx == p.nx && a.ny == p.ny && a.nz == p.nz && a.Lx == p.Lx && a.Lz == p.Lz && a.Re == p.Re &&
-          a.dt == p.dt && a.dtau_hat == p.dtau_hat && a.solve_kind == p.solve_kind && a.base_flow == p.base_flow) {
+          a.dt == p.dt && a.dtau_hat == p.dtau_hat && a.solve_kind == p.solve_kind && a.base_flow == p.base_flow &&
+          (a.base_flow != PCF_ASBL || a.suction_length == p.suction_length)) {
         found = grid_of[q];
         break;
       }
@@ -1189,6 +1238,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       I.cheb = g.cheb; I.cheb_ff = g.cheb_ff; I.rco = g.rco; I.ygrid = g.y; I.ubase = g.ub; I.ccw = g.ccw;
       I.kx = g.kx; I.kz = g.kz;
       I.twx = g.twx; I.twz = g.twz;
+      I.tanx = g.tanx; I.tanz = g.tanz; I.rotx = g.rotx; I.rotz = g.rotz;
       I.tab[0] = g.tab0; I.tab[1] = g.tab1;
       I.dense[0] = g.dense0; I.dense[1] = g.dense1;
       I.sigma[0] = g.sig[0]; I.sigma[1] = g.sig[1];

@@ -92,12 +92,16 @@ struct Inst {
   const float2* cheb_ff;  // the same table as float-float pairs (hi, lo), for the float-float form
   const double* rco;
   const double* ygrid;
-  const double* ubase;  // [2][ny]: base-flow profile U(y_j) and U'(y_j)
+  const double* ubase;  // [3][ny]: base-flow profile U(y_j), U'(y_j) and the constant V
   const double* ccw;
   const double* kx;   // [Mx]
   const double* kz;   // [Mz]
   const double2* twx; // e^{-2 pi i k/nx}, k < nx
   const double2* twz; // e^{-2 pi i k/nz}, k < nz
+  const double2* tanx;        // [2][nx] tangent-form twiddles (t, m) of the FP64 plane FFTs:
+  const double2* tanz;        //   forward, then inverse; see TwTan
+  const unsigned char* rotx;  // [nx] their rotation flags (|sin| > |cos|)
+  const unsigned char* rotz;  // [nz]
   const float2* twxf; // FP32 copies for the mixed-precision form
   const float2* twzf;
   const double* tab[2];  // per-mode solver tables: [0] sigma = 1/(nu dt), [1] sigma = 1/(nu dtau_hat)

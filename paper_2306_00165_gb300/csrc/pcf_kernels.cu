@@ -41,9 +41,9 @@ cudaError_t raise_smem_limit(const void* func, size_t bytes) {
 // One radix-R pass over nb batches of length L, batch b at b LS (Stockham autosort).  The
 // plane kernels use LS = L + 1: a warp that walks down a column of a batch array then meets
 // 32 different banks.
-template <int R, class C>
+template <int R, class C, class TW>
 __device__ __forceinline__ void stockham_pass(const C* __restrict__ a, C* __restrict__ b, int L, int LS, int nb,
-                                              int Ns, const C* __restrict__ tw, bool inv) {
+                                              int Ns, const TW& tw, bool inv) {
   const int nq = L / R;
   const int total = nq * nb;
   const int twstep = L / (Ns * R);
@@ -55,15 +55,8 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ a, C* __rest
     C v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = ab[j + r * nq];
-    if (Ns > 1) {
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        C w = tw[r * k * twstep];
-        if (inv) w.y = -w.y;
-        v[r] = cmul(v[r], w);
-      }
-    }
-    butterfly<R, C>(v, inv);
+    if (Ns > 1) tw_butterfly<R>(v, tw, k, twstep, L, inv);
+    else butterfly<R, C>(v, inv);
     const int idx = (j / Ns) * Ns * R + k;
     C* bb = b + bi * LS;
 #pragma unroll
@@ -72,8 +65,8 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ a, C* __rest
 }
 
 // Full transform of nb batches (stride LS); a holds the input; returns the buffer with the result.
-template <class C>
-__device__ C* fft_run(C* a, C* b, int L, int LS, int nb, const int* radix, int nr, const C* tw, bool inv) {
+template <class C, class TW>
+__device__ C* fft_run(C* a, C* b, int L, int LS, int nb, const int* radix, int nr, const TW& tw, bool inv) {
   int Ns = 1;
   for (int s = 0; s < nr; ++s) {
     const int R = radix[s];
@@ -94,9 +87,9 @@ __device__ C* fft_run(C* a, C* b, int L, int LS, int nb, const int* radix, int n
 // lies (and build it on the fly) and its last pass can write the result where it is needed,
 // without shared-memory round trips and barriers of their own.  Same arithmetic as
 // stockham_pass.
-template <int R, class C, class LD, class ST>
-__device__ __forceinline__ void stockham_pass_io(int L, int nb, int Ns, const C* __restrict__ tw, bool inv,
-                                                 const LD& ld, const ST& st) {
+template <int R, class C, class TW, class LD, class ST>
+__device__ __forceinline__ void stockham_pass_io(int L, int nb, int Ns, const TW& tw, bool inv, const LD& ld,
+                                                 const ST& st) {
   const int nq = L / R;
   const int total = nq * nb;
   const int twstep = L / (Ns * R);
@@ -107,15 +100,8 @@ __device__ __forceinline__ void stockham_pass_io(int L, int nb, int Ns, const C*
     C v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = ld(bi, j + r * nq);
-    if (Ns > 1) {
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        C w = tw[r * k * twstep];
-        if (inv) w.y = -w.y;
-        v[r] = cmul(v[r], w);
-      }
-    }
-    butterfly<R, C>(v, inv);
+    if (Ns > 1) tw_butterfly<R>(v, tw, k, twstep, L, inv);
+    else butterfly<R, C>(v, inv);
     const int idx = (j / Ns) * Ns * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) st(bi, idx + r * Ns, v[r]);
@@ -135,8 +121,9 @@ struct SmemSt {
   __device__ __forceinline__ void operator()(int b, int i, C v) const { p[b * LS + i] = v; }
 };
 
-template <class C, class LD, class ST>
-__device__ __forceinline__ void pass_r(int R, int L, int nb, int Ns, const C* tw, bool inv, const LD& ld, const ST& st) {
+template <class C, class TW, class LD, class ST>
+__device__ __forceinline__ void pass_r(int R, int L, int nb, int Ns, const TW& tw, bool inv, const LD& ld,
+                                       const ST& st) {
   if (R == 4) stockham_pass_io<4, C>(L, nb, Ns, tw, inv, ld, st);
   else if (R == 2) stockham_pass_io<2, C>(L, nb, Ns, tw, inv, ld, st);
   else stockham_pass_io<3, C>(L, nb, Ns, tw, inv, ld, st);
@@ -146,8 +133,8 @@ __device__ __forceinline__ void pass_r(int R, int L, int nb, int Ns, const C* tw
 // ping-pong between a and b (stride LS), the first pass writing a.  With OUT_ST the last
 // pass writes through st (returns null); otherwise the result stays in shared memory and
 // the buffer holding it is returned.  A barrier follows every pass but the last.
-template <bool OUT_ST, class C, class LD, class ST>
-__device__ C* fft_run_io(C* a, C* b, int L, int LS, int nb, const int* radix, int nr, const C* tw, bool inv,
+template <bool OUT_ST, class C, class TW, class LD, class ST>
+__device__ C* fft_run_io(C* a, C* b, int L, int LS, int nb, const int* radix, int nr, const TW& tw, bool inv,
                          const LD& ld, const ST& st) {
   int Ns = 1;
   C* cur = nullptr;
@@ -155,10 +142,10 @@ __device__ C* fft_run_io(C* a, C* b, int L, int LS, int nb, const int* radix, in
   for (int s = 0; s < nr; ++s) {
     const int R = radix[s];
     const bool first = s == 0, last = s == nr - 1 && OUT_ST;
-    if (first && last) pass_r(R, L, nb, Ns, tw, inv, ld, st);
-    else if (first) pass_r(R, L, nb, Ns, tw, inv, ld, SmemSt<C>{out, LS});
-    else if (last) pass_r(R, L, nb, Ns, tw, inv, SmemLd<C>{cur, LS}, st);
-    else pass_r(R, L, nb, Ns, tw, inv, SmemLd<C>{cur, LS}, SmemSt<C>{out, LS});
+    if (first && last) pass_r<C>(R, L, nb, Ns, tw, inv, ld, st);
+    else if (first) pass_r<C>(R, L, nb, Ns, tw, inv, ld, SmemSt<C>{out, LS});
+    else if (last) pass_r<C>(R, L, nb, Ns, tw, inv, SmemLd<C>{cur, LS}, st);
+    else pass_r<C>(R, L, nb, Ns, tw, inv, SmemLd<C>{cur, LS}, SmemSt<C>{out, LS});
     Ns *= R;
     if (s < nr - 1) __syncthreads();
     cur = out;
@@ -167,13 +154,39 @@ __device__ C* fft_run_io(C* a, C* b, int L, int LS, int nb, const int* radix, in
   return OUT_ST ? nullptr : cur;
 }
 
+// Twiddles of the plane kernels in shared memory: the standard tables (FP32, float-float), or
+// for FP64 the tangent-form entries of the transform's direction (inv: the inverse
+// transform) and their rotation flags.  PlaneTw<T>::type is the pass functions' view.
 template <class T>
-__device__ __forceinline__ void load_twiddles(const Inst& I, typename Cx<T>::c* twx, typename Cx<T>::c* twz) {
-  const typename Sto<T>::c* sx = twx_of<T>(I);
-  const typename Sto<T>::c* sz = twz_of<T>(I);
-  for (int t = threadIdx.x; t < I.nx; t += blockDim.x) twx[t] = load_c<T>(sx[t]);
-  for (int t = threadIdx.x; t < I.nz; t += blockDim.x) twz[t] = load_c<T>(sz[t]);
-}
+struct PlaneTw {
+  using C = typename Cx<T>::c;
+  using type = TwStd<C>;
+  static __device__ __forceinline__ type view(C* tw, unsigned char*) { return type{tw}; }
+  static __device__ __forceinline__ void load(const Inst& I, C* twx, C* twz, unsigned char*, unsigned char*, bool) {
+    const typename Sto<T>::c* sx = twx_of<T>(I);
+    const typename Sto<T>::c* sz = twz_of<T>(I);
+    for (int t = threadIdx.x; t < I.nx; t += blockDim.x) twx[t] = load_c<T>(sx[t]);
+    for (int t = threadIdx.x; t < I.nz; t += blockDim.x) twz[t] = load_c<T>(sz[t]);
+  }
+};
+template <>
+struct PlaneTw<double> {
+  using type = TwTan;
+  static __device__ __forceinline__ type view(double2* tw, unsigned char* rot) { return type{tw, rot}; }
+  static __device__ __forceinline__ void load(const Inst& I, double2* twx, double2* twz, unsigned char* rx,
+                                              unsigned char* rz, bool inv) {
+    const double2* sx = I.tanx + (inv ? I.nx : 0);
+    const double2* sz = I.tanz + (inv ? I.nz : 0);
+    for (int t = threadIdx.x; t < I.nx; t += blockDim.x) {
+      twx[t] = sx[t];
+      rx[t] = I.rotx[t];
+    }
+    for (int t = threadIdx.x; t < I.nz; t += blockDim.x) {
+      twz[t] = sz[t];
+      rz[t] = I.rotz[t];
+    }
+  }
+};
 
 // Shared-memory plan of a plane transform: two buffers of PB complex values; x-stage
 // batches (one per retained z mode) have stride LX = nx + 1, z-stage batches (one per row
@@ -198,9 +211,10 @@ __host__ __device__ inline PlanePlan plane_plan(const Inst& I, int elem) {
   }
   return pp;
 }
+// [B0 | B1 | twx (nx) | twz (nz) | 32 doubles of reduction | rotation flags of twx, twz]
 size_t smem_plane(const Inst& I, int elem) {
   const PlanePlan pp = plane_plan(I, elem);
-  return (size_t)elem * (2 * (size_t)pp.PB + I.nx + I.nz) + 8 * 32;
+  return (size_t)elem * (2 * (size_t)pp.PB + I.nx + I.nz) + 8 * 32 + (size_t)((I.nx + I.nz + 15) & ~15);
 }
 size_t smem_xzsynth(const Inst& I) { return smem_plane(I, sizeof(double2)); }
 size_t smem_prod(const Inst& I) { return smem_plane(I, sizeof(double2)); }
@@ -233,7 +247,10 @@ __global__ void __launch_bounds__(128, PCF_XZ_MINB) k_xzsynth_t(LaunchInfo li, i
   C* B1 = sm + pp.PB;
   C* twx = sm + 2 * pp.PB;
   C* twz = twx + nx;
-  load_twiddles<T>(I, twx, twz);  // first used after the first pass's barrier
+  unsigned char* rtx = reinterpret_cast<unsigned char*>(twz + nz) + 8 * 32;
+  unsigned char* rtz = rtx + nx;
+  PlaneTw<T>::load(I, twx, twz, rtx, rtz, true);  // first used after the first pass's barrier
+  const typename PlaneTw<T>::type tx = PlaneTw<T>::view(twx, rtx), tz = PlaneTw<T>::view(twz, rtz);
   const int LX = pp.LX, LZ = pp.LZ;
   const typename Sto<T>::c* src = yv_of<T>(I) + (((size_t)slot * kFieldsY + c_src[f]) * I.ny + j) * (size_t)I.nmodes;
   const int fac = c_fac[f];
@@ -254,7 +271,7 @@ __global__ void __launch_bounds__(128, PCF_XZ_MINB) k_xzsynth_t(LaunchInfo li, i
   const auto ldx = [&](int p, int bin) -> C {
     return (bin <= Kx || bin >= nx - Kx) ? B0[p * LX + bin] : Cx<T>::mk(0, 0);
   };
-  C* G = fft_run_io<false, C>(B1, B0, nx, LX, Mz, I.rx, I.nrx, twx, true, ldx, SmemSt<C>{nullptr, 0});
+  C* G = fft_run_io<false, C>(B1, B0, nx, LX, Mz, I.rx, I.nrx, tx, true, ldx, SmemSt<C>{nullptr, 0});
   __syncthreads();
   C* Zb = (G == B0) ? B1 : B0;
   const int nr = nx / 2;
@@ -286,7 +303,7 @@ __global__ void __launch_bounds__(128, PCF_XZ_MINB) k_xzsynth_t(LaunchInfo li, i
       out[(2 * (r0 + r)) * nz + z] = h.x;
       out[(2 * (r0 + r) + 1) * nz + z] = h.y;
     };
-    fft_run_io<true, C>(Z0, Z1, nz, LZ, nrc, I.rz, I.nrz, twz, true, ldz, stz);
+    fft_run_io<true, C>(Z0, Z1, nz, LZ, nrc, I.rz, I.nrz, tz, true, ldz, stz);
     if (r0 + pp.chunk < nr) __syncthreads();  // the next chunk rewrites Z0
   }
 }
@@ -297,9 +314,18 @@ __device__ __forceinline__ const T* fplane(const Inst& I, int s, int f, int j) {
   return phys_of<T>(I) + (((size_t)s * kFieldsSynth + f) * I.ny + j) * (size_t)I.nx * I.nz;
 }
 
+// The 11 field planes of a slot at one y-plane: field f at p + f fs (one base pointer and a
+// stride instead of 11 pointers held in registers).
+template <class T>
+struct PlaneSet {
+  const T* p;
+  int fs;
+  __device__ __forceinline__ const T* operator[](int f) const { return p + f * fs; }
+};
+
 // gradient component d_d (d = 0 x, 1 y, 2 z) of velocity component c at point e of plane j
 template <class T>
-__device__ __forceinline__ T grad_at(const T* const* F, int c, int d, int e) {
+__device__ __forceinline__ T grad_at(const PlaneSet<T>& F, int c, int d, int e) {
   // fields: 3 u_x, 4 u_y, 5 u_z, 6 v_x, 7 v_z, 8 w_x, 9 w_y, 10 w_z; v_y = -u_x - w_z
   if (c == 0) return F[3 + d][e];
   if (c == 2) return F[8 + d][e];
@@ -309,24 +335,27 @@ __device__ __forceinline__ T grad_at(const T* const* F, int c, int d, int e) {
 }
 
 // Pointwise products of the plane, row pairs packed as complex values.
-// Ub, dUb: the base-flow profile U(y_j) and U'(y_j) of the plane (u_b = (U(y), 0, 0)).
-template <class T, bool ADJ>
-__device__ __forceinline__ void product_pair(const Inst& I, const T* const* U, const T* const* Q, int c, T Ub,
-                                             T dUb, int e0, int e1, T* m, typename Acc<T>::type* sq) {
+// Ub, dUb: the base-flow profile U(y_j) and U'(y_j) of the plane; Vb: the base flow's
+// constant wall-normal velocity (u_b = (U(y), Vb, 0)), added to the advecting v only when VB
+// (so that the flows without suction keep their instruction count).
+template <class T, bool ADJ, bool VB>
+__device__ __forceinline__ void product_pair(const Inst& I, const PlaneSet<T>& U, const PlaneSet<T>& Q, int c, T Ub,
+                                             T dUb, T Vb, int e0, int e1, T* m, typename Acc<T>::type* sq) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int e = h == 0 ? e0 : e1;
     const T u = U[0][e], v = U[1][e], w = U[2][e];
+    const T va = VB ? v + Vb : v;  // wall-normal velocity of u_b + u
     if (!ADJ) {
       const T gx = grad_at<T>(U, c, 0, e), gy = grad_at<T>(U, c, 1, e), gz = grad_at<T>(U, c, 2, e);
-      T val = -fma(Ub + u, gx, fma(v, gy, w * gz));
+      T val = -fma(Ub + u, gx, fma(va, gy, w * gz));
       if (c == 0) val -= dUb * v;
       m[h] = val;
     } else {
       const T q0 = Q[0][e], q1 = Q[1][e], q2 = Q[2][e];
       const T qc = Q[c][e];
       acc_sq(sq, qc);
-      const T adv = fma(Ub + u, grad_at<T>(Q, c, 0, e), fma(v, grad_at<T>(Q, c, 1, e), w * grad_at<T>(Q, c, 2, e)));
+      const T adv = fma(Ub + u, grad_at<T>(Q, c, 0, e), fma(va, grad_at<T>(Q, c, 1, e), w * grad_at<T>(Q, c, 2, e)));
       const T tr = fma(q0, grad_at<T>(U, 0, c, e), fma(q1, grad_at<T>(U, 1, c, e), q2 * grad_at<T>(U, 2, c, e)));
       T val = adv - tr;
       if (c == 1) val -= dUb * q0;
@@ -336,26 +365,38 @@ __device__ __forceinline__ void product_pair(const Inst& I, const T* const* U, c
 }
 
 // Products of the rows r0 .. r0 + nrc - 1 of a plane for component CC (a compile-time
-// constant, so that the field indices fold and the plane pointers stay in registers).
-template <class T, bool ADJ, int CC>
-__device__ __forceinline__ void product_rows(const Inst& I, const T* const* U, const T* const* Q, T Ub, T dUb, int r0,
-                                             int nrc, int nz, int LZ, typename Cx<T>::c* Z0,
+// constant, so that the field indices fold).
+template <class T, bool ADJ, int CC, bool VB>
+__device__ __forceinline__ void product_rows(const Inst& I, const PlaneSet<T>& U, const PlaneSet<T>& Q, T Ub, T dUb,
+                                             T Vb, int r0, int nrc, int nz, int LZ, typename Cx<T>::c* Z0,
                                              typename Acc<T>::type* sq) {
   for (int t = threadIdx.x; t < nrc * nz; t += blockDim.x) {
     const int r = t / nz, z = t - r * nz;
     const int e0 = (2 * (r0 + r)) * nz + z, e1 = e0 + nz;
     T m[2];
-    product_pair<T, ADJ>(I, U, Q, CC, Ub, dUb, e0, e1, m, sq);
+    product_pair<T, ADJ, VB>(I, U, Q, CC, Ub, dUb, Vb, e0, e1, m, sq);
     Z0[r * LZ + z] = Cx<T>::mk(m[0], m[1]);
   }
 }
 
+// product_rows for component c (uniform in the CTA)
+template <class T, bool ADJ, bool VB>
+__device__ __forceinline__ void product_rows_c(int c, const Inst& I, const PlaneSet<T>& U, const PlaneSet<T>& Q,
+                                               T Ub, T dUb, T Vb, int r0, int nrc, int nz, int LZ,
+                                               typename Cx<T>::c* Z0, typename Acc<T>::type* sq) {
+  if (c == 0) product_rows<T, ADJ, 0, VB>(I, U, Q, Ub, dUb, Vb, r0, nrc, nz, LZ, Z0, sq);
+  else if (c == 1) product_rows<T, ADJ, 1, VB>(I, U, Q, Ub, dUb, Vb, r0, nrc, nz, LZ, Z0, sq);
+  else product_rows<T, ADJ, 2, VB>(I, U, Q, Ub, dUb, Vb, r0, nrc, nz, LZ, Z0, sq);
+}
+
 // CTA = (instance, plane j, component c): product component c on the plane (M(u) or
-// N(q) with W = u_b + u = (U(y) + u, v, w)), forward FFT in z then x, 2/3 truncation.  ADJ also sums
-// q_c^2 over the plane (in FP64) for J.
+// N(q) with W = u_b + u = (U(y) + u, Vb + v, w)), forward FFT in z then x, 2/3
+// truncation.  ADJ also sums q_c^2 over the plane (in FP64) for J.
 // Register budgets: eight resident CTAs per SM for M(u); six for N(q), which holds both
 // fields' plane pointers (at 8 x 32x33x32 its 792 CTAs then fit one wave of 152 SMs).
-template <class T, bool ADJ>
+// VB: some instance of the launch has a base flow with suction (its own instantiation, so
+// that the flows without suction keep their register allocation).
+template <class T, bool ADJ, bool VB>
 __global__ void __launch_bounds__(128, ADJ ? 6 : 8) k_prod_t(LaunchInfo li, int step_index) {
   using C = typename Cx<T>::c;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -372,15 +413,15 @@ __global__ void __launch_bounds__(128, ADJ ? 6 : 8) k_prod_t(LaunchInfo li, int 
   C* twx = sm + 2 * pp.PB;
   C* twz = twx + nx;
   double* red = reinterpret_cast<double*>(twz + nz);
-  load_twiddles<T>(I, twx, twz);
-  const T* U[kFieldsSynth];
-  const T* Q[kFieldsSynth];
-#pragma unroll
-  for (int f = 0; f < kFieldsSynth; ++f) {
-    U[f] = fplane<T>(I, 0, f, j);
-    Q[f] = ADJ ? fplane<T>(I, 1, f, j) : nullptr;
-  }
+  unsigned char* rtx = reinterpret_cast<unsigned char*>(red + 32);
+  unsigned char* rtz = rtx + nx;
+  PlaneTw<T>::load(I, twx, twz, rtx, rtz, false);
+  const typename PlaneTw<T>::type tx = PlaneTw<T>::view(twx, rtx), tz = PlaneTw<T>::view(twz, rtz);
+  const int fs = I.ny * nx * nz;  // between the fields of a slot
+  const PlaneSet<T> U{fplane<T>(I, 0, 0, j), fs};
+  const PlaneSet<T> Q{ADJ ? fplane<T>(I, 1, 0, j) : nullptr, fs};
   const T Ub = (T)I.ubase[j], dUb = (T)I.ubase[I.ny + j];
+  const T Vb = VB ? (T)I.ubase[2 * I.ny + j] : (T)0.0;  // suction velocity of the base flow
   const int nr = nx / 2, LX = pp.LX, LZ = pp.LZ;
   const bool whole = pp.chunk == nr;
   // the x-stage input X[p][x] lives in B0 when chunked (z chunks use B1), else decided below
@@ -391,11 +432,9 @@ __global__ void __launch_bounds__(128, ADJ ? 6 : 8) k_prod_t(LaunchInfo li, int 
     const int nrc = min(pp.chunk, nr - r0);
     C* Z0 = whole ? B0 : B1;
     C* Z1 = whole ? B1 : B1 + pp.chunk * LZ;
-    if (c == 0) product_rows<T, ADJ, 0>(I, U, Q, Ub, dUb, r0, nrc, nz, LZ, Z0, &sq);
-    else if (c == 1) product_rows<T, ADJ, 1>(I, U, Q, Ub, dUb, r0, nrc, nz, LZ, Z0, &sq);
-    else product_rows<T, ADJ, 2>(I, U, Q, Ub, dUb, r0, nrc, nz, LZ, Z0, &sq);
+    product_rows_c<T, ADJ, VB>(c, I, U, Q, Ub, dUb, Vb, r0, nrc, nz, LZ, Z0, &sq);
     __syncthreads();
-    C* R = fft_run<C>(Z0, Z1, nz, LZ, nrc, I.rz, I.nrz, twz, false);
+    C* R = fft_run<C>(Z0, Z1, nz, LZ, nrc, I.rz, I.nrz, tz, false);
     if (whole) X = (R == B0) ? B1 : B0;
     for (int t = threadIdx.x; t < nrc * Mz; t += blockDim.x) {
       const int r = t / Mz, p = t - r * Mz;
@@ -418,7 +457,7 @@ __global__ void __launch_bounds__(128, ADJ ? 6 : 8) k_prod_t(LaunchInfo li, int 
       I.normpart[(size_t)c * I.ny + j] = s;
     }
   }
-  C* Y = fft_run<C>(X, X == B0 ? B1 : B0, nx, LX, Mz, I.rx, I.nrx, twx, false);
+  C* Y = fft_run<C>(X, X == B0 ? B1 : B0, nx, LX, Mz, I.rx, I.nrx, tx, false);
   const T sc = (T)I.inv_nxnz;
   typename Sto<T>::c* dst = xz_of<T>(I) + ((size_t)c * I.ny + j) * I.nmodes;
   for (int t = threadIdx.x; t < I.nmodes; t += blockDim.x) {
@@ -489,16 +528,22 @@ void launch_xzsynth(int kind, int ctas, size_t smem, cudaStream_t s, LaunchInfo 
   else if (kind == 2) k_xzsynth_t<ff><<<ctas, 128, smem, s>>>(li, slot, nf);
   else k_xzsynth_t<double><<<ctas, 128, smem, s>>>(li, slot, nf);
 }
-void launch_prod(int kind, bool adj, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int step_index) {
+template <class T, bool VB>
+static void launch_prod_t(bool adj, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int step_index) {
+  if (adj) k_prod_t<T, true, VB><<<ctas, 128, smem, s>>>(li, step_index);
+  else k_prod_t<T, false, VB><<<ctas, 128, smem, s>>>(li, -1);
+}
+void launch_prod(int kind, bool adj, bool suction, int ctas, size_t smem, cudaStream_t s, LaunchInfo li,
+                 int step_index) {
   if (kind == 1) {
-    if (adj) k_prod_t<float, true><<<ctas, 128, smem, s>>>(li, step_index);
-    else k_prod_t<float, false><<<ctas, 128, smem, s>>>(li, -1);
+    if (suction) launch_prod_t<float, true>(adj, ctas, smem, s, li, step_index);
+    else launch_prod_t<float, false>(adj, ctas, smem, s, li, step_index);
   } else if (kind == 2) {
-    if (adj) k_prod_t<ff, true><<<ctas, 128, smem, s>>>(li, step_index);
-    else k_prod_t<ff, false><<<ctas, 128, smem, s>>>(li, -1);
+    if (suction) launch_prod_t<ff, true>(adj, ctas, smem, s, li, step_index);
+    else launch_prod_t<ff, false>(adj, ctas, smem, s, li, step_index);
   } else {
-    if (adj) k_prod_t<double, true><<<ctas, 128, smem, s>>>(li, step_index);
-    else k_prod_t<double, false><<<ctas, 128, smem, s>>>(li, -1);
+    if (suction) launch_prod_t<double, true>(adj, ctas, smem, s, li, step_index);
+    else launch_prod_t<double, false>(adj, ctas, smem, s, li, step_index);
   }
 }
 void launch_norm_planes(int kind, int ctas, cudaStream_t s, LaunchInfo li, int slot) {
@@ -510,8 +555,10 @@ template <class T>
 static cudaError_t set_plane_smem_t(size_t synth, size_t prod) {
   cudaError_t e;
   if ((e = raise_smem_limit((const void*)k_xzsynth_t<T>, synth))) return e;
-  if ((e = raise_smem_limit((const void*)k_prod_t<T, false>, prod))) return e;
-  return raise_smem_limit((const void*)k_prod_t<T, true>, prod);
+  if ((e = raise_smem_limit((const void*)k_prod_t<T, false, false>, prod))) return e;
+  if ((e = raise_smem_limit((const void*)k_prod_t<T, false, true>, prod))) return e;
+  if ((e = raise_smem_limit((const void*)k_prod_t<T, true, true>, prod))) return e;
+  return raise_smem_limit((const void*)k_prod_t<T, true, false>, prod);
 }
 cudaError_t set_plane_smem(int kind, size_t synth, size_t prod) {
   if (kind == 1) return set_plane_smem_t<float>(synth, prod);

@@ -80,7 +80,9 @@ cudaError_t raise_smem_limit(const void* func, size_t bytes);
 void launch_xzsynth(int kind, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int slot, int nf);
 // step_index >= 0 (adjoint product only): the last CTA of each instance also computes J from
 // the plane sums, its history entry and the convergence mask (in place of launch_jnorm)
-void launch_prod(int kind, bool adj, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int step_index = -1);
+// suction: some instance of the launch has a base flow with a wall-normal velocity (ASBL)
+void launch_prod(int kind, bool adj, bool suction, int ctas, size_t smem, cudaStream_t s, LaunchInfo li,
+                 int step_index = -1);
 void launch_norm_planes(int kind, int ctas, cudaStream_t s, LaunchInfo li, int slot);
 cudaError_t set_plane_smem(int kind, size_t synth, size_t prod);
 // Plane kernels of the FP32 form with the x, z transforms in warp registers

@@ -152,5 +152,78 @@ __device__ __forceinline__ void butterfly<3, float2>(float2* v, bool inv) { butt
 template <>
 __device__ __forceinline__ void butterfly<3, ff2>(ff2* v, bool inv) { butterfly3(v, inv); }
 
+// ------------------------------------------------------------------ twiddled butterflies
+// A Stockham pass of radix R with Ns > 1 multiplies input r of butterfly k by w^(r q1),
+// q1 = k * twstep, w = exp(-2 pi i/L) (its conjugate for the inverse transform), then applies
+// the radix-R DFT.  Two twiddle representations:
+//
+// TwStd: the table tw[q] = w^q; a complex multiply per twiddled input, then the butterfly
+// (radix 4 with three twiddles: 28 FP64 operations; radix 2: 8).
+//
+// TwTan (FP64): every twiddle in the tangent form of Linzer and Feig (FMA-based FFT
+// butterflies, IEEE Trans. Signal Process. 1993): w^q = m (rot ? i : 1)(1 + i t) with |t| <= 1, so that
+// x +- w^q y costs six fused multiply-adds: z = y (1 + i t) takes two, x +- m z four (a factor
+// i swaps the parts of z, done with selects on the integer pipe).  A radix-4 butterfly is
+// four such pairs, using w^(3 q1) y3 +- ... = w^q1 (y1 +- w^(2 q1) y3) and -i w^q1 = w^(q1 + L/4):
+// 24 FMAs.  Radix 2: one pair, 6 FMAs.  The entries e[q] = (t, m) and rot[q] are built on
+// the host for the transform's direction (conjugated for the inverse).
+template <class C>
+struct TwStd {
+  const C* tw;
+};
+struct TwTan {
+  const double2* e;
+  const unsigned char* rot;
+};
+
+// (x + w y, x - w y) for the tangent-form twiddle (e, rot)
+__device__ __forceinline__ void tan_pm(double2 x, double2 y, double2 e, bool rot, double2* P, double2* Q) {
+  const double zr = fma(-e.x, y.y, y.x), zi = fma(e.x, y.x, y.y);
+  const double u = rot ? zi : zr, v = rot ? zr : zi;
+  const double rp = fma(e.y, u, x.x), rm = fma(-e.y, u, x.x);
+  const double ip = fma(e.y, v, x.y), im = fma(-e.y, v, x.y);
+  *P = make_double2(rot ? rm : rp, ip);
+  *Q = make_double2(rot ? rp : rm, im);
+}
+
+// The twiddled radix-R butterfly of a pass (Ns > 1), input r of butterfly k at v[r].
+template <int R, class C>
+__device__ __forceinline__ void tw_butterfly(C* v, const TwStd<C>& T, int k, int twstep, int L, bool inv) {
+#pragma unroll
+  for (int r = 1; r < R; ++r) {
+    C w = T.tw[r * k * twstep];
+    if (inv) w.y = -w.y;
+    v[r] = cmul(v[r], w);
+  }
+  butterfly<R, C>(v, inv);
+}
+template <int R>
+__device__ __forceinline__ void tw_butterfly(double2* v, const TwTan& T, int k, int twstep, int L, bool inv) {
+  const int q1 = k * twstep;
+  if (R == 2) {
+    tan_pm(v[0], v[1], T.e[q1], T.rot[q1], &v[0], &v[1]);
+  } else if (R == 4) {
+    const int q2 = 2 * q1, q3 = q1 + L / 4;
+    const double2 e2 = T.e[q2];
+    const bool r2 = T.rot[q2];
+    double2 t0, t1, P, Q;
+    tan_pm(v[0], v[2], e2, r2, &t0, &t1);
+    tan_pm(v[1], v[3], e2, r2, &P, &Q);
+    tan_pm(t0, P, T.e[q1], T.rot[q1], &v[0], &v[2]);
+    tan_pm(t1, Q, T.e[q3], T.rot[q3], &v[1], &v[3]);
+  } else {
+    // radix 3: rebuild w^(r q1) = (m, m t) or (-m t, m) and multiply
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      const int q = r * q1;
+      const double2 e = T.e[q];
+      const double mt = e.y * e.x;
+      const double2 w = T.rot[q] ? make_double2(-mt, e.y) : make_double2(e.y, mt);
+      v[r] = cmul(v[r], w);
+    }
+    butterfly<R, double2>(v, inv);
+  }
+}
+
 
 }  // namespace pcf

@@ -334,8 +334,8 @@ struct GradField {
 // in the convective forms of §4, with the association order of product_pair (the last
 // term first), streamed so that only two fields are live at a time; ADJ also sums q_CC^2.
 template <class T, bool ADJ, int CC>
-__device__ __forceinline__ void product_seg(const T* U, const T* Q, int fstride, int off, int E, T Ub, T dUb, T* m,
-                                            double* sq) {
+__device__ __forceinline__ void product_seg(const T* U, const T* Q, int fstride, int off, int E, T Ub, T dUb, T Vb,
+                                            T* m, double* sq) {
   T a[4], g[4], acc[4];
   if (!ADJ) {
     seg<T, 2>(U, fstride, off, E, a);
@@ -346,7 +346,7 @@ __device__ __forceinline__ void product_seg(const T* U, const T* Q, int fstride,
     seg<T, 1>(U, fstride, off, E, vv);
     seg<T, GradField<CC, 1>::f>(U, fstride, off, E, g);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = fma(vv[q], g[q], acc[q]);
+    for (int q = 0; q < 4; ++q) acc[q] = fma(vv[q] + Vb, g[q], acc[q]);  // v of u_b + u
     seg<T, 0>(U, fstride, off, E, a);
     seg<T, GradField<CC, 0>::f>(U, fstride, off, E, g);
 #pragma unroll
@@ -364,7 +364,7 @@ __device__ __forceinline__ void product_seg(const T* U, const T* Q, int fstride,
     seg<T, 1>(U, fstride, off, E, a);
     seg<T, GradField<CC, 1>::f>(Q, fstride, off, E, g);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = fma(a[q], g[q], acc[q]);
+    for (int q = 0; q < 4; ++q) acc[q] = fma(a[q] + Vb, g[q], acc[q]);
     seg<T, 0>(U, fstride, off, E, a);
     seg<T, GradField<CC, 0>::f>(Q, fstride, off, E, g);
     T adv[4];
@@ -401,7 +401,7 @@ __device__ __forceinline__ void product_seg(const T* U, const T* Q, int fstride,
 // DIT transform, two-for-one unpacking of the retained z modes into X[p][x1], X[p][x1 + 1].
 template <class T, bool ADJ, int CC>
 __device__ __forceinline__ void prod_row_pair(const Inst& I, const T* U, const T* Q, int fstride, int x1, T Ub,
-                                              T dUb, int EZ, const typename Cx<T>::c* twz,
+                                              T dUb, T Vb, int EZ, const typename Cx<T>::c* twz,
                                               const typename Cx<T>::c* w32, typename Cx<T>::c* X, int LG, int lane,
                                               double* sq) {
   using C = typename Cx<T>::c;
@@ -412,7 +412,7 @@ __device__ __forceinline__ void prod_row_pair(const Inst& I, const T* U, const T
 #pragma unroll 1
   for (int row = 0; row < 2; ++row) {
     T m[4];
-    product_seg<T, ADJ, CC>(U, Q, fstride, (x1 + row) * nz + z0, EZ, Ub, dUb, m, sq);
+    product_seg<T, ADJ, CC>(U, Q, fstride, (x1 + row) * nz + z0, EZ, Ub, dUb, Vb, m, sq);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (row == 0) h[q].x = m[q];
@@ -466,15 +466,15 @@ __global__ void __launch_bounds__(kWarpPlaneThreads, 2) k_prod_w(LaunchInfo li, 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   C w32[4];
   net_twiddles(w32, twz, EZ, lane);
-  const T Ub = (T)I.ubase[j], dUb = (T)I.ubase[I.ny + j];
+  const T Ub = (T)I.ubase[j], dUb = (T)I.ubase[I.ny + j], Vb = (T)I.ubase[2 * I.ny + j];
   double sq = 0.0;
   const int fstride = I.ny * nx * I.nz;  // between the fields of a slot
   const T* U = phys_of<T>(I) + (size_t)j * nx * I.nz;
   const T* Q = ADJ ? U + (size_t)kFieldsSynth * fstride : nullptr;
   for (int r = warp; r < nx / 2; r += nw) {
-    if (c == 0) prod_row_pair<T, ADJ, 0>(I, U, Q, fstride, 2 * r, Ub, dUb, EZ, twz, w32, X, LG, lane, &sq);
-    else if (c == 1) prod_row_pair<T, ADJ, 1>(I, U, Q, fstride, 2 * r, Ub, dUb, EZ, twz, w32, X, LG, lane, &sq);
-    else prod_row_pair<T, ADJ, 2>(I, U, Q, fstride, 2 * r, Ub, dUb, EZ, twz, w32, X, LG, lane, &sq);
+    if (c == 0) prod_row_pair<T, ADJ, 0>(I, U, Q, fstride, 2 * r, Ub, dUb, Vb, EZ, twz, w32, X, LG, lane, &sq);
+    else if (c == 1) prod_row_pair<T, ADJ, 1>(I, U, Q, fstride, 2 * r, Ub, dUb, Vb, EZ, twz, w32, X, LG, lane, &sq);
+    else prod_row_pair<T, ADJ, 2>(I, U, Q, fstride, 2 * r, Ub, dUb, Vb, EZ, twz, w32, X, LG, lane, &sq);
   }
   if (ADJ) {
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(kFull, sq, o);

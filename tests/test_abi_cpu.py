@@ -40,7 +40,7 @@ def test_host_only_queries(lib):
     lib.pcf_state_len.restype = ctypes.c_longlong
     lib.pcf_psi_len.restype = ctypes.c_longlong
     lib.pcf_status_str.restype = ctypes.c_char_p
-    assert lib.pcf_abi_version() == 2
+    assert lib.pcf_abi_version() == 3
     assert lib.pcf_state_len(32, 33, 32) == 3 * 19 * 10 * 33
     assert lib.pcf_state_len(30, 33, 32) == 0          # 30 = 2*3*5 has a radix-5 factor
     assert lib.pcf_state_len(32, 32, 32) == 0          # even ny rejected
@@ -56,3 +56,8 @@ def test_create_rejects_bad_params_without_gpu(lib):
     h = ctypes.c_void_p()
     assert pcf._lib.pcf_create(ctypes.byref(p), None, ctypes.byref(h)) == 1   # PCF_EINVAL, before any CUDA call
     assert not h.value
+    # the suction boundary layer needs a finite suction length > 0, and s1 maps it to blowing
+    for delta, sym in ((0.0, 0), (-0.5, 0), (float("nan"), 0), (float("inf"), 0), (0.5, pcf.SYM_S1)):
+        p = pcf._Params(32, 33, 32, 1, 1.0, 1.0, 400.0, 0.25, 0.25, 0, 0, 0, pcf.ASBL, sym, 0, 0, delta)
+        assert pcf._lib.pcf_create(ctypes.byref(p), None, ctypes.byref(h)) == 1
+        assert not h.value
