@@ -35,7 +35,8 @@ WORKLOAD = "PCF Re=400 box 2pi/1.14 x 2 x 2pi/2.5, 32x33x32, 8 streak/roll guess
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel classes,
 # read from one ncu capture of the current kernels on this workload; reset an entry to None
 # when that kernel changes.
-TRAFFIC_BYTES = {"xzsynth_u": 4.09e6, "xzsynth_q": 4.09e6}
+# Capture of the tangent-twiddle plane kernels (--mode-tile 4, one step's launches).
+TRAFFIC_BYTES = {"xzsynth_u": 4.096768e6, "xzsynth_q": 4.096768e6, "prod_M": 23.83616e6, "prod_N": 47.641088e6}
 
 
 def _peaks():
