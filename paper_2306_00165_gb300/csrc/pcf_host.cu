@@ -551,9 +551,9 @@ pcf_status step_body(pcf_ctx* c, int s) {
     PCF_TRY(launch_mode(c, MODE_PHI, 0, s));
     PCF_TRY(launch_tc_synth(c, 1));
     PCF_TRY(launch_synth(c, 1, kFieldsSynth));
-    PCF_TRY(launch_prodN(c));
+    PCF_TRY(launch_prodN(c, s));  // with J, its history entry and the convergence mask
     PCF_TRY(launch_tc_analysis(c));
-    PCF_TRY(launch_mode(c, MODE_PSI_UPDATE, 1, s));
+    PCF_TRY(launch_mode(c, MODE_PSI_UPDATE, 1, -1));
     if (c->any_sym) PCF_TRY(launch_sym(c, -1));  // the next step's synthesis reads the projected state
     return PCF_OK;
   }
@@ -595,8 +595,8 @@ pcf_status step_body(pcf_ctx* c, int s) {
   PCF_TRY(launch_prodM(c));
   PCF_TRY(launch_mode(c, MODE_PHI, 0, s));
   PCF_TRY(launch_synth(c, 1, kFieldsSynth));
-  PCF_TRY(launch_prodN(c));
-  PCF_TRY(launch_mode(c, MODE_PSI_UPDATE, 1, s));
+  PCF_TRY(launch_prodN(c, s));  // with J, its history entry and the convergence mask
+  PCF_TRY(launch_mode(c, MODE_PSI_UPDATE, 1, -1));
   if (c->any_sym) {
     PCF_TRY(launch_sym(c, -1));
     PCF_TRY(launch_ysynth(c, 0));

@@ -581,6 +581,30 @@ size_t smem_mode(const Inst& I, int mpc) {
   return d * sizeof(double);
 }
 
+// a0 += sum_j col[j stride] x0[j] and a1 += sum_j col[j stride] x1[j] over j < n, each chain in
+// index order; the operator column is read through the read-only cache eight elements ahead of
+// the FMAs, so that a thread keeps eight loads in flight (the dense operators of a large grid
+// come from HBM, and one outstanding load per thread left the solve waiting on latency).
+__device__ __forceinline__ void dot2_ldg(const double* col, int stride, const double* x0, const double* x1, int n,
+                                         double& a0, double& a1) {
+  int j = 0;
+  for (; j + 8 <= n; j += 8) {
+    double d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) d[k] = __ldg(col + (j + k) * stride);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      a0 = fma(d[k], x0[j + k], a0);
+      a1 = fma(d[k], x1[j + k], a1);
+    }
+  }
+  for (; j < n; ++j) {
+    const double d = __ldg(col + j * stride);
+    a0 = fma(d, x0[j], a0);
+    a1 = fma(d, x1[j], a1);
+  }
+}
+
 __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, int mpc_arg, int step_index) {
   extern __shared__ double smd[];
   int local;
@@ -596,14 +620,18 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
   const ChebLayout CL(N);
   const bool solve = (op != MODE_SYNTH_ONLY);
 
-  // descent: norm of r1 (computed by k_prod_N), history and convergence decision
+  // descent: J = ||r1|| from the plane sums of k_prod<N>, its history entry and the
+  // convergence decision; step_index < 0: the product kernel has taken them already (the
+  // instance's mask then holds this step's J < tol)
   if (op == MODE_PSI_UPDATE) {
     if (!inst_active(I)) return;
-    const double J = norm_from_parts(I);
-    if (local == 0 && threadIdx.x == 0 && I.hist) I.hist[(size_t)step_index * I.hist_stride] = J;
-    if (I.tol > 0.0 && J < I.tol) {
-      if (local == 0 && threadIdx.x == 0 && I.active) *I.active = 0;
-      return;
+    if (step_index >= 0) {
+      const double J = norm_from_parts(I);
+      if (local == 0 && threadIdx.x == 0 && I.hist) I.hist[(size_t)step_index * I.hist_stride] = J;
+      if (I.tol > 0.0 && J < I.tol) {
+        if (local == 0 && threadIdx.x == 0 && I.active) *I.active = 0;
+        return;
+      }
     }
   } else if (op != MODE_SOLVE && op != MODE_SYNTH_ONLY && !inst_active(I)) {
     return;
@@ -720,43 +748,53 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
         sc[Mh + i] = sgn * fma(kz, fu, -kx * fw);
       }
       __syncthreads();
-      for (int t = threadIdx.x; t < nmod * 4 * 3 * Mh; t += blockDim.x) {
-        const int r = t % Mh, q = t / Mh, which = q % 3, c4 = q / 3, mm = c4 >> 2, g = (c4 >> 1) & 1,
-                  rho = c4 & 1;
+      // Two task lists, so that a warp's lanes carry chains of one length: list A, one v row
+      // (Av f_v + Ag g: McV + McP terms) per task; list B, two eta rows (Eh h: McP terms
+      // each) per task.  A task runs both parts' chains (real and imaginary right-hand
+      // sides), which share each operator load; every chain keeps the index order of the
+      // other kernel organisations.  Mean mode: list A holds the u rows, list B the w rows.
+      const int HB = (Mh + 1) / 2, nA = nmod * 2 * Mh, nB = nmod * 2 * HB;
+      for (int t = threadIdx.x; t < nA + nB; t += blockDim.x) {
+        const bool isA = t < nA;
+        const int tt = isA ? t : t - nA, per = isA ? Mh : HB;
+        const int r = tt % per, q = tt / per, g = q & 1, mm = q >> 1;
         const int pv = g, pP = 1 - g, McV = (N - pv) / 2 + 1, McP = (N - pP) / 2 + 1;
         const int m = m0 + mm, ix = m / Mz, p = m - ix * Mz;
         const double kx = I.kx[ix], kz = I.kz[p];
         const double* D = dn + (size_t)m * DL.per_mode();
         const double* fr = Fr + (size_t)mm * 6 * L2;
-        double* sc = Ch + ((size_t)mm * 4 + g * 2 + rho) * 6 * Mh;
+        double* s0 = Ch + ((size_t)mm * 4 + g * 2) * 6 * Mh;  // real part's chain scratch
+        double* s1 = s0 + 6 * Mh;                            // imaginary part's
         if (kx == 0.0 && kz == 0.0) {
-          // mean mode: u (which 0) and w (which 1) of class g
           const int Mc = (N - g) / 2 + 1;
-          if (which == 2 || r >= Mc) continue;
-          const double* col = D + DL.at(g, DL.kEh, r, 0);
-          const double* f = fr + ((which == 0 ? 0 : 2) * 2 + rho) * L2 + g * Mh;
-          double a = 0.0;
-          for (int j = 0; j < Mc; ++j) a = fma(__ldg(col + j * Mh), f[j], a);
-          sc[(which == 0 ? 0 : Mh) + r] = a;
+          const double* f0 = fr + (isA ? 0 : 4) * L2 + g * Mh;  // f_u or f_w, class g
+          for (int h = 0; h < (isA ? 1 : 2); ++h) {
+            const int row = r + h * HB;
+            if (row >= Mc) continue;
+            double a0 = 0.0, a1 = 0.0;
+            dot2_ldg(D + DL.at(g, DL.kEh, row, 0), Mh, f0, f0 + L2, Mc, a0, a1);
+            s0[(isA ? 0 : Mh) + row] = a0;
+            s1[(isA ? 0 : Mh) + row] = a1;
+          }
           continue;
         }
-        const double* fv = fr + (1 * 2 + rho) * L2 + pv * Mh;
-        if (which == 0) {
+        if (isA) {  // v = Av f_v + Ag g
           if (r >= McV) continue;
-          const double* ra = D + DL.at(g, DL.kAv, r, 0);
-          const double* rg = D + DL.at(g, DL.kAg, r, 0);
-          double a = 0.0;
-          for (int j = 0; j < McV; ++j) a = fma(__ldg(ra + j * Mh), fv[j], a);
-          for (int j = 0; j < McP; ++j) a = fma(__ldg(rg + j * Mh), sc[j], a);
-          sc[2 * Mh + r] = a;
-        } else if (which == 1) {
-          continue;  // xi = -dv/dy follows from v below
-        } else {
-          if (r >= McP) continue;
-          const double* re = D + DL.at(g, DL.kEh, r, 0);
-          double a = 0.0;
-          for (int j = 0; j < McP; ++j) a = fma(__ldg(re + j * Mh), sc[Mh + j], a);
-          sc[4 * Mh + r] = a;
+          const double* fv0 = fr + 2 * L2 + pv * Mh;
+          double a0 = 0.0, a1 = 0.0;
+          dot2_ldg(D + DL.at(g, DL.kAv, r, 0), Mh, fv0, fv0 + L2, McV, a0, a1);
+          dot2_ldg(D + DL.at(g, DL.kAg, r, 0), Mh, s0, s1, McP, a0, a1);
+          s0[2 * Mh + r] = a0;
+          s1[2 * Mh + r] = a1;
+        } else {  // eta = Eh h, rows r and r + HB
+          for (int h = 0; h < 2; ++h) {
+            const int row = r + h * HB;
+            if (row >= McP) continue;
+            double a0 = 0.0, a1 = 0.0;
+            dot2_ldg(D + DL.at(g, DL.kEh, row, 0), Mh, s0 + Mh, s1 + Mh, McP, a0, a1);
+            s0[4 * Mh + row] = a0;
+            s1[4 * Mh + row] = a1;
+          }
         }
       }
       __syncthreads();
