@@ -573,11 +573,11 @@ __global__ void k_norm_final(LaunchInfo li, double* out) {
 // ------------------------------------------------------------------ per-mode kernel
 size_t smem_mode(const Inst& I, int mpc) {
   // [cheb (FP64 form only)] + rco + per mode: [solver table (sweep solve only)],
-  // Fr/U0/Out ([3][2][L2] each), chain scratch [4][6][Mh]
+  // Fr/U0/Out ([3][2][L2] each), chain scratch [4][6][Mh], 1/k^2
   const int N = I.N, Mh = N / 2 + 1, H = Mh, L2 = 2 * Mh;
   const TabLayout TL(N);
   size_t d = (I.mixed ? 0 : 6 * (size_t)H * H) + 10 * (size_t)Mh;
-  d += (size_t)mpc * ((I.dense[0] ? 0 : TL.per_mode()) + 18 * (size_t)L2 + 24 * (size_t)Mh);
+  d += (size_t)mpc * ((I.dense[0] ? 0 : TL.per_mode()) + 18 * (size_t)L2 + 24 * (size_t)Mh + 1);
   return d * sizeof(double);
 }
 
@@ -646,6 +646,15 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
   double* U0 = Fr + (size_t)mpc * 6 * L2;        // [mpc][3][2][L2]
   double* Out = U0 + (size_t)mpc * 6 * L2;       // [mpc][3][2][L2] (also y-values input)
   double* Ch = Out + (size_t)mpc * 6 * L2;       // [mpc][4][6][Mh]
+  double* IK2 = Ch + (size_t)mpc * 24 * Mh;      // [mpc] 1/k^2 (0 for the mean mode)
+
+  // 1/k^2 once per mode: an FP64 division costs the pipe per lane-instruction
+  for (int t = threadIdx.x; t < nmod; t += blockDim.x) {
+    const int m = m0 + t, ix = m / Mz, p = m - ix * Mz;
+    const double kx = I.kx[ix], kz = I.kz[p];
+    const double k2 = kx * kx + kz * kz;
+    IK2[t] = m == 0 ? 0.0 : 1.0 / k2;
+  }
 
   if (need_cheb)
     for (int t = threadIdx.x; t < CL.total(); t += blockDim.x) cheb[t] = I.cheb[t];
@@ -738,7 +747,7 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
         const int pP = 1 - g, McP = (N - pP) / 2 + 1;
         const int m = m0 + mm, ix = m / Mz, p = m - ix * Mz;
         const double kx = I.kx[ix], kz = I.kz[p];
-        if (i >= McP || (kx == 0.0 && kz == 0.0)) continue;
+        if (i >= McP || m == 0) continue;  // m == 0: the mean mode
         const double* fr = Fr + (size_t)mm * 6 * L2;
         const double fu = fr[(0 * 2 + (1 - rho)) * L2 + pP * Mh + i];
         const double fw = fr[(2 * 2 + (1 - rho)) * L2 + pP * Mh + i];
@@ -759,13 +768,12 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
         const int tt = isA ? t : t - nA, per = isA ? Mh : HB;
         const int r = tt % per, q = tt / per, g = q & 1, mm = q >> 1;
         const int pv = g, pP = 1 - g, McV = (N - pv) / 2 + 1, McP = (N - pP) / 2 + 1;
-        const int m = m0 + mm, ix = m / Mz, p = m - ix * Mz;
-        const double kx = I.kx[ix], kz = I.kz[p];
+        const int m = m0 + mm;
         const double* D = dn + (size_t)m * DL.per_mode();
         const double* fr = Fr + (size_t)mm * 6 * L2;
         double* s0 = Ch + ((size_t)mm * 4 + g * 2) * 6 * Mh;  // real part's chain scratch
         double* s1 = s0 + 6 * Mh;                            // imaginary part's
-        if (kx == 0.0 && kz == 0.0) {
+        if (m == 0) {  // the mean mode
           const int Mc = (N - g) / 2 + 1;
           const double* f0 = fr + (isA ? 0 : 4) * L2 + g * Mh;  // f_u or f_w, class g
           for (int h = 0; h < (isA ? 1 : 2); ++h) {
@@ -802,7 +810,7 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
       for (int t = threadIdx.x; t < nmod * 4; t += blockDim.x) {
         const int mm = t >> 2, g = (t >> 1) & 1, rho = t & 1;
         const int m = m0 + mm, ix = m / Mz, p = m - ix * Mz;
-        if (I.kx[ix] == 0.0 && I.kz[p] == 0.0) continue;
+        if (m == 0) continue;
         double* sc = Ch + ((size_t)mm * 4 + g * 2 + rho) * 6 * Mh;
         xi_from_v(N, g, sc + 2 * Mh, 1, sc + 3 * Mh, 1);
       }
@@ -842,10 +850,9 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
       }
       const int m = m0 + mm, ix = m / Mz, p = m - ix * Mz;
       const double kx = I.kx[ix], kz = I.kz[p];
-      const double k2 = kx * kx + kz * kz;
       const double* chv_re = Ch + ((size_t)mm * 4 + par * 2 + 0) * 6 * Mh;
       const double* chv_im = Ch + ((size_t)mm * 4 + par * 2 + 1) * 6 * Mh;
-      if (k2 == 0.0) {
+      if (m == 0) {  // the mean mode
         o[0 * L2 + pos] = chv_re[i];
         o[1 * L2 + pos] = chv_im[i];
         o[2 * L2 + pos] = 0.0;
@@ -858,7 +865,7 @@ __global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, in
       const double* cxe_im = Ch + ((size_t)mm * 4 + (1 - par) * 2 + 1) * 6 * Mh;
       const double xr = cxe_re[3 * Mh + i], xi = cxe_im[3 * Mh + i];
       const double er = cxe_re[4 * Mh + i], ei = cxe_im[4 * Mh + i];
-      const double ik2 = 1.0 / k2;
+      const double ik2 = IK2[mm];
       o[0 * L2 + pos] = fma(kx, xi, kz * ei) * ik2;
       o[1 * L2 + pos] = -fma(kx, xr, kz * er) * ik2;
       o[2 * L2 + pos] = chv_re[2 * Mh + i];
