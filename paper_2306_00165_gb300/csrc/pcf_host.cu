@@ -424,7 +424,7 @@ pcf_status timed(pcf_ctx* c, int cls, F&& launch) {
 
 pcf_status launch_mode(pcf_ctx* c, int op, int sig, int step_index) {
   return timed(c, op == MODE_PHI ? 3 : (op == MODE_SYNTH_ONLY ? 0 : 6), [&] {
-    k_mode<<<c->cta_mode, 128, c->sm_mode, c->cs>>>(li_of(c, c->pre_mode), op, sig, c->mpc, step_index);
+    k_mode<<<c->cta_mode, c->mode_thr, c->sm_mode, c->cs>>>(li_of(c, c->pre_mode), op, sig, c->mpc, step_index);
   });
 }
 pcf_status launch_synth(pcf_ctx* c, int slot, int nf) {
@@ -801,6 +801,17 @@ static pcf_status set_mode_tiles(pcf_ctx* c, int want) {
   }
   c->mpc = want;
   c->sm_mode = sm;
+  // threads per CTA: with the dense operators, one warp-padded pass over the solve's tasks
+  // (two v rows, or two pairs of eta rows, per mode and parity group), 128 to 320 (the
+  // kernel's launch bound)
+  int thr = 128;
+  for (int b = 0; b < c->B; ++b) {
+    const Inst& I = c->hinst[b];
+    if (!I.dense[0]) continue;
+    const int Mh = I.N / 2 + 1, tasks = I.mpc * (2 * Mh + 2 * ((Mh + 1) / 2));
+    thr = std::max(thr, std::min(320, (tasks + 31) / 32 * 32));
+  }
+  c->mode_thr = thr;
   PCF_TRY(upload_prefix(c, per, &c->pre_mode, &c->cta_mode));
   PCF_CUDA(raise_smem_limit((const void*)k_mode, c->sm_mode));
   return PCF_OK;
@@ -1049,10 +1060,10 @@ static pcf_status time_mode_tiles(pcf_ctx* c, cudaEvent_t a, cudaEvent_t b, int*
   for (int mpc : cand) {
     if (set_mode_tiles(c, mpc) != PCF_OK) continue;
     PCF_TRY(push_descriptors(c));
-    k_mode<<<c->cta_mode, 128, c->sm_mode, c->cs>>>(li_of(c, c->pre_mode), MODE_PHI, 0, mpc, 0);
+    k_mode<<<c->cta_mode, c->mode_thr, c->sm_mode, c->cs>>>(li_of(c, c->pre_mode), MODE_PHI, 0, mpc, 0);
     PCF_CUDA(cudaEventRecord(a, c->cs));
     for (int r = 0; r < 3; ++r)
-      k_mode<<<c->cta_mode, 128, c->sm_mode, c->cs>>>(li_of(c, c->pre_mode), MODE_PHI, 0, mpc, 0);
+      k_mode<<<c->cta_mode, c->mode_thr, c->sm_mode, c->cs>>>(li_of(c, c->pre_mode), MODE_PHI, 0, mpc, 0);
     PCF_CUDA(cudaEventRecord(b, c->cs));
     PCF_CUDA(cudaEventSynchronize(b));
     float ms = 0.f;

@@ -605,7 +605,7 @@ __device__ __forceinline__ void dot2_ldg(const double* col, int stride, const do
   }
 }
 
-__global__ void __launch_bounds__(128) k_mode(LaunchInfo li, int op, int sig, int mpc_arg, int step_index) {
+__global__ void __launch_bounds__(320) k_mode(LaunchInfo li, int op, int sig, int mpc_arg, int step_index) {
   extern __shared__ double smd[];
   int local;
   const int b = find_inst(li, blockIdx.x, &local);
