@@ -1,11 +1,11 @@
-"""The exact gradient g_h of the discrete cost J_h = 1/2 ||r1||^2 (§8's reading of the
-north_star's "gradient against finite differences of J"), and the paper's direction f
-against it (CPU only).
+"""The exact gradient g_h of the discrete cost J_h = 1/2 ||r1||^2 (the discrete reading of
+a gradient check against finite differences of J), and the paper's direction f against
+it (CPU only).
 
 * J_h of the PyTorch restatement equals 1/2 J^2 of the numpy oracle.
 * <g_h, v> equals the centred finite difference of the numpy oracle's 1/2 J^2 along v to
-  1e-6 relative, for admissible and for arbitrary directions v, with Couette and
-  Poiseuille base flows: the transposed discrete chain is right.
+  1e-6 relative, for admissible and for arbitrary directions v, with the Couette,
+  Poiseuille and suction boundary layer base flows: the transposed discrete chain is right.
 * The paper's f (§4 steps 3-4, Eq. (f_approximation)) is a descent direction of J_h:
   <g_h, f> < 0, at the paper's step sizes and at larger ones.
 * A mistake planted in the differentiated residual (a dropped production term) fails the
