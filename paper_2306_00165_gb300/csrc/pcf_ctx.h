@@ -14,6 +14,7 @@ struct pcf_ctx {
   bool uniform = true;   // every instance on the same problem
   bool suction = false;  // some instance has a base flow with suction (PCF_ASBL)
   int mode_thr = 128;    // threads per CTA of the single per-mode kernel
+  int thr_ya = 256, thr_yy = 128;  // threads per CTA of the split analysis and synthesis
   bool mixed = false;    // mixed-precision form (FP32 planes, split-BF16 Chebyshev, FP64 solves)
   int plane_kind = 0;    // arithmetic of the x-z plane kernels: 0 FP64, 1 FP32, 2 float-float
   bool plane_warp = false;  // FP32 plane kernels with the transforms in warp registers

@@ -469,8 +469,8 @@ GroupLaunch gl_of(pcf_ctx* c, const int* pre, int red = 0) {
 // red: the reduced launch of a symmetric descent step (modes m >= 0 only)
 pcf_status launch_split_analysis(pcf_ctx* c, int op, bool red = false) {
   return timed(c, 7, [&] {
-    launch_yanalysis(red ? c->cta_ya_r : c->cta_ya, c->sm_ya, c->cs, gl_of(c, red ? c->pre_ya_r : c->pre_ya, red), op,
-                     c->plane_kind == 2, c->smt);
+    launch_yanalysis(red ? c->cta_ya_r : c->cta_ya, c->thr_ya, c->sm_ya, c->cs,
+                     gl_of(c, red ? c->pre_ya_r : c->pre_ya, red), op, c->plane_kind == 2, c->smt);
   });
 }
 GroupLaunch gl_solve(pcf_ctx* c, bool red = false) {
@@ -491,8 +491,8 @@ pcf_status launch_split_jnorm(pcf_ctx* c, int step_index) {
 }
 pcf_status launch_split_synth(pcf_ctx* c, int slot, int in_step, bool red = false) {
   return timed(c, in_step ? 8 : 0, [&] {
-    launch_ysynth_split(red ? c->cta_yy_r : c->cta_yy, c->sm_yy, c->cs, gl_of(c, red ? c->pre_yy_r : c->pre_yy, red),
-                        slot, in_step, c->plane_kind == 2, c->smt_y);
+    launch_ysynth_split(red ? c->cta_yy_r : c->cta_yy, c->thr_yy, c->sm_yy, c->cs,
+                        gl_of(c, red ? c->pre_yy_r : c->pre_yy, red), slot, in_step, c->plane_kind == 2, c->smt_y);
   });
 }
 
@@ -896,6 +896,7 @@ static pcf_status set_split_groups(pcf_ctx* c, int G, int mt = 1, int mt_y = 0) 
   while (mt_y > 1 && split_col_pad(gmax) * mt_y > 32) mt_y >>= 1;
   std::vector<int> pa(ng + 1, 0), py(ng + 1, 0), pf(ng + 1, 0), par(ng + 1, 0), pyr(ng + 1, 0);
   size_t sa = 0, sy = 0;
+  int thr_a = 64, thr_y = 64;  // threads per CTA: one pass over the row tasks of any group
   for (int q = 0; q < ng; ++q) {
     const Inst& I = c->hinst[groups[q].x];
     const int nrun = (I.Kx + 1) * I.Mz;  // the reduced launches: modes m >= 0
@@ -906,6 +907,9 @@ static pcf_status set_split_groups(pcf_ctx* c, int G, int mt = 1, int mt_y = 0) 
     pyr[q + 1] = pyr[q] + split_ctas_per_group(2, nrun, mt_y);
     sa = std::max(sa, smem_yanalysis(I.N, groups[q].y, mt));
     sy = std::max(sy, smem_ysynth(I.N, groups[q].y, mt_y));
+    const bool fp64 = c->plane_kind != 2;
+    thr_a = std::max(thr_a, split_yanalysis_threads(I.N, groups[q].y, mt, fp64));
+    thr_y = std::max(thr_y, split_ysynth_threads(I.N, groups[q].y, mt_y, fp64));
   }
   if (std::max(sa, sy) > 227 * 1024) return PCF_ENOTSUP;
   if (!c->d_groups) {
@@ -932,6 +936,8 @@ static pcf_status set_split_groups(pcf_ctx* c, int G, int mt = 1, int mt_y = 0) 
   c->cta_yy = py[ng];
   c->sm_ya = sa;
   c->sm_yy = sy;
+  c->thr_ya = thr_a;
+  c->thr_yy = thr_y;
   if (c->sm_yf <= 227 * 1024) PCF_CUDA(set_ystep_smem(c->sm_yf));
   // the solve follows the same group size unless tuned on its own (autotune_split)
   return set_solve_groups(c, G);
@@ -968,9 +974,10 @@ static pcf_status autotune_split(pcf_ctx* c) {
             return;
           }
           for (int op : {(int)MODE_PHI, (int)MODE_PSI_UPDATE}) {
-            launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), op, c->plane_kind == 2, c->smt);
+            launch_yanalysis(c->cta_ya, c->thr_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), op, c->plane_kind == 2,
+                             c->smt);
             launch_ysolve(c->grid_ys, c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys, c->cs, gl_solve(c), op);
-            launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), op == MODE_PHI ? 1 : 0, 1,
+            launch_ysynth_split(c->cta_yy, c->thr_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), op == MODE_PHI ? 1 : 0, 1,
                                 c->plane_kind == 2, c->smt_y);
           }
         };
@@ -1010,11 +1017,13 @@ static pcf_status autotune_split(pcf_ctx* c) {
       if (set_split_groups(c, best, mt, mt) != PCF_OK || c->smt != mt || c->smt_y != mt) continue;
       float ms = 0.f;
       PCF_TRY(time5([&] {
-        launch_yanalysis(c->cta_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), MODE_PHI, c->plane_kind == 2, c->smt);
+        launch_yanalysis(c->cta_ya, c->thr_ya, c->sm_ya, c->cs, gl_of(c, c->pre_ya), MODE_PHI, c->plane_kind == 2,
+                         c->smt);
       }, &ms));
       if (ms < ba) { ba = ms; mt_a = mt; }
       PCF_TRY(time5([&] {
-        launch_ysynth_split(c->cta_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), 1, 1, c->plane_kind == 2, c->smt_y);
+        launch_ysynth_split(c->cta_yy, c->thr_yy, c->sm_yy, c->cs, gl_of(c, c->pre_yy), 1, 1, c->plane_kind == 2,
+                            c->smt_y);
       }, &ms));
       if (ms < by) { by = ms; mt_y = mt; }
     }

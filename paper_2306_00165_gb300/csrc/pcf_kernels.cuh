@@ -127,13 +127,17 @@ size_t smem_ysolve(int N, int G);
 size_t smem_ysynth(int N, int G, int mt);
 // ff_arith: the Chebyshev dot products in float-float arithmetic (float-float form)
 // mt: consecutive modes per CTA of the analysis and synthesis kernels (col_pad(G) mt <= 32)
-void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith, int mt);
+void launch_yanalysis(int ctas, int threads, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith,
+                      int mt);
 void launch_ysolve(int ctas, int nitems, int bufsz, int scr_rows, size_t smem, cudaStream_t s, GroupLaunch gl,
                    int op);
 void launch_jnorm(int ninst, cudaStream_t s, const Inst* insts, int step_index);
 int ysolve_ctas_per_sm(size_t smem);
-void launch_ysynth_split(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int slot, int check_active,
-                         bool ff_arith, int mt);
+void launch_ysynth_split(int ctas, int threads, size_t smem, cudaStream_t s, GroupLaunch gl, int slot,
+                         int check_active, bool ff_arith, int mt);
+// threads per CTA of the split analysis / synthesis: one pass over a CTA's row tasks
+int split_yanalysis_threads(int N, int G, int mt, bool fp64);
+int split_ysynth_threads(int N, int G, int mt, bool fp64);
 cudaError_t set_split_smem(size_t analysis, size_t solve, size_t synth);
 // The fused per-mode half-step (analysis + solve + synthesis), one CTA per (group, mode).
 size_t smem_ystep(int N, int G);

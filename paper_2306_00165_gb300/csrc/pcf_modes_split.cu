@@ -42,6 +42,12 @@ namespace pcf {
 #endif
 constexpr int kSplitThreads = PCF_SPLIT_THREADS;
 constexpr int kAnalysisThreads = PCF_ANALYSIS_THREADS;
+// Launch bounds of the split synthesis and analysis kernels: the host sizes each launch to
+// one pass over a CTA's row tasks (split_ysynth_threads, split_yanalysis_threads), within
+// these bounds; the register budgets (five and four resident CTAs) are those of the 128- and
+// 256-thread kernels with ten and five resident CTAs.
+constexpr int kSynthMaxThreads = 256;
+constexpr int kAnalysisMaxThreads = 320;
 #ifndef PCF_SOLVE_THREADS
 #define PCF_SOLVE_THREADS 128
 #endif
@@ -137,7 +143,7 @@ __device__ __forceinline__ void group_flags(const GroupLaunch& gl, int first, in
 // Five resident CTAs per SM (48 registers): with one mode per CTA a 32x33x32 batch of 8 has
 // 7.5 CTAs per SM, one and a half waves at five and two at four.
 template <class A>
-__global__ void __launch_bounds__(kAnalysisThreads, 5) k_yanalysis(GroupLaunch gl, int op, int mt) {
+__global__ void __launch_bounds__(kAnalysisMaxThreads, 4) k_yanalysis(GroupLaunch gl, int op, int mt) {
   extern __shared__ double sm[];
   __shared__ int live[kMaxGroup];
   int local;
@@ -492,7 +498,7 @@ __device__ __forceinline__ double* mirror_dst(const GroupLaunch& gl, const Inst&
 template <class A, bool RED>
 // RED: a reduced launch (gl.reduced), which also writes the mirrored y-values of mode -m
 // (a separate instantiation, so that the full launch keeps its register budget).
-__global__ void __launch_bounds__(kSplitThreads, 10) k_ysynth(GroupLaunch gl, int slot, int check_active, int mt) {
+__global__ void __launch_bounds__(kSynthMaxThreads, 5) k_ysynth(GroupLaunch gl, int slot, int check_active, int mt) {
   extern __shared__ double sm[];
   __shared__ int live[kMaxGroup];
   int local;
@@ -975,9 +981,27 @@ size_t smem_ysynth(int N, int G, int mt) {
   const size_t H = N / 2 + 1, XS = col_pad_host(G) * mt + 1;
   return sizeof(double) * (2 * H * H + (2 * H) * XS);
 }
-void launch_yanalysis(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith, int mt) {
-  if (ff_arith) k_yanalysis<ff><<<ctas, kAnalysisThreads, smem, s>>>(gl, op, mt);
-  else k_yanalysis<double><<<ctas, kAnalysisThreads, smem, s>>>(gl, op, mt);
+// Row tasks of one CTA, as the kernels count them (pairs of rows per lane in whole warps,
+// then the lone middle row's single-chain tasks in FP64), and the threads for one pass.
+static int tasks_ru(int a, int b) { return (a + b - 1) / b * b; }
+int split_yanalysis_threads(int N, int G, int mt, bool fp64) {
+  const int H = N / 2 + 1, half = N / 2, SPt = (int)col_pad_host(G) * mt, RW = 32 / SPt;
+  const int hE = (H + 1) / 2, hO = (half + 1) / 2;
+  const bool loneE = fp64 && (H & 1) && (hE - 1) % RW == 0, loneO = fp64 && (half & 1) && (hO - 1) % RW == 0;
+  const int pE = hE - (loneE ? 1 : 0), pO = hO - (loneO ? 1 : 0);
+  const int ntask = (tasks_ru(pE, RW) + tasks_ru(pO, RW)) * SPt + (loneE || loneO ? SPt : 0);
+  return std::max(64, std::min(kAnalysisMaxThreads, tasks_ru(ntask, 32)));
+}
+int split_ysynth_threads(int N, int G, int mt, bool fp64) {
+  const int H = N / 2 + 1, SPt = (int)col_pad_host(G) * mt, RW = 32 / SPt, hJ = (H + 1) / 2;
+  const bool lone = fp64 && (H & 1) && (hJ - 1) % RW == 0;
+  const int ntask = tasks_ru(hJ - (lone ? 1 : 0), RW) * SPt + (lone ? SPt : 0);
+  return std::max(64, std::min(kSynthMaxThreads, tasks_ru(ntask, 32)));
+}
+void launch_yanalysis(int ctas, int threads, size_t smem, cudaStream_t s, GroupLaunch gl, int op, bool ff_arith,
+                      int mt) {
+  if (ff_arith) k_yanalysis<ff><<<ctas, threads, smem, s>>>(gl, op, mt);
+  else k_yanalysis<double><<<ctas, threads, smem, s>>>(gl, op, mt);
 }
 void launch_ysolve(int ctas, int nitems, int bufsz, int scr_rows, size_t smem, cudaStream_t s, GroupLaunch gl,
                    int op) {
@@ -991,14 +1015,14 @@ int ysolve_ctas_per_sm(size_t smem) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ysolve, kSolveThreads, smem) != cudaSuccess) return 0;
   return n;
 }
-void launch_ysynth_split(int ctas, size_t smem, cudaStream_t s, GroupLaunch gl, int slot, int check_active,
-                         bool ff_arith, int mt) {
+void launch_ysynth_split(int ctas, int threads, size_t smem, cudaStream_t s, GroupLaunch gl, int slot,
+                         int check_active, bool ff_arith, int mt) {
   if (gl.reduced) {
-    if (ff_arith) k_ysynth<ff, true><<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active, mt);
-    else k_ysynth<double, true><<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active, mt);
+    if (ff_arith) k_ysynth<ff, true><<<ctas, threads, smem, s>>>(gl, slot, check_active, mt);
+    else k_ysynth<double, true><<<ctas, threads, smem, s>>>(gl, slot, check_active, mt);
   } else {
-    if (ff_arith) k_ysynth<ff, false><<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active, mt);
-    else k_ysynth<double, false><<<ctas, kSplitThreads, smem, s>>>(gl, slot, check_active, mt);
+    if (ff_arith) k_ysynth<ff, false><<<ctas, threads, smem, s>>>(gl, slot, check_active, mt);
+    else k_ysynth<double, false><<<ctas, threads, smem, s>>>(gl, slot, check_active, mt);
   }
 }
 cudaError_t set_split_smem(size_t analysis, size_t solve, size_t synth) {
