@@ -57,7 +57,8 @@ typedef enum {
 typedef enum {
   PCF_FP64 = 0,         /* the plain method: FP64 throughout */
   PCF_MIXED = 1,        /* FP32 x-z transforms and products, split-BF16 tensor-core Chebyshev
-                           transforms, FP64 Stokes solves, norms and state */
+                           transforms, FP64 Stokes solves, norms and state; ny <= 113
+                           (PCF_ENOTSUP above) */
   PCF_FLOAT_FLOAT = 2   /* x-z transforms and products in float-float arithmetic (pairs of
                            FP32, ~48 significant bits) on the FP32 pipe; everything else FP64 */
 } pcf_precision;
@@ -94,8 +95,10 @@ typedef struct pcf_params {
                            pcf_plane_variant reports the choice. */
   int contraction_kernel; /* Chebyshev transforms of the mixed form (split-BF16, FP32
                            accumulation): 0 = tcgen05 MMAs with the accumulator in tensor
-                           memory; 1 = warp-level mma.sync.  pcf_contraction_variant reports
-                           the choice.  Ignored by the other forms. */
+                           memory (the padded matrix in one 128-row MMA tile, its operand
+                           moved by bulk copies on the TMA engine); 1 = warp-level
+                           mma.sync.  pcf_contraction_variant reports the choice.  Ignored
+                           by the other forms. */
   double suction_length; /* PCF_ASBL only: suction length delta of the boundary layer in
                            units of the half-height (> 0, finite; PCF_EINVAL otherwise).
                            Ignored by the other base flows. */

@@ -103,24 +103,35 @@ __global__ void __launch_bounds__(kT5Threads) k_cheb_tc05(LaunchInfo li, int slo
   unsigned char* sAl = sm5 + abytes;
   unsigned char* sBh = sm5 + t5_aregion(P);
   unsigned char* sBl = sBh + bbytes;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sBl + bbytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sBl + bbytes);  // MMA completion
+  uint64_t* abar = mbar + 1;                                      // A operand arrival
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
   float* sD = reinterpret_cast<float*>(sm5);
-  // A: analysis Cinv (matrix 2), synthesis C (0) for the values, C' (1) for the y-derivatives
+  // A: analysis Cinv (matrix 2), synthesis C (0) for the values, C' (1) for the y-derivatives.
+  // Its hi and lo parts are stored in global memory as images of the shared-memory region
+  // (core-matrix layout), and one thread moves them with two bulk copies on the TMA engine
+  // while the CTA splits its B tile.
   const int mat = SYN ? (q < 3 ? 0 : 1) : 2;
-  const uint4* Ahg = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(I.tcA) + (size_t)(2 * mat) * P * P);
-  const uint4* Alg = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(I.tcA) + (size_t)(2 * mat + 1) * P * P);
-  // consecutive threads take consecutive rows of one K chunk: contiguous 16-byte stores
-  for (int t = threadIdx.x; t < kT5Rows * KC; t += blockDim.x) {
-    const int kc = t / kT5Rows, r = t - kc * kT5Rows;
-    uint4 h = make_uint4(0u, 0u, 0u, 0u), l = h;
-    if (r < P) {
-      h = Ahg[(size_t)r * KC + kc];
-      l = Alg[(size_t)r * KC + kc];
-    }
-    const uint32_t o = chunk_off(r, kc, kT5Rows);
-    *reinterpret_cast<uint4*>(sAh + o) = h;
-    *reinterpret_cast<uint4*>(sAl + o) = l;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(abar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const unsigned char* img = static_cast<const unsigned char*>(I.tcA5) + (size_t)(2 * mat) * abytes;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(abar)),
+                 "r"((uint32_t)(2 * abytes))
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(sAh)),
+        "l"(img), "r"((uint32_t)abytes), "r"(smem_addr(abar))
+        : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(sAl)),
+        "l"(img + abytes), "r"((uint32_t)abytes), "r"(smem_addr(abar))
+        : "memory");
   }
   // B: 8 consecutive K elements of one column per task, split into BF16 high and low parts
   for (int t = threadIdx.x; t < kT5Cols * KC; t += blockDim.x) {
@@ -159,14 +170,30 @@ __global__ void __launch_bounds__(kT5Threads) k_cheb_tc05(LaunchInfo li, int slo
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_addr(tslot)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (threadIdx.x == 0) {
-    ok = 1;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
-  }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
+  // the A operand must have arrived before the MMAs read it (bounded wait, as below)
+  bool a_ok = true;
   if (threadIdx.x == 0) {
+    uint32_t arrived = 0;
+    const long long ta = clock64();
+    while (!arrived) {
+      asm volatile(
+          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(arrived)
+          : "r"(smem_addr(abar)), "r"(0u)
+          : "memory");
+      if (!arrived && clock64() - ta > 4000000000LL) break;
+    }
+    if (!arrived) {
+      // no MMAs: release the waiters below through the completion barrier, outputs NaN
+      a_ok = false;
+      ok = 0;
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
+    }
+  }
+  if (threadIdx.x == 0 && a_ok) {
     // kind::f16 instruction descriptor: FP32 accumulator (bits 4-5 = 1), BF16 A and B (bits
     // 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kT5Cols >> 3) << 17) |
@@ -205,7 +232,7 @@ __global__ void __launch_bounds__(kT5Threads) k_cheb_tc05(LaunchInfo li, int slo
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   // tcgen05.ld is warp-collective: read the accumulator only if every lane saw the MMAs finish
-  if (__all_sync(0xffffffffu, done)) {
+  if (__all_sync(0xffffffffu, done && ok)) {
     {
       const int quarter = warp & 3, half = warp >> 2;
       uint32_t r[32];

@@ -332,6 +332,23 @@ std::vector<uint16_t> make_tc_matrices(int N) {
   return t;
 }
 
+// The tcgen05 contraction's operands as byte images of its shared-memory A region: for each
+// matrix and part (hi, lo) of make_tc_matrices, 128 rows (rows >= P zero) x P K elements in
+// the no-swizzle K-major core-matrix layout, where the chunk of row r and K elements
+// 8kc..8kc+7 starts at element ((kc * 16 + r / 8) * 64 + (r % 8) * 8).  One bulk copy then
+// fills the region.  Empty when P > 128 (the kernel is not used there).
+std::vector<uint16_t> make_tc05_images(const std::vector<uint16_t>& t, int P) {
+  if (P > 128) return {};
+  const size_t img = (size_t)128 * P;
+  std::vector<uint16_t> o(6 * img, 0);
+  for (int a = 0; a < 6; ++a)
+    for (int r = 0; r < P; ++r)
+      for (int kc = 0; kc < P / 8; ++kc)
+        for (int e = 0; e < 8; ++e)
+          o[a * img + ((size_t)kc * 16 + r / 8) * 64 + (r % 8) * 8 + e] = t[(size_t)a * P * P + (size_t)r * P + 8 * kc + e];
+  return o;
+}
+
 std::vector<float2> to_float2(const std::vector<double2>& v) {
   std::vector<float2> o(v.size());
   for (size_t i = 0; i < v.size(); ++i) o[i] = make_float2((float)v[i].x, (float)v[i].y);
@@ -684,6 +701,7 @@ struct GridTables {
   unsigned char *rotx, *rotz;
   float2 *twxf = nullptr, *twzf = nullptr;
   uint16_t* tcA = nullptr;
+  uint16_t* tcA5 = nullptr;
   double sig[2];
 };
 
@@ -750,12 +768,17 @@ static pcf_status build_tables(pcf_ctx* c, const pcf_params* prm, GridTables* g)
     c->allocs.push_back(g->cheb_ff);
   }
   if (prm->precision == PCF_MIXED) {
-    if (upload(to_float2(twx), &g->twxf) || upload(to_float2(twz), &g->twzf) ||
-        upload(make_tc_matrices(N), &g->tcA))
+    const std::vector<uint16_t> tcm = make_tc_matrices(N);
+    if (upload(to_float2(twx), &g->twxf) || upload(to_float2(twz), &g->twzf) || upload(tcm, &g->tcA))
       return PCF_ECUDA;
     c->allocs.push_back(g->twxf);
     c->allocs.push_back(g->twzf);
     c->allocs.push_back(g->tcA);
+    const std::vector<uint16_t> img = make_tc05_images(tcm, (ny + 15) & ~15);
+    if (!img.empty()) {
+      if (upload(img, &g->tcA5)) return PCF_ECUDA;
+      c->allocs.push_back(g->tcA5);
+    }
   }
   g->dense0 = g->dense1 = nullptr;
   const bool dense = N <= kDenseMaxN && prm->solve_kind != 1;
@@ -1235,7 +1258,11 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
   // the FP32 form's plane kernels keep their transforms in warp registers wherever every
   // instance's nx and nz allow it (unless the caller asks for the shared-memory kernels)
   c->plane_warp = c->mixed && list[0].plane_kernel != 1;
+  // the tcgen05 contraction holds the whole padded matrix in one 128-row MMA tile (the mixed
+  // form's ny <= 113 keeps it there)
   c->tc05 = c->mixed && list[0].contraction_kernel != 1;
+  for (int k = 0; k < nlist; ++k)
+    if (((list[k].ny + 15) & ~15) > 128) c->tc05 = false;
   // symmetric descent on the modes m >= 0 when every instance enforces s2 (split kernels)
   c->reduced = true;
   for (int k = 0; k < nlist; ++k)
@@ -1266,7 +1293,7 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
       I.jcount = jc + b;
       if (c->mixed) {
         I.yvf = yvf + o_yv; I.physf = phf + o_ph; I.xzf = xzf + o_xz; I.xzc = xzc + o_xz;
-        I.twxf = g.twxf; I.twzf = g.twzf; I.tcA = g.tcA; I.mixed = 1;
+        I.twxf = g.twxf; I.twzf = g.twzf; I.tcA = g.tcA; I.tcA5 = g.tcA5; I.mixed = 1;
       } else {
         I.yv = yv + o_yv; I.phys = ph + o_ph; I.xz = xz + o_xz; I.frg = fr + o_fr;
       }

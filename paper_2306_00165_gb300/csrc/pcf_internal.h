@@ -123,6 +123,8 @@ struct Inst {
   float2* xzc;        // [3][ny][Mx][Mz]: Chebyshev coefficients of xzf (n in place of j)
   int mixed;          // 1: the mode kernel reads xzc and leaves the synthesis to the tensor-core kernel
   const void* tcA;    // bf16 [6][P][P], P = ny rounded up to 16: C hi/lo, C' hi/lo, Cinv hi/lo
+  const void* tcA5;   // the same as [6] shared-memory images of the tcgen05 kernel's A region
+                      // (128 x P, core-matrix layout); null when P > 128
   double* hist;       // J history base (may be null)
   int hist_stride;
   int* active;        // 1 = keep updating

@@ -57,6 +57,15 @@ def test_mixed_residual_and_gradient_per_field(pcf, grid, plane_kernel, contract
         assert abs(float(J[b]) - J_ref) <= 1e-5 * J_ref
 
 
+def test_mixed_ny_limit(pcf):
+    """The mixed form serves ny <= 113 (one 128-row tensor-core tile of the padded Chebyshev
+    matrix); a larger ny is refused at creation, before any launch."""
+    with pytest.raises(pcf.PCFError, match="not supported"):
+        pcf.Solver(16, 129, 16, batch=1, precision=1)
+    with pytest.raises(pcf.PCFError, match="not supported"):
+        pcf.Solver(16, 115, 16, batch=1, precision=1)
+
+
 def test_mixed_descent_then_fp64_refinement(pcf):
     """30 mixed steps track the oracle to 1e-5; 10 FP64 refinement steps continued on the
     GPU keep tracking the oracle's plain trajectory from the same seeded guess, without
