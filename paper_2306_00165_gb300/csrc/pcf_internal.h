@@ -183,17 +183,24 @@ PCF_HD void class_deriv(int N, int q, const double* __restrict__ a, const double
 }
 
 // xi = -dv/dy from the class array v (parity pv, stride vs) into the class array xi (parity
-// 1 - pv, stride xs): class_deriv's recurrence with its 2(n+1) factors formed in place (exact
-// integers, so the operations and their results are those of class_deriv followed by the sign).
-PCF_HD void xi_from_v(int N, int pv, const double* __restrict__ v, int vs, double* __restrict__ xi, int xs) {
+// 1 - pv, stride xs): class_deriv's recurrence with the sign carried in the accumulator,
+// nacc = -acc (fma(-c, v, nacc) = -fma(c, v, acc) exactly), so that each step is one FMA on
+// the dependent chain; two_n holds 2n for v's class elements (RcoLayout off(pv, 4)).  The
+// results are those of class_deriv followed by the sign.
+PCF_HD void xi_from_v(int N, int pv, const double* __restrict__ v, int vs, double* __restrict__ xi, int xs,
+                      const double* __restrict__ two_n) {
   const int p = 1 - pv;
   const int Md = (N - p) / 2 + 1;
-  double acc = 0.0;
+  double nacc = 0.0;
   for (int j = Md - 1; j >= 0; --j) {
     const int n = p + 2 * j;
-    if (n + 1 <= N) acc += (double)(2 * (n + 1)) * v[((n + 1 - pv) / 2) * vs];
-    xi[j * xs] = (p == 0 && j == 0) ? -(acc * 0.5) : -acc;
+    if (n + 1 <= N) {
+      const int i = (n + 1 - pv) / 2;
+      nacc = fma(-two_n[i], v[i * vs], nacc);
+    }
+    xi[j * xs] = nacc;
   }
+  if (p == 0) xi[0] = nacc * 0.5;
 }
 
 // One chain of the per-mode Stokes solve: group g (v parity g), real (rho = 0) or

@@ -812,7 +812,7 @@ __global__ void __launch_bounds__(320) k_mode(LaunchInfo li, int op, int sig, in
         const int m = m0 + mm, ix = m / Mz, p = m - ix * Mz;
         if (m == 0) continue;
         double* sc = Ch + ((size_t)mm * 4 + g * 2 + rho) * 6 * Mh;
-        xi_from_v(N, g, sc + 2 * Mh, 1, sc + 3 * Mh, 1);
+        xi_from_v(N, g, sc + 2 * Mh, 1, sc + 3 * Mh, 1, rco + RL.off(g, 4));
       }
     } else {
     // Stokes step: 4 chains per mode (group x part)

@@ -423,7 +423,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_ysolve(GroupLaunch gl, int op
     }
     __syncthreads();
     if (!mean) {  // xi = -dv/dy (class 1-g), one column per thread
-      for (int s = threadIdx.x; s < SP; s += blockDim.x) xi_from_v(N, pv, OV + s, XS, OX + s, XS);
+      for (int s = threadIdx.x; s < SP; s += blockDim.x)
+        xi_from_v(N, pv, OV + s, XS, OX + s, XS, I0.rco + RcoLayout(N).off(pv, 4));
       __syncthreads();
     }
     // assembly and output: v (class g) and u, w (class 1-g); mean mode: u, v = 0, w (class g)
@@ -853,7 +854,8 @@ __global__ void __launch_bounds__(kStepThreads) k_ystep(GroupLaunch gl, int op) 
     }
     __syncthreads();
     if (!mean) {  // xi = -dv/dy (class 1-g), one column per thread
-      for (int s = threadIdx.x; s < SP; s += blockDim.x) xi_from_v(N, pv, OV + s, XS, OX + s, XS);
+      for (int s = threadIdx.x; s < SP; s += blockDim.x)
+        xi_from_v(N, pv, OV + s, XS, OX + s, XS, I0.rco + RcoLayout(N).off(pv, 4));
       __syncthreads();
     }
     // assembly: v (class g) and u, w (class 1-g); mean mode: u, v = 0, w (class g)
