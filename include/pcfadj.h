@@ -82,8 +82,12 @@ typedef struct pcf_params {
                            or fused kernels over instance groups; mixed form: dense against
                            sweeps), see pcf_solve_variant.  1: banded sweeps.  2: dense
                            operators inside the single per-mode kernel.  3: FP64 split
-                           analysis / solve / synthesis kernels.  4: FP64 fused per-mode
-                           half-step kernel.  2, 3 and 4 give bit-identical results. */
+                           analysis / solve / synthesis kernels with the dense solve.  4: FP64
+                           fused per-mode half-step kernel.  2, 3 and 4 give bit-identical
+                           results.  5: FP64 split analysis and synthesis kernels with the
+                           Stokes solve by banded sweeps, one thread per chain (group g, mode,
+                           real or imaginary part); with 0 the autotuner times it against the
+                           dense solve. */
   int base_flow;        /* pcf_base_flow: the laminar base flow u_b = (U(y), V, 0) */
   int symmetry;         /* pcf_symmetry mask enforced along the descent and the DNS (0: none).
                            s1 requires PCF_COUETTE (it maps the Poiseuille profile to its
@@ -178,9 +182,11 @@ int pcf_mode_tile(const pcf_ctx* ctx);
 /* Stokes solve the descent step uses: 0 banded tau sweeps inside the per-mode kernel,
  * 1 dense per-mode operators inside the per-mode kernel, 2 dense operators in the split
  * analysis / solve / synthesis kernels over instance groups, 3 dense operators in the fused
- * per-mode half-step kernel over instance groups (2 and 3: FP64 form).  With solve_kind 0
- * the FP64 form times 2 against 3 and the mixed-precision form 0 against 1 at creation,
- * and each keeps the faster.  -1 for a NULL context. */
+ * per-mode half-step kernel over instance groups, 4 banded sweeps with one thread per chain
+ * between the split analysis and synthesis kernels (2, 3 and 4: FP64 and float-float forms).
+ * With solve_kind 0 the FP64 form times 2 against 3 and then the chosen dense solve against
+ * 4, the mixed-precision form 0 against 1, at creation, and each keeps the faster.  -1 for a
+ * NULL context. */
 int pcf_solve_variant(const pcf_ctx* ctx);
 
 /* x-z plane kernels the context launches: 0 shared-memory Stockham passes, 1 transforms in

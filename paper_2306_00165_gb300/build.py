@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpcfadj.so")
 SOURCES = ["pcf_kernels.cu", "pcf_host.cu", "pcf_noalloc.cu", "pcf_dmd.cu", "pcf_cheb_tc.cu", "pcf_modes_split.cu",
-           "pcf_fno.cu", "pcf_sym_dns.cu", "pcf_planes_warp.cu", "pcf_cheb_tc05.cu"]
+           "pcf_fno.cu", "pcf_sym_dns.cu", "pcf_planes_warp.cu", "pcf_cheb_tc05.cu",
+           "pcf_sweep.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-rdc=false"]

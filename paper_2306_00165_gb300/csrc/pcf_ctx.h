@@ -57,6 +57,13 @@ struct pcf_ctx {
   // the solve's own instance groups (its right-hand sides are per instance, so its grouping
   // is independent of the analysis and synthesis kernels'); tuned separately
   int sgrp_s = 0, ngroups_s = 0;
+  // the split step's Stokes solve by banded sweeps, one thread per chain (k_sweep), in place
+  // of the dense solve: CTA prefixes per instance (full and reduced launches) and geometry
+  bool sweep = false;
+  int* pre_sw = nullptr;
+  int* pre_sw_r = nullptr;
+  int cta_sw = 0, cta_sw_r = 0, thr_sw = 32;
+  size_t sm_sw = 0;
   int2* d_groups_s = nullptr;
   bool fused = false;           // the step runs the fused per-mode kernel (k_ystep)
   int* pre_yf = nullptr;        // its CTA prefix over groups [B + 1]

@@ -494,6 +494,11 @@ GroupLaunch gl_solve(pcf_ctx* c, bool red = false) {
   return GroupLaunch{c->dinst, red ? c->pre_ys_r : c->pre_ys, c->d_groups_s, c->ngroups_s, red ? 1 : 0};
 }
 pcf_status launch_split_solve(pcf_ctx* c, int op, bool red = false) {
+  if (c->sweep)
+    return timed(c, op == MODE_PHI ? 3 : 6, [&] {
+      launch_sweep(red ? c->cta_sw_r : c->cta_sw, c->thr_sw, c->sm_sw, c->cs,
+                   LaunchInfo{c->dinst, red ? c->pre_sw_r : c->pre_sw, c->B}, op, red ? 1 : 0);
+    });
   return timed(c, op == MODE_PHI ? 3 : 6, [&] {
     launch_ysolve(red ? c->grid_ys_r : c->grid_ys, red ? c->cta_ys_r : c->cta_ys, c->buf_ys, c->rows_ys, c->sm_ys,
                   c->cs, gl_solve(c, red), op);
@@ -684,7 +689,7 @@ long long pcf_psi_len(int nx, int ny, int nz) {
 
 static bool params_ok(const pcf_params* prm) {
   return grid_ok(prm->nx, prm->ny, prm->nz) && prm->batch >= 1 && prm->Re > 0 && prm->dt > 0 &&
-         prm->dtau_hat > 0 && prm->Lx > 0 && prm->Lz > 0 && prm->solve_kind >= 0 && prm->solve_kind <= 4 &&
+         prm->dtau_hat > 0 && prm->Lx > 0 && prm->Lz > 0 && prm->solve_kind >= 0 && prm->solve_kind <= 5 &&
          prm->modes_per_block >= 0 &&
          (prm->base_flow == PCF_COUETTE || prm->base_flow == PCF_POISEUILLE ||
           (prm->base_flow == PCF_ASBL && prm->suction_length > 0 && std::isfinite(prm->suction_length))) &&
@@ -857,6 +862,27 @@ static std::vector<int2> make_groups(const pcf_ctx* c, int G) {
   return groups;
 }
 
+// Geometry of the split step's sweep solve with `threads` lanes per CTA (32 or 64): CTA
+// prefixes over the instances for the full and the reduced launch, shared memory.
+static pcf_status set_sweep(pcf_ctx* c, int threads) {
+  std::vector<int> per(c->B), perr(c->B);
+  int Nmax = 0;
+  for (int b = 0; b < c->B; ++b) {
+    const Inst& I = c->hinst[b];
+    Nmax = std::max(Nmax, I.N);
+    per[b] = sweep_ctas(I.nmodes, threads);
+    perr[b] = sweep_ctas((I.Kx + 1) * I.Mz, threads);
+  }
+  const size_t sm = smem_sweep(Nmax, threads);
+  if (sm > 227 * 1024) return PCF_ENOTSUP;
+  PCF_TRY(upload_prefix(c, per, &c->pre_sw, &c->cta_sw));
+  PCF_TRY(upload_prefix(c, perr, &c->pre_sw_r, &c->cta_sw_r));
+  PCF_CUDA(set_sweep_smem(sm));
+  c->thr_sw = threads;
+  c->sm_sw = sm;
+  return PCF_OK;
+}
+
 // Instance groups of the persistent Stokes solve (at most G instances each): items, prefix,
 // shared-memory layout and grid.
 static pcf_status set_solve_groups(pcf_ctx* c, int G) {
@@ -986,7 +1012,8 @@ static pcf_status autotune_split(pcf_ctx* c) {
       if (set_split_groups(c, G, mt) != PCF_OK || c->sgrp != G || c->smt != mt) continue;
       for (int fuse = 0; fuse < 2; ++fuse) {
         if (fuse && (mt > 1 || c->sm_yf > 227 * 1024)) continue;  // the fused kernel has no mode tile
-        if ((c->prm.solve_kind == 3 && fuse) || (c->prm.solve_kind == 4 && !fuse)) continue;
+        if (((c->prm.solve_kind == 3 || c->prm.solve_kind == 5) && fuse) || (c->prm.solve_kind == 4 && !fuse))
+          continue;
         // the per-mode work of a whole step in each organisation (both half-steps; the fused
         // path also launches the separate norm kernel)
         auto seq = [&] {
@@ -1052,6 +1079,7 @@ static pcf_status autotune_split(pcf_ctx* c) {
     }
     st = set_split_groups(c, best, mt_a, mt_y);
   }
+  float solve_ms = 1e30f;  // five dense solves in the chosen groups
   if (st == PCF_OK && !c->fused) {
     // the solve alone over its own group sizes
     int best_s = c->sgrp_s;
@@ -1078,6 +1106,34 @@ static pcf_status autotune_split(pcf_ctx* c) {
       }
     }
     st = set_solve_groups(c, best_s);
+    solve_ms = best_s_ms;
+  }
+  c->sweep = false;
+  if (st == PCF_OK && !c->fused && c->prm.solve_kind != 3) {
+    // the banded sweeps, one thread per chain, against the dense solve (solve_kind 5: always)
+    int best_t = 0;
+    float best_t_ms = c->prm.solve_kind == 5 ? 1e30f : solve_ms;
+    for (int thr : {32, 64}) {
+      if (set_sweep(c, thr) != PCF_OK) continue;
+      auto seq = [&] {
+        launch_sweep(c->cta_sw, c->thr_sw, c->sm_sw, c->cs, LaunchInfo{c->dinst, c->pre_sw, c->B}, MODE_PHI, 0);
+      };
+      seq();
+      PCF_CUDA(cudaEventRecord(a, c->cs));
+      for (int r = 0; r < 5; ++r) seq();
+      PCF_CUDA(cudaEventRecord(b, c->cs));
+      PCF_CUDA(cudaEventSynchronize(b));
+      float ms = 0.f;
+      PCF_CUDA(cudaEventElapsedTime(&ms, a, b));
+      if (ms < best_t_ms) {
+        best_t_ms = ms;
+        best_t = thr;
+      }
+    }
+    if (best_t > 0) {
+      st = set_sweep(c, best_t);
+      c->sweep = st == PCF_OK;
+    }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -1341,6 +1397,10 @@ static pcf_status create_batch(const pcf_params* list, int nlist, void* stream, 
   if (st == PCF_OK && want > 0 && c->split) {
     st = set_split_groups(c, want);
     c->fused = st == PCF_OK && c->prm.solve_kind == 4 && c->sm_yf <= 227 * 1024;
+    if (st == PCF_OK && c->prm.solve_kind == 5) {
+      st = set_sweep(c, 32);
+      c->sweep = st == PCF_OK;
+    }
   }
   if (st != PCF_OK) return fail(st);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(PCF_ECUDA);
@@ -1375,7 +1435,7 @@ int pcf_symmetric_modes(const pcf_ctx* c) {
 
 int pcf_solve_variant(const pcf_ctx* c) {
   if (!c) return -1;
-  if (c->split) return c->fused ? 3 : 2;
+  if (c->split) return c->fused ? 3 : (c->sweep ? 4 : 2);
   return c->hinst[0].dense[0] ? 1 : 0;
 }
 

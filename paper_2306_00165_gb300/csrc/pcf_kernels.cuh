@@ -76,6 +76,14 @@ __device__ __forceinline__ double norm_from_parts(const Inst& I) {
 // context that needs less must not lower the limit another context launches with.
 cudaError_t raise_smem_limit(const void* func, size_t bytes);
 
+// Stokes step by banded tau sweeps, one thread per chain (pcf_sweep.cu): shared memory per
+// CTA of `threads` lanes, CTAs for an instance whose launch covers nmodes_run modes, launch
+// over a CTA prefix per instance (red: the modes m >= 0 only), and the shared-memory limit.
+size_t smem_sweep(int N, int threads);
+int sweep_ctas(int nmodes_run, int threads);
+void launch_sweep(int ctas, int threads, size_t smem, cudaStream_t s, LaunchInfo li, int op, int red);
+cudaError_t set_sweep_smem(size_t smem);
+
 // kind: plane arithmetic, 0 FP64, 1 FP32 (mixed form), 2 float-float
 void launch_xzsynth(int kind, int ctas, size_t smem, cudaStream_t s, LaunchInfo li, int slot, int nf);
 // step_index >= 0 (adjoint product only): the last CTA of each instance also computes J from

@@ -125,18 +125,25 @@ def test_uneven_64_instance_batch(pcf):
 def test_kernel_organisations_give_the_same_bits(pcf, grids, tile):
     """The per-mode work of a step as one per-mode kernel (solve_kind 2), as analysis, solve
     and synthesis kernels (3), or as one fused half-step kernel over instance groups (4):
-    the same operations per output, so the same bits."""
+    the same operations per output, so the same bits.  The autotuner's choice (0) gives the
+    same bits when it keeps a dense solve; the banded sweeps (variant 4) are another
+    algorithm, held to the parity tolerance."""
     us = _mixed_inputs(grids)
-    outs, hists = [], []
+    outs, hists, variants = [], [], []
     for kind, launches, variant in ((2, 6, 1), (3, 10, 2), (4, 7, 3), (0, None, None)):
         s = pcf.Solver.batched(grids, solve_kind=kind, modes_per_block=tile)
         if launches is not None:
             assert s.launches_per_step() == launches and s.solve_variant() == variant
             assert s.launches_per_call(3) == 1 + 3 * launches - (1 if kind == 3 else 0)
+        variants.append(s.solve_variant())
         u = _flat(us)
         hists.append(s.descent_step(u, 0.01, 4).cpu().numpy())
         outs.append(u.cpu().numpy())
     for k in (1, 2, 3):   # 3: whatever group size, mode tile and organisation the autotuner picked
+        if variants[k] == 4:
+            assert _rel(outs[k], outs[0]) <= TOL
+            assert np.max(np.abs(hists[k] - hists[0]) / hists[0]) <= TOL
+            continue
         assert np.array_equal(outs[0], outs[k])
         assert np.array_equal(hists[0], hists[k])
 
