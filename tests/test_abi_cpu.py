@@ -56,6 +56,10 @@ def test_create_rejects_bad_params_without_gpu(lib):
     h = ctypes.c_void_p()
     assert pcf._lib.pcf_create(ctypes.byref(p), None, ctypes.byref(h)) == 1   # PCF_EINVAL, before any CUDA call
     assert not h.value
+    # solve_kind runs 0..5 (5: the banded sweeps with one thread per chain)
+    p = pcf._Params(32, 33, 32, 1, 1.0, 1.0, 400.0, 0.25, 0.25, 0, 0, 6, 0)
+    assert pcf._lib.pcf_create(ctypes.byref(p), None, ctypes.byref(h)) == 1
+    assert not h.value
     # the suction boundary layer needs a finite suction length > 0, and s1 maps it to blowing
     for delta, sym in ((0.0, 0), (-0.5, 0), (float("nan"), 0), (float("inf"), 0), (0.5, pcf.SYM_S1)):
         p = pcf._Params(32, 33, 32, 1, 1.0, 1.0, 400.0, 0.25, 0.25, 0, 0, 0, pcf.ASBL, sym, 0, 0, delta)
