@@ -762,7 +762,11 @@ __global__ void __launch_bounds__(320) k_mode(LaunchInfo li, int op, int sig, in
       // each) per task.  A task runs both parts' chains (real and imaginary right-hand
       // sides), which share each operator load; every chain keeps the index order of the
       // other kernel organisations.  Mean mode: list A holds the u rows, list B the w rows.
+      // Every task is two operator segments run by the same code (a v row continues its chain
+      // into the second segment; an eta pair stores the first row and starts the second), so
+      // the warp that holds the last tasks of list A and the first of list B runs one pass.
       const int HB = (Mh + 1) / 2, nA = nmod * 2 * Mh, nB = nmod * 2 * HB;
+      const int S1 = 6 * Mh;  // the imaginary part's chain scratch follows the real part's
       for (int t = threadIdx.x; t < nA + nB; t += blockDim.x) {
         const bool isA = t < nA;
         const int tt = isA ? t : t - nA, per = isA ? Mh : HB;
@@ -772,37 +776,46 @@ __global__ void __launch_bounds__(320) k_mode(LaunchInfo li, int op, int sig, in
         const double* D = dn + (size_t)m * DL.per_mode();
         const double* fr = Fr + (size_t)mm * 6 * L2;
         double* s0 = Ch + ((size_t)mm * 4 + g * 2) * 6 * Mh;  // real part's chain scratch
-        double* s1 = s0 + 6 * Mh;                            // imaginary part's
-        if (m == 0) {  // the mean mode
+        const double *c1 = D, *c2 = D;
+        const double *x10 = s0, *x11 = s0, *x20 = s0, *x21 = s0;  // segment inputs, real / imaginary
+        int n1 = 0, n2 = 0;
+        double *o1 = nullptr, *o2 = nullptr;  // real-part outputs (imaginary at + S1)
+        if (m == 0) {  // the mean mode: Eh of class g applied to f_u (list A) or f_w (list B)
           const int Mc = (N - g) / 2 + 1;
-          const double* f0 = fr + (isA ? 0 : 4) * L2 + g * Mh;  // f_u or f_w, class g
-          for (int h = 0; h < (isA ? 1 : 2); ++h) {
-            const int row = r + h * HB;
-            if (row >= Mc) continue;
-            double a0 = 0.0, a1 = 0.0;
-            dot2_ldg(D + DL.at(g, DL.kEh, row, 0), Mh, f0, f0 + L2, Mc, a0, a1);
-            s0[(isA ? 0 : Mh) + row] = a0;
-            s1[(isA ? 0 : Mh) + row] = a1;
+          const double* f0 = fr + (isA ? 0 : 4) * L2 + g * Mh;
+          x10 = x20 = f0;
+          x11 = x21 = f0 + L2;
+          if (r < Mc) { c1 = D + DL.at(g, DL.kEh, r, 0); n1 = Mc; o1 = s0 + (isA ? 0 : Mh) + r; }
+          if (!isA && r + HB < Mc) { c2 = D + DL.at(g, DL.kEh, r + HB, 0); n2 = Mc; o2 = s0 + Mh + r + HB; }
+        } else if (isA) {  // v = Av f_v + Ag g, one chain over both segments
+          if (r < McV) {
+            c1 = D + DL.at(g, DL.kAv, r, 0);
+            x10 = fr + 2 * L2 + pv * Mh;
+            x11 = x10 + L2;
+            n1 = McV;
+            c2 = D + DL.at(g, DL.kAg, r, 0);
+            x20 = s0;
+            x21 = s0 + S1;
+            n2 = McP;
+            o2 = s0 + 2 * Mh + r;
           }
-          continue;
-        }
-        if (isA) {  // v = Av f_v + Ag g
-          if (r >= McV) continue;
-          const double* fv0 = fr + 2 * L2 + pv * Mh;
-          double a0 = 0.0, a1 = 0.0;
-          dot2_ldg(D + DL.at(g, DL.kAv, r, 0), Mh, fv0, fv0 + L2, McV, a0, a1);
-          dot2_ldg(D + DL.at(g, DL.kAg, r, 0), Mh, s0, s1, McP, a0, a1);
-          s0[2 * Mh + r] = a0;
-          s1[2 * Mh + r] = a1;
         } else {  // eta = Eh h, rows r and r + HB
-          for (int h = 0; h < 2; ++h) {
-            const int row = r + h * HB;
-            if (row >= McP) continue;
-            double a0 = 0.0, a1 = 0.0;
-            dot2_ldg(D + DL.at(g, DL.kEh, row, 0), Mh, s0 + Mh, s1 + Mh, McP, a0, a1);
-            s0[4 * Mh + row] = a0;
-            s1[4 * Mh + row] = a1;
-          }
+          x10 = x20 = s0 + Mh;
+          x11 = x21 = s0 + Mh + S1;
+          if (r < McP) { c1 = D + DL.at(g, DL.kEh, r, 0); n1 = McP; o1 = s0 + 4 * Mh + r; }
+          if (r + HB < McP) { c2 = D + DL.at(g, DL.kEh, r + HB, 0); n2 = McP; o2 = s0 + 4 * Mh + r + HB; }
+        }
+        double a0 = 0.0, a1 = 0.0;
+        dot2_ldg(c1, Mh, x10, x11, n1, a0, a1);
+        if (o1) {
+          o1[0] = a0;
+          o1[S1] = a1;
+          a0 = a1 = 0.0;
+        }
+        dot2_ldg(c2, Mh, x20, x21, n2, a0, a1);
+        if (o2) {
+          o2[0] = a0;
+          o2[S1] = a1;
         }
       }
       __syncthreads();
